@@ -1,0 +1,295 @@
+"""Benchmark of the tDPD + RBC step on GB300.
+
+One bench step is one time step of the whole hot path (binning and sort,
+membrane forces, pair force + flux, velocity-Verlet update) over the
+single-RBC workload: a 500-vertex biconcave membrane in tDPD solvent, 20^3
+periodic box at density 3, 24,500 particles. The metric is particle-steps/s.
+
+Native arm (default): libtdpd.so through its C ABI. Each timed step is one
+captured graph replay with CUDA event nodes around every kernel; an L2 flush
+(a write larger than the 129 MB L2) separates the timed steps. The pair
+kernel's duration comes from those events, on the stream it runs on.
+Reference arm (--impl reference): the FP64 CPU oracle on the host cores.
+
+N > 1 (torchrun): replicas only -- every rank advances its own copy of the
+workload (different seed); value sums the particle-steps of all ranks over
+the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = 'tDPD particle-steps/s on 1 GB300 (% HBM roofline); batched vs plain at tol'
+UNIT = 'particle-steps/s'
+WORKLOAD = 'single RBC (500-vertex biconcave, WLC-POW, kb=20kT, area/volume constraints, ' \
+           'membrane viscosity) in tDPD solvent, 20^3 periodic box, rho=3, 24,500 particles, ' \
+           '1 species, permeability 0.1, dt=0.01'
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, 'MEASURED_PEAKS.json')) as f:
+            p = json.load(f)
+        return float(p['hbm_gbs']), 'measured'
+    except Exception:
+        return 6800.0, 'fallback'
+
+
+def dist_env():
+    rank = int(os.environ.get('RANK', '0'))
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+         'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+         'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile('w+', suffix='.csv', delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(['nvidia-smi', '-i', str(self.index), '--query-gpu=' + self.Q,
+                                       '--format=csv,noheader,nounits', '-lms', '100'],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        try:
+            rows = [l.split(',') for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        except Exception:
+            rows = []
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == 'active':
+                        reasons.add(nm)
+            except Exception:
+                pass
+        if not sm:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['unsampled']}
+        return {'sm_mhz': statistics.median(sm), 'sm_max_mhz': max(mx), 'reasons': sorted(reasons),
+                'samples': len(sm)}
+
+
+def oracle_rate(desc, seconds=12.0, max_steps=400):
+    """FP64 oracle (cell-list mode, OpenMP on all host cores) on the workload:
+    steps until ~seconds of CPU work; returns particle-steps/s, steps, cores."""
+    import oracle
+    o = oracle.Oracle(desc, mode=1)
+    n = W.n_mobile(desc)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        o.run(1)
+        steps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return n * steps / dt, steps, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    desc = W.single_rbc()
+    n = W.n_mobile(desc)
+    o = oracle.Oracle(desc, mode=1)
+    for _ in range(args.warmup):
+        o.run(1)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.run(1)
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    value = n * args.steps / total
+    cores = oracle.num_threads()
+    line = {
+        'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world,
+        'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': 1e3 * total / args.steps,
+        'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
+        'data': 'synthetic', 'config': {'workload': WORKLOAD, 'particles': n},
+        'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': cores, 'kind': 'oracle',
+                         'sample': 'full workload, %d oracle steps (FP64 cell list, OpenMP)' % args.steps},
+        'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=torch.device('cuda', local))
+    import paper_1611_06163_gb300 as pkg
+    pkg.build()
+    from paper_1611_06163_gb300 import binding as bd
+
+    desc = W.single_rbc(seed=1002 + rank)
+    n = W.n_mobile(desc)
+    stream = torch.cuda.Stream()
+    h = bd.create_from(desc, stream_ptr=stream.cuda_stream)
+    bd.tdpd_commit(h)
+    nk = bd.tdpd_launches_per_step(h)
+    names = [bd.tdpd_kernel_name(h, k) for k in range(nk)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device='cuda')
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            flush.fill_(1.0)
+            bd.tdpd_step_timed(h)
+    bd.tdpd_sync(h)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kms = []
+    barrier()
+    with Clocks(local) as clk:
+        t_wall = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(float(k))            # evict the previous step's state from L2
+                ev[k][0].record(stream)
+                kms.append(bd.tdpd_step_timed(h))   # graph replay + per-kernel events; syncs
+                ev[k][1].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    bd.tdpd_sync(h)
+    if world > 1:
+        t = torch.tensor([total_ms], device='cuda', dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * args.steps / (total_ms * 1e-3)
+
+    # dominant kernel: the pair force + flux + update
+    K = np.array(kms)
+    mean_k = K.mean(axis=0)
+    ipair = names.index('pair')
+    pair_ms = float(mean_k[ipair])
+    # algorithmic bytes per particle of the pair kernel: read r, v~ (16 B
+    # each), C~ (4 B per species), v, F (16 B each), C, Q (4 B per species);
+    # write v, F (16 B each), C, Q (4 B per species); plus the (cell, rank)
+    # of the next binning (8 B) = 112 + 16 * ns bytes
+    ns = int(desc['n_species'])
+    bytes_pp = 112 + 16 * ns
+    hbm, src = peaks()
+    achieved = bytes_pp * n / (pair_ms * 1e-3) / 1e9
+    roof = {'bound': 'hbm', 'achieved': achieved, 'peak': hbm, 'unit': 'GB/s',
+            'frac': achieved / hbm, 'traffic': None, 'peak_source': src,
+            'kernel': 'k_pair', 'bytes_per_particle': bytes_pp,
+            'kernel_ms': {nm: float(m) for nm, m in zip(names, mean_k)}}
+
+    # end to end through the public API: host state in (pinned), one step,
+    # observables out
+    pos, vel, conc = bd.tdpd_read_state(h, 0, ns)
+    hp = torch.from_numpy(pos).pin_memory()
+    hv = torch.from_numpy(vel).pin_memory()
+    hc = torch.from_numpy(conc).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        bd.tdpd_set_state(h, 0, hp.numpy(), hv.numpy(), hc.numpy())
+        bd.tdpd_step(h, 1)
+        bd.tdpd_read_observables(h, 0)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {'value': world * n * e2e_steps / e2e_s, 'unit': UNIT,
+           'h2d_bytes_per_step': int(pos.nbytes + vel.nbytes + conc.nbytes),
+           'd2h_bytes_per_step': 8 * (5 + 8),
+           'path': 'tdpd_set_state (pinned host) + tdpd_step(1) + tdpd_read_observables'}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, steps, cores = oracle_rate(W.single_rbc(), seconds=args.cpu_seconds)
+        cpu = {'value': rate, 'unit': UNIT, 'cores': cores, 'kind': 'oracle',
+               'sample': 'full workload, %d FP64 oracle steps (cell list, OpenMP)' % steps}
+    bd.tdpd_destroy(h)
+    if rank == 0:
+        line = {
+            'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world, 'steps': args.steps,
+            'warmup': args.warmup, 'ms_per_step': total_ms / args.steps, 'higher_is_better': True,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
+            'config': {'workload': WORKLOAD, 'particles': n, 'box': [20, 20, 20], 'rho': 3,
+                       'l2': 'flushed between timed steps (256 MB write)',
+                       'parallelism': 'replicas only' if world > 1 else 'single GPU'},
+            'roofline': roof,
+            'cpu_baseline': cpu,
+            'e2e': e2e,
+            'gpu_launches': nk * args.steps,
+            'clocks': clk.summary(),
+            'wall_s': t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=200)
+    ap.add_argument('--warmup', type=int, default=10)
+    ap.add_argument('--impl', default='native', choices=['native', 'reference'])
+    ap.add_argument('--cpu-seconds', type=float, default=12.0)
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    args = ap.parse_args()
+    if args.impl == 'reference':
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == '__main__':
+    sys.exit(main())

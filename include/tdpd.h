@@ -1,0 +1,200 @@
+/*
+ * tdpd.h -- C ABI of libtdpd.so: transport Dissipative Particle Dynamics
+ * (tDPD) with triangulated red-blood-cell (RBC) membranes on one GB300 GPU.
+ *
+ * The method is that of Blumers, Tang, Li, Li & Karniadakis, "GPU-accelerated
+ * red blood cell simulations with transport dissipative particle dynamics"
+ * (arXiv:1611.06163), Sec. 2:
+ *   - pairwise conservative, dissipative and random forces (Eq. 1-4),
+ *   - Fickian concentration flux per species (Eq. 5-6; the random flux Q^R is
+ *     dropped as in Sec. 2.1; Q^S is a first-order reaction A -> B),
+ *   - membrane forces: WLC + POW bonds (Eq. 10-11), bond viscosity and random
+ *     force (Eq. 12-13), global/local area and global volume constraints
+ *     (Eq. 14-15), bending (Eq. 16),
+ *   - a Groot-Warren modified velocity-Verlet update of r, v and C.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns tdpd_status; TDPD_OK is 0. On failure the
+ *     handle's message is available from tdpd_last_error(). No C++ exception
+ *     crosses this boundary. Calls on one handle are not thread-safe.
+ *   - Handles are opaque. The library owns every device allocation behind a
+ *     handle; the caller owns every pointer it passes. Host arrays are read or
+ *     written during the call only (the call copies); none is retained.
+ *   - Particle arrays are in load order: the free particles of each
+ *     tdpd_add_particles call in order, then the vertices of each membrane
+ *     (tdpd_add_rbc) in vertex order. pos/vel/force are float[n*3] (x,y,z per
+ *     particle), conc/flux are float[n*n_species] (species fastest).
+ *   - A particle's id is its load-order index within its replica; the pairwise
+ *     random numbers are keyed on ids (Sec. 3.1 "particle signatures").
+ *   - Work is enqueued on the stream given to tdpd_set_stream (default: the
+ *     library's own stream). tdpd_step does not synchronise; reads do.
+ */
+#ifndef TDPD_H
+#define TDPD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TDPD_MAX_TYPES 4
+#define TDPD_MAX_SPECIES 8
+#define TDPD_MAX_IDS (1 << 24)      /* particles per replica */
+
+typedef enum {
+    TDPD_OK = 0,
+    TDPD_EINVAL = 1,      /* bad argument or parameter (message says which) */
+    TDPD_ENOMEM = 2,      /* device or host allocation failed */
+    TDPD_ECUDA = 3,       /* a CUDA runtime call failed */
+    TDPD_EOVERFLOW = 4,   /* an index or size limit was exceeded */
+    TDPD_ENONFINITE = 5,  /* a replica produced a non-finite force or state */
+    TDPD_ETIMEOUT = 6,    /* a bounded device wait gave up */
+    TDPD_ESTATE = 7       /* call not valid in the handle's current state */
+} tdpd_status;
+
+typedef struct tdpd_sys tdpd_sys;
+
+/* One replica: box, species, cut-offs and integrator (Sec. 2.1, Eq. 3-6).
+ * The cell list needs at least three cells of edge >= max(rc, rcc) per axis. */
+typedef struct {
+    float L[3];                 /* box edges; positions live in [0, L) */
+    int32_t periodic[3];        /* 1 periodic; axis 2 may be 0 (walls) */
+    float wall_lo, wall_hi;     /* bounce-back planes along z if !periodic[2] */
+    int32_t n_types;            /* 1..TDPD_MAX_TYPES */
+    int32_t n_species;          /* 1..TDPD_MAX_SPECIES */
+    uint64_t seed;              /* keys every random number of the replica */
+    float dt, lambda;           /* time step; velocity-Verlet predictor lambda */
+    float rc, s_f;              /* force cut-off; w_R = (1 - r/rc)^(s_f/2) */
+    float rcc, s_c;             /* flux cut-off; w_DC = (1 - r/rcc)^s_c */
+    float body_force[3];        /* added to every non-frozen particle */
+    uint32_t frozen_types;      /* bit t: particles of type t are not moved */
+    int32_t exclude_same_body;  /* 1: no Eq. 3 forces within one membrane */
+} tdpd_config;
+
+/* Membrane constants (Sec. 2.2). Bond l_m = l0/x0 and k_p are set per bond
+ * so each bond is force-free at its rest length l0. V0 = v_ratio * A0^1.5
+ * (the A-V scaling of Sec. 2.2); v_ratio <= 0 takes the rest volume. */
+typedef struct {
+    float kT, p, x0, m;         /* Eq. 10-11 */
+    float kg, kl, kv;           /* Eq. 14-15 */
+    float kb, theta0;           /* Eq. 16 */
+    float gammaT, gammaC;       /* Eq. 12-13; needs 3*gammaC >= gammaT */
+    float v_ratio;
+} tdpd_membrane;
+
+/* FP64 observables of one replica at its current step. */
+typedef struct {
+    int64_t step;
+    int32_t n_particles, n_mobile, n_species, n_rbc;
+    double kT;                          /* sum |v - vbar|^2 / (3 (n_mobile-1)) */
+    double momentum[3];                 /* sum v over non-frozen particles */
+    double mass[TDPD_MAX_SPECIES];      /* sum C_s over all particles */
+} tdpd_obs;
+
+/* ---------------------------------------------------------------- set-up */
+
+/* Create a handle holding one replica described by cfg (Sec. 2.1). Pair
+ * coefficients default to zero and every kappa to zero. */
+tdpd_status tdpd_create(tdpd_sys **out, const tdpd_config *cfg);
+
+/* Eq. 3 coefficients alpha_ij, gamma_ij, sigma_ij for the type pair (set
+ * symmetrically). Eq. 4 (sigma^2 = 2 kT gamma) is the caller's choice. */
+tdpd_status tdpd_set_pair(tdpd_sys *s, int type_i, int type_j, float a, float gamma, float sigma);
+
+/* Eq. 6 kappa_ij of one species for the type pair (set symmetrically). */
+tdpd_status tdpd_set_kappa(tdpd_sys *s, int type_i, int type_j, int species, float kappa);
+
+/* Source term Q^S of Eq. 5: dC_dst/dt += k C_src, dC_src/dt -= k C_src on
+ * particles whose type bit is set in types. */
+tdpd_status tdpd_set_reaction(tdpd_sys *s, float k, int src, int dst, uint32_t types);
+
+/* Membrane constants for every membrane of the replica (Sec. 2.2). */
+tdpd_status tdpd_set_membrane(tdpd_sys *s, const tdpd_membrane *m);
+
+/* Append n free particles (host arrays; conc may be NULL for zeros). */
+tdpd_status tdpd_add_particles(tdpd_sys *s, int n, const float *pos, const float *vel,
+                               const float *conc, const int32_t *type);
+
+/* Append one membrane: nv vertices (host pos/vel/conc, all of `type`) and
+ * ntri triangles (int32[ntri*3], counter-clockwise seen from outside) of a
+ * closed genus-0 surface (checked: V - E + F = 2, each edge in two opposite
+ * triangles). rest_pos (may be NULL = pos) fixes l0, A0_j, A0, V0. Writes the
+ * membrane's index to *rbc_index if not NULL. At most 1024 vertices. */
+tdpd_status tdpd_add_rbc(tdpd_sys *s, int nv, const float *pos, const float *vel,
+                         const float *conc, int type, int ntri, const int32_t *tri,
+                         const float *rest_pos, int *rbc_index);
+
+/* New handle advancing the given replicas together, every phase of a step
+ * launched once for all of them (batched ensemble). Copies each replica's
+ * description and current state; the inputs stay valid and independent. */
+tdpd_status tdpd_batch_create(tdpd_sys **out, tdpd_sys *const *replicas, int n);
+
+/* CUDA stream (cudaStream_t) on which later work is enqueued; NULL selects
+ * the library's own stream. */
+tdpd_status tdpd_set_stream(tdpd_sys *s, void *cuda_stream);
+
+/* Upload, bin and compute the forces F(0), Q(0) of the loaded state. Called
+ * implicitly by the first step or read; afterwards no particles can be added. */
+tdpd_status tdpd_commit(tdpd_sys *s);
+
+/* --------------------------------------------------------------- advance */
+
+/* Advance every replica by n steps (n >= 0): per step a cell-list binning and
+ * sort, the membrane forces, the pair force + flux and the velocity-Verlet
+ * update, all on the device and replayed from a captured CUDA graph. */
+tdpd_status tdpd_step(tdpd_sys *s, int n);
+
+/* One step (as tdpd_step(s, 1)) from a graph that also records CUDA events
+ * around each of its kernels on the same stream; waits for it and writes the
+ * duration in milliseconds of each kernel, in launch order, to kernel_ms
+ * (at most max_kernels values; *n_kernels receives the count). Names of the
+ * kernels come from tdpd_kernel_name. */
+tdpd_status tdpd_step_timed(tdpd_sys *s, float *kernel_ms, int max_kernels, int *n_kernels);
+const char *tdpd_kernel_name(const tdpd_sys *s, int k);
+
+/* Wait for enqueued work; returns TDPD_ENONFINITE if any replica reported a
+ * non-finite value since the last call (see tdpd_replica_status). */
+tdpd_status tdpd_sync(tdpd_sys *s);
+
+/* Replace the state of replica r (host arrays in load order) and recompute
+ * F, Q at the current step. conc may be NULL to keep the concentrations. */
+tdpd_status tdpd_set_state(tdpd_sys *s, int replica, const float *pos, const float *vel,
+                           const float *conc);
+
+/* ------------------------------------------------------------------ read */
+
+tdpd_status tdpd_read_state(tdpd_sys *s, int replica, float *pos, float *vel, float *conc);
+/* Total force (pair + membrane + body force) and flux (pair + source) of the
+ * current step, the values the next update uses. */
+tdpd_status tdpd_read_forces(tdpd_sys *s, int replica, float *force, float *flux);
+tdpd_status tdpd_read_observables(tdpd_sys *s, int replica, tdpd_obs *out);
+/* Area and volume (FP64, compensated sums) of each membrane of the replica at
+ * the current step, as used by the constraint forces (Eq. 14-15). */
+tdpd_status tdpd_read_rbc(tdpd_sys *s, int replica, double *area, double *volume);
+/* Per-replica status words (TDPD_OK or TDPD_ENONFINITE), int32[n_replicas]. */
+tdpd_status tdpd_replica_status(tdpd_sys *s, int32_t *status);
+
+int tdpd_num_replicas(const tdpd_sys *s);
+int tdpd_num_particles(const tdpd_sys *s, int replica);
+int64_t tdpd_current_step(const tdpd_sys *s);
+/* Kernel launches one tdpd_step(s, 1) enqueues (after commit). */
+int tdpd_launches_per_step(const tdpd_sys *s);
+
+const char *tdpd_last_error(const tdpd_sys *s);
+void tdpd_destroy(tdpd_sys *s);
+
+/* ----------------------------------------------------------- parity hook */
+
+/* The device pairwise random numbers (Sec. 3.1): for each k the TEA output
+ * bits[2k..2k+1] for the pair (i[k], j[k]) at step[k], stream[k], and the two
+ * standard normals normal[2k..2k+1] the force kernels draw from them.
+ * Host arrays; runs on the current device and synchronises. */
+tdpd_status tdpd_debug_rng(uint64_t seed, int n, const uint32_t *i, const uint32_t *j,
+                           const uint32_t *step, const uint32_t *stream,
+                           uint32_t *bits, float *normal);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDPD_H */

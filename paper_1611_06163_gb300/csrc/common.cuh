@@ -1,0 +1,210 @@
+// Device data layout and small device helpers shared by the tDPD kernels.
+//
+// Storage (all replicas concatenated, replica-major, cell-sorted):
+//   pos  float4[N]  x, y, z, w = bits(id | type << 24)      predicted r_{k+1}
+//   vt   float4[N]  predicted velocity v~, w = bits(body)   (-1: free particle)
+//   vel  float4[N]  velocity v_k, w = bits(replica)
+//   frc  float4[N]  force F_k (pair + membrane + body force)
+//   C, Ct, Q        float[N * NS] concentration, predicted concentration, flux
+// Two copies of every array alternate between steps (sorted gather A -> B).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tdpd.h"
+
+namespace tdpd {
+
+constexpr int MAXT = TDPD_MAX_TYPES;
+constexpr int MAXS = TDPD_MAX_SPECIES;
+constexpr uint32_t ID_MASK = 0x00FFFFFFu;
+
+// Per-replica constants, read through the read-only path.
+struct RepParams {
+    float L[3];
+    float cell_scale[3];     // cells per unit length (nc / L)
+    int nc[3];
+    int periodic[3];
+    int cell_base, n_cells;  // global cell index range of the replica
+    int pbase, n;            // slot (and load-order) range of the replica
+    float wall_lo, wall_hi;
+    uint32_t seed_lo, seed_hi;
+    uint32_t step0;          // RNG step offset of the replica
+    int ntypes, ns;
+    float dt, hdt, hdt2, ldt, inv_sqrt_dt;
+    float rc2, inv_rc, rcc2, inv_rcc, rcut2;
+    float sR;                // exponent of w_R: s_f / 2
+    float s_c;
+    int sR_is1, sc_is2;      // integer fast paths
+    float a[MAXT * MAXT], gamma[MAXT * MAXT], sigma[MAXT * MAXT];
+    float kappa[MAXT * MAXT * MAXS];
+    float fbody[3];
+    uint32_t frozen_mask, react_mask;
+    float k_react;
+    int r_src, r_dst;
+    int exclude_same_body;
+    // membrane constants
+    float m_kT, m_p, m_x0, m_m, m_kg, m_kl, m_kv, m_kb, m_cos0, m_sin0, m_gT, m_gC;
+    float m_wlc0;            // kT/p
+    float m_rand_T, m_rand_C;  // sqrt(2kT/dt) sqrt(2 gT), sqrt(2kT/dt) sqrt(3gC-gT)/3
+};
+
+// One membrane.
+struct RbcDev {
+    int gbase;      // load-order (global) index of vertex 0
+    int rep;        // replica
+    int topo;       // topology index
+    int nv, ntri, ne;
+    int a0j_off;    // offset of per-triangle rest areas
+    int bond_off;   // offset of per-edge (l_m, k_p)
+    double A0, V0;
+};
+
+// One closed triangulation (shared by every membrane with the same mesh).
+struct TopoDev {
+    int nv, ntri, ne;
+    int tri_off;    // int[ntri*3]
+    int ring_off;   // int[nv+1] CSR offsets into the ring arrays (absolute)
+    int max_deg;
+};
+
+// Ring (one-ring fan) entry of a vertex v, counter-clockwise seen from
+// outside: triangles (v, nb[l], nb[l+1]) are the mesh triangles around v.
+struct RingEntry {
+    int nb;       // neighbour vertex nb[l]
+    int edge;     // edge index of (v, nb[l])
+    int tri;      // triangle index of (v, nb[l], nb[l+1])
+    int across;   // vertex opposite v across the edge (nb[l], nb[l+1])
+};
+
+__device__ __forceinline__ int wbits(float w) { return __float_as_int(w); }
+__device__ __forceinline__ float bitsw(int b) { return __int_as_float(b); }
+
+// ---------------------------------------------------------------- RNG
+// TEA (Wheeler & Needham 1994), 8 rounds, 64-bit block = the unordered pair
+// of ids, 128-bit key = (seed, step, stream).
+__device__ __forceinline__ uint2 tea8(uint32_t y, uint32_t z, uint32_t k0, uint32_t k1,
+                                      uint32_t k2, uint32_t k3)
+{
+    uint32_t sum = 0u;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        sum += 0x9E3779B9u;
+        y += ((z << 4) + k0) ^ (z + sum) ^ ((z >> 5) + k1);
+        z += ((y << 4) + k2) ^ (y + sum) ^ ((y >> 5) + k3);
+    }
+    return make_uint2(y, z);
+}
+
+__device__ __forceinline__ uint2 pair_bits(uint32_t i, uint32_t j, uint32_t seed_lo,
+                                           uint32_t seed_hi, uint32_t step, uint32_t stream)
+{
+    uint32_t lo = min(i, j), hi = max(i, j);
+    return tea8(lo, hi, seed_lo, seed_hi, step, stream);
+}
+
+// Uniform in (0, 1) from the top 23 bits, centred in its bin: exact in fp32.
+__device__ __forceinline__ float u23(uint32_t b)
+{
+    return __fmaf_rn((float)(b >> 9), 0x1p-23f, 0x1p-24f);
+}
+
+// Box-Muller: (r cos(2 pi u2), r sin(2 pi u2)), r = sqrt(-2 ln u1). The angle
+// is taken in [-pi, pi) as 2 pi (u2 - 1/2), where the fast sine/cosine are
+// accurate, and the half turn is undone by the sign.
+__device__ __forceinline__ float2 normal2(uint2 b)
+{
+    float u1 = u23(b.x), u2 = u23(b.y);
+    float rad = sqrtf(-2.0f * __logf(u1));
+    float s, c;
+    __sincosf(6.28318530717958648f * (u2 - 0.5f), &s, &c);
+    return make_float2(-rad * c, -rad * s);
+}
+
+__device__ __forceinline__ float normal_cos(uint2 b)
+{
+    float u1 = u23(b.x), u2 = u23(b.y);
+    float rad = sqrtf(-2.0f * __logf(u1));
+    return -rad * __cosf(6.28318530717958648f * (u2 - 0.5f));
+}
+
+// ---------------------------------------------------------- geometry
+__device__ __forceinline__ int cell_coord(float x, float scale, int n)
+{
+    int c = __float2int_rd(__fmul_rn(x, scale));
+    return min(max(c, 0), n - 1);
+}
+
+__device__ __forceinline__ int cell_of(const RepParams &P, float x, float y, float z)
+{
+    int cx = cell_coord(x, P.cell_scale[0], P.nc[0]);
+    int cy = cell_coord(y, P.cell_scale[1], P.nc[1]);
+    int cz = cell_coord(z, P.cell_scale[2], P.nc[2]);
+    return P.cell_base + (cz * P.nc[1] + cy) * P.nc[0] + cx;
+}
+
+// Fold a coordinate back into [0, L) after a move of less than one box.
+__device__ __forceinline__ float wrap_coord(float x, float L)
+{
+    if (x < 0.0f) x = __fadd_rn(x, L);
+    else if (x >= L) x = __fsub_rn(x, L);
+    if (!(x >= 0.0f && x < L)) {         // far jump, rounding onto L, or NaN
+        x = __fsub_rn(x, __fmul_rn(L, floorf(__fdiv_rn(x, L))));
+        if (!(x >= 0.0f && x < L)) x = 0.0f;
+    }
+    return x;
+}
+
+// Position predictor r_{k+1} = r_k + dt v_k + dt^2/2 F_k with periodic wrap
+// and bounce-back at the z walls. Explicit rounding keeps the result
+// bit-identical wherever it is recomputed. flip: velocity must be reversed.
+__device__ __forceinline__ float3 predict_pos(const RepParams &P, float4 p, float4 v, float4 f,
+                                              bool &flip)
+{
+    float r[3] = {__fmaf_rn(P.hdt2, f.x, __fmaf_rn(P.dt, v.x, p.x)),
+                  __fmaf_rn(P.hdt2, f.y, __fmaf_rn(P.dt, v.y, p.y)),
+                  __fmaf_rn(P.hdt2, f.z, __fmaf_rn(P.dt, v.z, p.z))};
+    flip = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (P.periodic[c]) {
+            r[c] = wrap_coord(r[c], P.L[c]);
+        } else {
+            if (r[c] < P.wall_lo) { r[c] = __fsub_rn(2.0f * P.wall_lo, r[c]); flip = true; }
+            else if (r[c] > P.wall_hi) { r[c] = __fsub_rn(2.0f * P.wall_hi, r[c]); flip = true; }
+            if (!(r[c] >= 0.0f && r[c] < P.L[c])) r[c] = fminf(fmaxf(r[c], 0.0f), P.L[c] * 0.99999994f);
+        }
+    }
+    return make_float3(r[0], r[1], r[2]);
+}
+
+__device__ __forceinline__ float min_image(float d, float L, int periodic)
+{
+    if (periodic) {
+        if (d > 0.5f * L) d -= L;
+        else if (d < -0.5f * L) d += L;
+    }
+    return d;
+}
+
+// ---------------------------------------------------- FP64 compensated sum
+struct KSum {
+    double s, c;
+    __device__ __forceinline__ void add(double x)
+    {
+        double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return s + c; }
+};
+
+__device__ __forceinline__ void ksum_merge(KSum &a, const KSum &b)
+{
+    a.add(b.s);
+    a.c += b.c;
+}
+
+}  // namespace tdpd

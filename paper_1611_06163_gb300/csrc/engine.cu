@@ -1,0 +1,1076 @@
+// Host runtime behind the C ABI of tdpd.h: replica descriptions, device
+// layout, membrane topology tables, the captured per-step CUDA graphs, and
+// the read-back paths.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "launch.h"
+
+using namespace tdpd;
+
+namespace {
+
+constexpr int OBS_K = 5 + MAXS;
+constexpr int GRAPH_LONG = 16;   // steps per long graph (even: keeps the buffer parity)
+
+struct HostRbc {
+    int nv = 0, ntri = 0, type = 1;
+    std::vector<int32_t> tri;
+    std::vector<float> rest;   // nv*3
+};
+
+struct HostRep {
+    tdpd_config cfg{};
+    float a[MAXT * MAXT] = {}, gamma[MAXT * MAXT] = {}, sigma[MAXT * MAXT] = {};
+    float kappa[MAXT * MAXT * MAXS] = {};
+    float k_react = 0.f;
+    int r_src = 0, r_dst = 0;
+    uint32_t r_types = 0;
+    tdpd_membrane mem{};
+    bool has_mem = false;
+    std::vector<float> pos, vel, conc;     // load order
+    std::vector<int32_t> type, body;       // body: local membrane index or -1
+    std::vector<HostRbc> rbcs;
+    int n_free = 0;
+    int64_t step = 0;
+    int nc[3] = {0, 0, 0};
+};
+
+struct Topo {
+    int nv, ntri, ne;
+    std::vector<int32_t> tri;
+    std::vector<int> ring_off;         // nv+1, relative
+    std::vector<RingEntry> ring;
+    std::map<std::pair<int, int>, int> edge_id;
+    std::vector<std::pair<int, int>> edges;
+};
+
+}  // namespace
+
+struct tdpd_sys {
+    std::vector<HostRep> reps;
+    bool committed = false;
+    std::string err;
+    cudaStream_t user = nullptr, own = nullptr, cap = nullptr;
+    int N = 0, NC = 0, ns = 0, n_rbc = 0, max_nv = 0;
+    int parity = 0;
+    int64_t step = 0;
+    Buffers buf[2] = {};
+    std::vector<void *> allocs;
+    float4 *fext = nullptr;
+    int *inv = nullptr, *count = nullptr, *cell_start = nullptr;
+    int2 *cellrank = nullptr, *keys = nullptr;
+    uint32_t *errw = nullptr, *step_ctr = nullptr;
+    RepParams *d_reps = nullptr;
+    RbcDev *d_rbcs = nullptr;
+    TopoDev *d_topos = nullptr;
+    int *d_tri = nullptr, *d_ring_off = nullptr;
+    RingEntry *d_ring = nullptr;
+    float *d_a0j = nullptr;
+    float2 *d_bond = nullptr;
+    float4 *d_ref[2] = {nullptr, nullptr};
+    double2 *d_av = nullptr;
+    double *d_obs = nullptr;
+    std::vector<int> rep_pbase, rep_rbc0;
+    std::vector<RbcDev> h_rbcs;
+    std::vector<Topo> topos;
+    std::vector<float4> h_ref;
+    cudaGraphExec_t g1[2] = {nullptr, nullptr}, glong[2] = {nullptr, nullptr}, gtimed[2] = {nullptr, nullptr};
+    cudaEvent_t ev[8] = {};
+    int n_ev = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+tdpd_status fail(tdpd_sys *s, tdpd_status code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail(s, TDPD_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                         \
+    } while (0)
+
+cudaStream_t exec_stream(tdpd_sys *s) { return s->user ? s->user : s->own; }
+
+template <class T>
+tdpd_status dalloc(tdpd_sys *s, T **p, size_t n)
+{
+    void *q = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+    if (e != cudaSuccess) return fail(s, TDPD_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    s->allocs.push_back(q);
+    *p = (T *)q;
+    return TDPD_OK;
+}
+
+template <class T>
+tdpd_status upload(tdpd_sys *s, T *dst, const T *src, size_t n)
+{
+    if (n == 0) return TDPD_OK;
+    CU(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, exec_stream(s)));
+    return TDPD_OK;
+}
+
+double min_image_d(double d, double L, int periodic)
+{
+    if (!periodic) return d;
+    return d - L * std::floor(d / L + 0.5);
+}
+
+// Build the one-ring tables of a closed oriented triangulation.
+tdpd_status build_topo(tdpd_sys *s, int nv, int ntri, const int32_t *tri, Topo &T)
+{
+    T.nv = nv;
+    T.ntri = ntri;
+    T.tri.assign(tri, tri + 3 * ntri);
+    std::map<std::pair<int, int>, int> opp;   // directed edge -> third vertex
+    std::map<std::pair<int, int>, int> dtri;  // directed edge -> triangle
+    for (int t = 0; t < ntri; ++t) {
+        for (int k = 0; k < 3; ++k) {
+            int a = tri[3 * t + k], b = tri[3 * t + (k + 1) % 3], c = tri[3 * t + (k + 2) % 3];
+            if (a < 0 || a >= nv || a == b || b == c || a == c)
+                return fail(s, TDPD_EINVAL, "triangle %d has a bad vertex index", t);
+            auto key = std::make_pair(a, b);
+            if (opp.count(key)) return fail(s, TDPD_EINVAL, "directed edge (%d,%d) occurs twice: mesh not consistently oriented", a, b);
+            opp[key] = c;
+            dtri[key] = t;
+        }
+    }
+    for (auto &kv : opp) {
+        auto rev = std::make_pair(kv.first.second, kv.first.first);
+        if (!opp.count(rev)) return fail(s, TDPD_EINVAL, "edge (%d,%d) has one triangle: mesh not closed", kv.first.first, kv.first.second);
+        if (kv.first.first < kv.first.second) {
+            T.edge_id[kv.first] = (int)T.edges.size();
+            T.edges.push_back(kv.first);
+        }
+    }
+    T.ne = (int)T.edges.size();
+    if (nv - T.ne + ntri != 2) return fail(s, TDPD_EINVAL, "V - E + F = %d, not a closed genus-0 surface", nv - T.ne + ntri);
+    auto eid = [&](int a, int b) { return T.edge_id[std::make_pair(std::min(a, b), std::max(a, b))]; };
+    // fan of each vertex: triangles (v, a, b) chain a -> b
+    std::vector<std::vector<std::pair<int, int>>> fan(nv);   // (a, triangle) keyed by a, next b
+    std::vector<std::map<int, int>> next(nv), ftri(nv);
+    for (int t = 0; t < ntri; ++t)
+        for (int k = 0; k < 3; ++k) {
+            int v = tri[3 * t + k], a = tri[3 * t + (k + 1) % 3], b = tri[3 * t + (k + 2) % 3];
+            next[v][a] = b;
+            ftri[v][a] = t;
+        }
+    T.ring_off.assign(nv + 1, 0);
+    for (int v = 0; v < nv; ++v) {
+        int deg = (int)next[v].size();
+        if (deg < 3) return fail(s, TDPD_EINVAL, "vertex %d has degree %d", v, deg);
+        T.ring_off[v] = (int)T.ring.size();
+        int a0 = next[v].begin()->first, a = a0;
+        for (int l = 0; l < deg; ++l) {
+            auto it = next[v].find(a);
+            if (it == next[v].end()) return fail(s, TDPD_EINVAL, "vertex %d: open fan", v);
+            int b = it->second;
+            RingEntry E;
+            E.nb = a;
+            E.edge = eid(v, a);
+            E.tri = ftri[v][a];
+            E.across = opp[std::make_pair(b, a)];
+            T.ring.push_back(E);
+            a = b;
+        }
+        if (a != a0) return fail(s, TDPD_EINVAL, "vertex %d: fan is not a single cycle", v);
+    }
+    T.ring_off[nv] = (int)T.ring.size();
+    return TDPD_OK;
+}
+
+// Unwrap a membrane (nv*3 floats) by walking edges with the minimum image.
+void unwrap(const HostRep &R, const Topo &T, const float *p, std::vector<double> &x)
+{
+    const int nv = T.nv;
+    x.assign(3 * (size_t)nv, 0.0);
+    std::vector<char> done(nv, 0);
+    std::vector<int> stack{0};
+    for (int c = 0; c < 3; ++c) x[c] = p[c];
+    done[0] = 1;
+    while (!stack.empty()) {
+        int v = stack.back();
+        stack.pop_back();
+        for (int k = T.ring_off[v]; k < T.ring_off[v + 1]; ++k) {
+            int u = T.ring[k].nb;
+            if (done[u]) continue;
+            for (int c = 0; c < 3; ++c)
+                x[3 * u + c] = x[3 * v + c] + min_image_d((double)p[3 * u + c] - p[3 * v + c], R.cfg.L[c], R.cfg.periodic[c]);
+            done[u] = 1;
+            stack.push_back(u);
+        }
+    }
+}
+
+RepParams make_params(const HostRep &R, int cell_base, int pbase, int n)
+{
+    RepParams P;
+    std::memset(&P, 0, sizeof P);
+    const tdpd_config &c = R.cfg;
+    for (int k = 0; k < 3; ++k) {
+        P.L[k] = c.L[k];
+        P.nc[k] = R.nc[k];
+        P.cell_scale[k] = (float)((double)R.nc[k] / (double)c.L[k]);
+        P.periodic[k] = c.periodic[k];
+        P.fbody[k] = c.body_force[k];
+    }
+    P.cell_base = cell_base;
+    P.n_cells = R.nc[0] * R.nc[1] * R.nc[2];
+    P.pbase = pbase;
+    P.n = n;
+    P.wall_lo = c.wall_lo;
+    P.wall_hi = c.wall_hi;
+    P.seed_lo = (uint32_t)(c.seed & 0xffffffffu);
+    P.seed_hi = (uint32_t)(c.seed >> 32);
+    P.step0 = (uint32_t)R.step;
+    P.ntypes = c.n_types;
+    P.ns = c.n_species;
+    P.dt = c.dt;
+    P.hdt = (float)(0.5 * c.dt);
+    P.hdt2 = (float)(0.5 * (double)c.dt * c.dt);
+    P.ldt = (float)((double)c.lambda * c.dt);
+    P.inv_sqrt_dt = (float)(1.0 / std::sqrt((double)c.dt));
+    P.rc2 = c.rc * c.rc;
+    P.inv_rc = (float)(1.0 / c.rc);
+    P.rcc2 = c.rcc * c.rcc;
+    P.inv_rcc = c.rcc > 0 ? (float)(1.0 / c.rcc) : 0.f;
+    const float rcut = std::max(c.rc, c.rcc);
+    P.rcut2 = rcut * rcut;
+    P.sR = 0.5f * c.s_f;
+    P.s_c = c.s_c;
+    P.sR_is1 = (P.sR == 1.0f);
+    P.sc_is2 = (c.s_c == 2.0f);
+    std::memcpy(P.a, R.a, sizeof P.a);
+    std::memcpy(P.gamma, R.gamma, sizeof P.gamma);
+    std::memcpy(P.sigma, R.sigma, sizeof P.sigma);
+    // kappa packed as [ti*T + tj][ns] for the replica's own T and ns
+    const int T = c.n_types, S = c.n_species;
+    for (int i = 0; i < T; ++i)
+        for (int j = 0; j < T; ++j)
+            for (int k = 0; k < S; ++k) P.kappa[(i * T + j) * S + k] = R.kappa[(i * MAXT + j) * MAXS + k];
+    for (int i = 0; i < T; ++i)
+        for (int j = 0; j < T; ++j) {
+            P.a[i * T + j] = R.a[i * MAXT + j];
+            P.gamma[i * T + j] = R.gamma[i * MAXT + j];
+            P.sigma[i * T + j] = R.sigma[i * MAXT + j];
+        }
+    P.frozen_mask = c.frozen_types;
+    P.react_mask = R.r_types;
+    P.k_react = R.k_react;
+    P.r_src = R.r_src;
+    P.r_dst = R.r_dst;
+    P.exclude_same_body = c.exclude_same_body;
+    const tdpd_membrane &m = R.mem;
+    P.m_kT = m.kT; P.m_p = m.p; P.m_x0 = m.x0; P.m_m = m.m;
+    P.m_kg = m.kg; P.m_kl = m.kl; P.m_kv = m.kv; P.m_kb = m.kb;
+    P.m_cos0 = (float)std::cos((double)m.theta0);
+    P.m_sin0 = (float)std::sin((double)m.theta0);
+    P.m_gT = m.gammaT; P.m_gC = m.gammaC;
+    P.m_wlc0 = m.p > 0 ? (float)((double)m.kT / m.p) : 0.f;
+    const double s0 = std::sqrt(2.0 * (double)m.kT / c.dt);
+    P.m_rand_T = (float)(s0 * std::sqrt(2.0 * (double)m.gammaT));
+    P.m_rand_C = (float)(s0 * std::sqrt(std::max(0.0, 3.0 * (double)m.gammaC - m.gammaT)) / 3.0);
+    return P;
+}
+
+tdpd_status free_device(tdpd_sys *s)
+{
+    for (int p = 0; p < 2; ++p) {
+        if (s->g1[p]) cudaGraphExecDestroy(s->g1[p]);
+        if (s->glong[p]) cudaGraphExecDestroy(s->glong[p]);
+        if (s->gtimed[p]) cudaGraphExecDestroy(s->gtimed[p]);
+        s->g1[p] = s->glong[p] = s->gtimed[p] = nullptr;
+    }
+    for (int k = 0; k < s->n_ev; ++k) cudaEventDestroy(s->ev[k]);
+    s->n_ev = 0;
+    for (void *p : s->allocs) cudaFree(p);
+    s->allocs.clear();
+    return TDPD_OK;
+}
+
+const char *const KERNEL_NAMES[] = {"scan", "scatter_keys", "rank_gather", "mem_gather", "mem_forces", "pair"};
+
+MemArgs mem_args(tdpd_sys *s, const Buffers &b, int ref_in)
+{
+    MemArgs m{};
+    m.pos = b.pos; m.vt = b.vt; m.inv = s->inv; m.reps = s->d_reps; m.rbcs = s->d_rbcs;
+    m.topos = s->d_topos; m.tri = s->d_tri; m.ring_off = s->d_ring_off; m.ring = s->d_ring;
+    m.a0j = s->d_a0j; m.bond = s->d_bond; m.ref_in = s->d_ref[ref_in]; m.ref_out = s->d_ref[1 - ref_in];
+    m.av = s->d_av; m.fext = s->fext; m.step_ctr = s->step_ctr; m.n_rbc = s->n_rbc; m.max_nv = s->max_nv;
+    return m;
+}
+
+PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate)
+{
+    PairArgs a{};
+    a.b = b; a.fext = s->fext; a.reps = s->d_reps; a.cell_start = s->cell_start; a.count = s->count;
+    a.cellrank = s->cellrank; a.err = s->errw; a.step_ctr = s->step_ctr; a.n = s->N; a.ns = s->ns;
+    a.integrate = integrate;
+    return a;
+}
+
+// Kernel kinds one step launches, in order (indices into KERNEL_NAMES).
+std::vector<int> step_kernels(const tdpd_sys *s)
+{
+    std::vector<int> k{0, 1, 2};
+    if (s->n_rbc) { k.push_back(3); k.push_back(4); }
+    k.push_back(5);
+    return k;
+}
+
+// Enqueue one step reading buffer p and leaving the state in buffer 1-p. With
+// ev (one event per kernel plus one), event-record nodes bracket each kernel.
+void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr)
+{
+    const Buffers &cur = s->buf[p], &nxt = s->buf[1 - p];
+    int e = 0;
+    auto mark = [&]() { if (ev) cudaEventRecordWithFlags(ev[e++], st, cudaEventRecordExternal); };
+    mark();
+    launch_scan(s->count, s->cell_start, s->NC, s->step_ctr, 1, st);
+    mark();
+    launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st);
+    mark();
+    launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st);
+    mark();
+    if (s->n_rbc) {
+        const MemArgs m = mem_args(s, nxt, 1 - p);
+        launch_mem_gather(m, st);
+        mark();
+        launch_mem_forces(m, st);
+        mark();
+    }
+    launch_pair(pair_args(s, nxt, 1), st);
+    mark();
+}
+
+// Upload every replica's load-order state into buffer 0, bin and sort it into
+// buffer 1 and compute the forces of the current step there.
+tdpd_status init_state(tdpd_sys *s)
+{
+    cudaStream_t st = exec_stream(s);
+    const int N = s->N, ns = s->ns;
+    std::vector<float4> pos(N), vel(N), vt(N);
+    std::vector<float> C((size_t)N * ns);
+    int rb0 = 0;
+    for (size_t r = 0; r < s->reps.size(); ++r) {
+        const HostRep &R = s->reps[r];
+        const int base = s->rep_pbase[r];
+        const int n = (int)R.type.size();
+        for (int i = 0; i < n; ++i) {
+            const int g = base + i;
+            const uint32_t w = (uint32_t)i | ((uint32_t)R.type[i] << 24);
+            pos[g] = make_float4(R.pos[3 * i], R.pos[3 * i + 1], R.pos[3 * i + 2], 0.f);
+            std::memcpy(&pos[g].w, &w, 4);
+            vel[g] = make_float4(R.vel[3 * i], R.vel[3 * i + 1], R.vel[3 * i + 2], 0.f);
+            int rr = (int)r;
+            std::memcpy(&vel[g].w, &rr, 4);
+            vt[g] = vel[g];
+            int body = R.body[i] >= 0 ? rb0 + R.body[i] : -1;
+            std::memcpy(&vt[g].w, &body, 4);
+            for (int k = 0; k < ns; ++k) C[(size_t)g * ns + k] = R.conc[(size_t)i * ns + k];
+        }
+        rb0 += (int)R.rbcs.size();
+    }
+    // membrane reference points: centroid of the unwrapped vertices
+    s->h_ref.assign(s->n_rbc, make_float4(0, 0, 0, 0));
+    for (int b = 0; b < s->n_rbc; ++b) {
+        const RbcDev &D = s->h_rbcs[b];
+        const HostRep &R = s->reps[D.rep];
+        const int first = D.gbase - s->rep_pbase[D.rep];
+        std::vector<double> x;
+        unwrap(R, s->topos[D.topo], &R.pos[3 * (size_t)first], x);
+        double c[3] = {0, 0, 0};
+        for (int v = 0; v < D.nv; ++v)
+            for (int k = 0; k < 3; ++k) c[k] += x[3 * v + k];
+        float cf[3];
+        for (int k = 0; k < 3; ++k) {
+            double y = c[k] / D.nv;
+            if (R.cfg.periodic[k]) y -= R.cfg.L[k] * std::floor(y / R.cfg.L[k]);
+            cf[k] = (float)y;
+        }
+        s->h_ref[b] = make_float4(cf[0], cf[1], cf[2], 0.f);
+    }
+    tdpd_status rc;
+    if ((rc = upload(s, s->buf[0].pos, pos.data(), N))) return rc;
+    if ((rc = upload(s, s->buf[0].vel, vel.data(), N))) return rc;
+    if ((rc = upload(s, s->buf[0].vt, vt.data(), N))) return rc;
+    if ((rc = upload(s, s->buf[0].C, C.data(), (size_t)N * ns))) return rc;
+    if ((rc = upload(s, s->buf[0].Ct, C.data(), (size_t)N * ns))) return rc;
+    if (s->n_rbc && (rc = upload(s, s->d_ref[1], s->h_ref.data(), s->n_rbc))) return rc;
+    CU(cudaMemsetAsync(s->buf[0].frc, 0, sizeof(float4) * N, st));
+    CU(cudaMemsetAsync(s->buf[0].Q, 0, sizeof(float) * (size_t)N * ns, st));
+    CU(cudaMemsetAsync(s->count, 0, sizeof(int) * s->NC, st));
+    CU(cudaMemsetAsync(s->errw, 0, sizeof(uint32_t) * s->reps.size(), st));
+    CU(cudaMemsetAsync(s->fext, 0, sizeof(float4) * N, st));
+    const uint32_t step32 = (uint32_t)s->step;
+    if ((rc = upload(s, s->step_ctr, &step32, 1))) return rc;
+    launch_bin_init(s->buf[0], s->d_reps, N, s->count, s->cellrank, st);
+    launch_scan(s->count, s->cell_start, s->NC, s->step_ctr, 0, st);
+    launch_scatter_keys(s->buf[0], s->cellrank, s->cell_start, s->keys, N, st);
+    launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0, st);
+    if (s->n_rbc) {
+        const MemArgs m = mem_args(s, s->buf[1], 1);
+        launch_mem_gather(m, st);
+        launch_mem_forces(m, st);
+    }
+    launch_pair(pair_args(s, s->buf[1], 0), st);
+    CU(cudaGetLastError());
+    s->parity = 1;
+    return TDPD_OK;
+}
+
+tdpd_status capture(tdpd_sys *s, int p, int len, cudaGraphExec_t *out, cudaEvent_t *ev = nullptr)
+{
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < len; ++k) enqueue_step(s, (p + k) & 1, s->cap, ev);
+    cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+    if (e != cudaSuccess) return fail(s, TDPD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(s, TDPD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return TDPD_OK;
+}
+
+tdpd_status commit(tdpd_sys *s)
+{
+    if (s->committed) return TDPD_OK;
+    if (s->reps.empty()) return fail(s, TDPD_ESTATE, "no replicas");
+    s->ns = s->reps[0].cfg.n_species;
+    int N = 0, NC = 0;
+    s->rep_pbase.clear();
+    s->rep_rbc0.clear();
+    s->h_rbcs.clear();
+    s->topos.clear();
+    std::vector<RepParams> P;
+    std::vector<float> a0j;
+    std::vector<float2> bond;
+    int max_nv = 0;
+    for (size_t r = 0; r < s->reps.size(); ++r) {
+        HostRep &R = s->reps[r];
+        if (R.cfg.n_species != s->ns) return fail(s, TDPD_EINVAL, "replica %zu: all replicas need the same number of species", r);
+        const int n = (int)R.type.size();
+        if (n > TDPD_MAX_IDS) return fail(s, TDPD_EOVERFLOW, "replica %zu: %d particles exceed %d", r, n, TDPD_MAX_IDS);
+        const float rcut = std::max(R.cfg.rc, R.cfg.rcc);
+        for (int c = 0; c < 3; ++c) {
+            R.nc[c] = (int)std::floor((double)R.cfg.L[c] / ((double)rcut * 1.0001));
+            if (R.nc[c] < 3)
+                return fail(s, TDPD_EINVAL, "replica %zu: box edge %g holds fewer than 3 cells of %g", r, R.cfg.L[c], rcut);
+        }
+        const long ncells = (long)R.nc[0] * R.nc[1] * R.nc[2];
+        if ((long)NC + ncells > (1L << 30)) return fail(s, TDPD_EOVERFLOW, "too many cells");
+        if (!R.rbcs.empty() && !R.has_mem) return fail(s, TDPD_ESTATE, "replica %zu has membranes but no tdpd_set_membrane", r);
+        s->rep_pbase.push_back(N);
+        s->rep_rbc0.push_back((int)s->h_rbcs.size());
+        P.push_back(make_params(R, NC, N, n));
+        // membranes
+        int first = R.n_free;
+        for (size_t b = 0; b < R.rbcs.size(); ++b) {
+            const HostRbc &H = R.rbcs[b];
+            int ti = -1;
+            for (size_t t = 0; t < s->topos.size(); ++t)
+                if (s->topos[t].nv == H.nv && s->topos[t].tri == H.tri) { ti = (int)t; break; }
+            if (ti < 0) {
+                Topo T;
+                tdpd_status rc = build_topo(s, H.nv, H.ntri, H.tri.data(), T);
+                if (rc) return rc;
+                s->topos.push_back(std::move(T));
+                ti = (int)s->topos.size() - 1;
+            }
+            const Topo &T = s->topos[ti];
+            RbcDev D{};
+            D.gbase = N + first;
+            D.rep = (int)r;
+            D.topo = ti;
+            D.nv = H.nv;
+            D.ntri = H.ntri;
+            D.ne = T.ne;
+            D.a0j_off = (int)a0j.size();
+            D.bond_off = (int)bond.size();
+            std::vector<double> x;
+            unwrap(R, T, H.rest.data(), x);
+            double A = 0, V = 0;
+            for (int t = 0; t < H.ntri; ++t) {
+                const double *p0 = &x[3 * H.tri[3 * t]], *p1 = &x[3 * H.tri[3 * t + 1]], *p2 = &x[3 * H.tri[3 * t + 2]];
+                double u[3], w[3], n3[3], c12[3];
+                for (int k = 0; k < 3; ++k) { u[k] = p1[k] - p0[k]; w[k] = p2[k] - p0[k]; }
+                n3[0] = u[1] * w[2] - u[2] * w[1];
+                n3[1] = u[2] * w[0] - u[0] * w[2];
+                n3[2] = u[0] * w[1] - u[1] * w[0];
+                c12[0] = p1[1] * p2[2] - p1[2] * p2[1];
+                c12[1] = p1[2] * p2[0] - p1[0] * p2[2];
+                c12[2] = p1[0] * p2[1] - p1[1] * p2[0];
+                const double At = 0.5 * std::sqrt(n3[0] * n3[0] + n3[1] * n3[1] + n3[2] * n3[2]);
+                a0j.push_back((float)At);
+                A += At;
+                V += (p0[0] * c12[0] + p0[1] * c12[1] + p0[2] * c12[2]) / 6.0;
+            }
+            const tdpd_membrane &m = R.mem;
+            const double x0 = m.x0;
+            const double fw = (double)m.kT / m.p * (0.25 / ((1 - x0) * (1 - x0)) - 0.25 + x0);
+            for (int e = 0; e < T.ne; ++e) {
+                const int i = T.edges[e].first, j = T.edges[e].second;
+                double d2 = 0;
+                for (int k = 0; k < 3; ++k) d2 += (x[3 * i + k] - x[3 * j + k]) * (x[3 * i + k] - x[3 * j + k]);
+                const double l0 = std::sqrt(d2);
+                bond.push_back(make_float2((float)(l0 / x0), (float)(fw * std::pow(l0, (double)m.m))));
+            }
+            D.A0 = A;
+            D.V0 = m.v_ratio > 0 ? (double)m.v_ratio * std::pow(A, 1.5) : V;
+            s->h_rbcs.push_back(D);
+            max_nv = std::max(max_nv, H.nv);
+            first += H.nv;
+        }
+        N += n;
+        NC += (int)ncells;
+    }
+    s->N = N;
+    s->NC = NC;
+    s->n_rbc = (int)s->h_rbcs.size();
+    s->max_nv = max_nv;
+    if (N == 0) return fail(s, TDPD_ESTATE, "no particles loaded");
+
+    // device allocations
+    tdpd_status rc;
+    const int ns = s->ns;
+    for (int p = 0; p < 2; ++p) {
+        Buffers &B = s->buf[p];
+        if ((rc = dalloc(s, &B.pos, N)) || (rc = dalloc(s, &B.vt, N)) || (rc = dalloc(s, &B.vel, N)) ||
+            (rc = dalloc(s, &B.frc, N)) || (rc = dalloc(s, &B.C, (size_t)N * ns)) ||
+            (rc = dalloc(s, &B.Ct, (size_t)N * ns)) || (rc = dalloc(s, &B.Q, (size_t)N * ns)))
+            return rc;
+    }
+    if ((rc = dalloc(s, &s->fext, N)) || (rc = dalloc(s, &s->inv, N)) || (rc = dalloc(s, &s->cellrank, N)) ||
+        (rc = dalloc(s, &s->keys, N)) || (rc = dalloc(s, &s->count, NC)) || (rc = dalloc(s, &s->cell_start, NC + 1)) ||
+        (rc = dalloc(s, &s->errw, s->reps.size())) || (rc = dalloc(s, &s->step_ctr, 1)) ||
+        (rc = dalloc(s, &s->d_reps, P.size())) || (rc = dalloc(s, &s->d_obs, OBS_K * s->reps.size())))
+        return rc;
+    if ((rc = upload(s, s->d_reps, P.data(), P.size()))) return rc;
+    if (s->n_rbc) {
+        std::vector<TopoDev> td;
+        std::vector<int> tri, roff;
+        std::vector<RingEntry> ring;
+        for (const Topo &T : s->topos) {
+            TopoDev D{};
+            D.nv = T.nv; D.ntri = T.ntri; D.ne = T.ne;
+            D.tri_off = (int)tri.size();
+            D.ring_off = (int)roff.size();
+            int mx = 0;
+            for (int v = 0; v < T.nv; ++v) mx = std::max(mx, T.ring_off[v + 1] - T.ring_off[v]);
+            D.max_deg = mx;
+            tri.insert(tri.end(), T.tri.begin(), T.tri.end());
+            const int rbase = (int)ring.size();
+            for (int v = 0; v <= T.nv; ++v) roff.push_back(rbase + T.ring_off[v]);
+            ring.insert(ring.end(), T.ring.begin(), T.ring.end());
+            td.push_back(D);
+        }
+        if ((rc = dalloc(s, &s->d_rbcs, s->n_rbc)) || (rc = dalloc(s, &s->d_topos, td.size())) ||
+            (rc = dalloc(s, &s->d_tri, tri.size())) || (rc = dalloc(s, &s->d_ring_off, roff.size())) ||
+            (rc = dalloc(s, &s->d_ring, ring.size())) || (rc = dalloc(s, &s->d_a0j, a0j.size())) ||
+            (rc = dalloc(s, &s->d_bond, bond.size())) || (rc = dalloc(s, &s->d_ref[0], s->n_rbc)) ||
+            (rc = dalloc(s, &s->d_ref[1], s->n_rbc)) || (rc = dalloc(s, &s->d_av, s->n_rbc)))
+            return rc;
+        if ((rc = upload(s, s->d_rbcs, s->h_rbcs.data(), s->n_rbc)) || (rc = upload(s, s->d_topos, td.data(), td.size())) ||
+            (rc = upload(s, s->d_tri, tri.data(), tri.size())) || (rc = upload(s, s->d_ring_off, roff.data(), roff.size())) ||
+            (rc = upload(s, s->d_ring, ring.data(), ring.size())) || (rc = upload(s, s->d_a0j, a0j.data(), a0j.size())) ||
+            (rc = upload(s, s->d_bond, bond.data(), bond.size())))
+            return rc;
+    }
+    s->step = 0;
+    for (auto &R : s->reps) (void)R;
+    if ((rc = init_state(s))) return rc;
+    const int nk = (int)step_kernels(s).size();
+    for (int k = 0; k <= nk; ++k) CU(cudaEventCreate(&s->ev[k]));
+    s->n_ev = nk + 1;
+    for (int p = 0; p < 2; ++p) {
+        if ((rc = capture(s, p, 1, &s->g1[p]))) return rc;
+        if ((rc = capture(s, p, GRAPH_LONG, &s->glong[p]))) return rc;
+        if ((rc = capture(s, p, 1, &s->gtimed[p], s->ev))) return rc;
+    }
+    CU(cudaStreamSynchronize(exec_stream(s)));
+    s->committed = true;
+    return TDPD_OK;
+}
+
+tdpd_status ensure(tdpd_sys *s)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    return s->committed ? TDPD_OK : commit(s);
+}
+
+HostRep *rep_of(tdpd_sys *s, int r)
+{
+    if (r < 0 || r >= (int)s->reps.size()) return nullptr;
+    return &s->reps[r];
+}
+
+// Download the current sorted state of replica r into load order.
+tdpd_status download(tdpd_sys *s, int r, float *pos, float *vel, float *conc, float *frc, float *flux)
+{
+    cudaStream_t st = exec_stream(s);
+    const HostRep &R = s->reps[r];
+    const int n = (int)R.type.size(), base = s->rep_pbase[r], ns = s->ns;
+    std::vector<int> inv(n);
+    std::vector<float4> a(n), b(n);
+    std::vector<float> c((size_t)n * ns), q((size_t)n * ns);
+    const Buffers &B = s->buf[s->parity];
+    CU(cudaMemcpyAsync(inv.data(), s->inv + base, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+    // the replica's slots are the contiguous range [base, base+n)
+    if (pos) CU(cudaMemcpyAsync(a.data(), B.pos + base, sizeof(float4) * n, cudaMemcpyDeviceToHost, st));
+    if (vel) CU(cudaMemcpyAsync(b.data(), B.vel + base, sizeof(float4) * n, cudaMemcpyDeviceToHost, st));
+    if (conc) CU(cudaMemcpyAsync(c.data(), B.C + (size_t)base * ns, sizeof(float) * n * ns, cudaMemcpyDeviceToHost, st));
+    std::vector<float4> f(frc ? n : 0);
+    if (frc) CU(cudaMemcpyAsync(f.data(), B.frc + base, sizeof(float4) * n, cudaMemcpyDeviceToHost, st));
+    if (flux) CU(cudaMemcpyAsync(q.data(), B.Q + (size_t)base * ns, sizeof(float) * n * ns, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) {
+        const int k = inv[i] - base;
+        if (k < 0 || k >= n) return fail(s, TDPD_ESTATE, "corrupt slot map");
+        if (pos) { pos[3 * i] = a[k].x; pos[3 * i + 1] = a[k].y; pos[3 * i + 2] = a[k].z; }
+        if (vel) { vel[3 * i] = b[k].x; vel[3 * i + 1] = b[k].y; vel[3 * i + 2] = b[k].z; }
+        if (frc) { frc[3 * i] = f[k].x; frc[3 * i + 1] = f[k].y; frc[3 * i + 2] = f[k].z; }
+        for (int sp = 0; sp < ns; ++sp) {
+            if (conc) conc[(size_t)i * ns + sp] = c[(size_t)k * ns + sp];
+            if (flux) flux[(size_t)i * ns + sp] = q[(size_t)k * ns + sp];
+        }
+    }
+    return TDPD_OK;
+}
+
+tdpd_status check_config(tdpd_sys *s, const tdpd_config *c)
+{
+    if (!c) return fail(s, TDPD_EINVAL, "null config");
+    for (int k = 0; k < 3; ++k)
+        if (!(c->L[k] > 0) || !std::isfinite(c->L[k])) return fail(s, TDPD_EINVAL, "box edge %d must be positive", k);
+    if (!c->periodic[0] || !c->periodic[1]) return fail(s, TDPD_EINVAL, "x and y must be periodic (walls only along z)");
+    if (!c->periodic[2] && !(c->wall_lo >= 0 && c->wall_lo < c->wall_hi && c->wall_hi <= c->L[2]))
+        return fail(s, TDPD_EINVAL, "walls need 0 <= wall_lo < wall_hi <= L[2]");
+    if (c->n_types < 1 || c->n_types > MAXT) return fail(s, TDPD_EINVAL, "n_types must be in 1..%d", MAXT);
+    if (c->n_species < 1 || c->n_species > MAXS) return fail(s, TDPD_EINVAL, "n_species must be in 1..%d", MAXS);
+    if (!(c->dt > 0)) return fail(s, TDPD_EINVAL, "dt must be positive");
+    if (!(c->rc > 0) || !(c->rcc >= 0)) return fail(s, TDPD_EINVAL, "cut-offs: rc > 0, rcc >= 0");
+    if (!(c->s_f > 0) || !(c->s_c > 0)) return fail(s, TDPD_EINVAL, "weight exponents must be positive");
+    if (c->frozen_types >> c->n_types) return fail(s, TDPD_EINVAL, "frozen_types names a type >= n_types");
+    return TDPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tdpd_status tdpd_create(tdpd_sys **out, const tdpd_config *cfg)
+{
+    if (!out) return fail(nullptr, TDPD_EINVAL, "null output handle");
+    *out = nullptr;
+    tdpd_status rc = check_config(nullptr, cfg);
+    if (rc) return rc;
+    tdpd_sys *s = new (std::nothrow) tdpd_sys;
+    if (!s) return fail(nullptr, TDPD_ENOMEM, "host allocation failed");
+    s->reps.emplace_back();
+    s->reps[0].cfg = *cfg;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        fail(nullptr, TDPD_ECUDA, "stream creation: %s", cudaGetErrorString(e));
+        delete s;
+        return TDPD_ECUDA;
+    }
+    *out = s;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_pair(tdpd_sys *s, int ti, int tj, float a, float gamma, float sigma)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed) return fail(s, TDPD_ESTATE, "parameters are fixed after commit");
+    HostRep &R = s->reps[0];
+    if (s->reps.size() != 1) return fail(s, TDPD_ESTATE, "set parameters on the replicas before batching");
+    if (ti < 0 || tj < 0 || ti >= R.cfg.n_types || tj >= R.cfg.n_types) return fail(s, TDPD_EINVAL, "type out of range");
+    if (!std::isfinite(a) || !(gamma >= 0) || !(sigma >= 0)) return fail(s, TDPD_EINVAL, "bad pair coefficients");
+    for (int k = 0; k < 2; ++k) {
+        const int i = k ? tj : ti, j = k ? ti : tj;
+        R.a[i * MAXT + j] = a;
+        R.gamma[i * MAXT + j] = gamma;
+        R.sigma[i * MAXT + j] = sigma;
+    }
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_kappa(tdpd_sys *s, int ti, int tj, int sp, float kappa)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed || s->reps.size() != 1) return fail(s, TDPD_ESTATE, "parameters are fixed after commit or batching");
+    HostRep &R = s->reps[0];
+    if (ti < 0 || tj < 0 || ti >= R.cfg.n_types || tj >= R.cfg.n_types || sp < 0 || sp >= R.cfg.n_species)
+        return fail(s, TDPD_EINVAL, "type or species out of range");
+    if (!(kappa >= 0) || !std::isfinite(kappa)) return fail(s, TDPD_EINVAL, "kappa must be finite and >= 0");
+    R.kappa[(ti * MAXT + tj) * MAXS + sp] = kappa;
+    R.kappa[(tj * MAXT + ti) * MAXS + sp] = kappa;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_reaction(tdpd_sys *s, float k, int src, int dst, uint32_t types)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed || s->reps.size() != 1) return fail(s, TDPD_ESTATE, "parameters are fixed after commit or batching");
+    HostRep &R = s->reps[0];
+    if (src < 0 || dst < 0 || src >= R.cfg.n_species || dst >= R.cfg.n_species || src == dst)
+        return fail(s, TDPD_EINVAL, "reaction species out of range");
+    if (!std::isfinite(k)) return fail(s, TDPD_EINVAL, "reaction rate must be finite");
+    R.k_react = k;
+    R.r_src = src;
+    R.r_dst = dst;
+    R.r_types = types;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_membrane(tdpd_sys *s, const tdpd_membrane *m)
+{
+    if (!s || !m) return fail(s, TDPD_EINVAL, "null argument");
+    if (s->committed || s->reps.size() != 1) return fail(s, TDPD_ESTATE, "parameters are fixed after commit or batching");
+    if (!(m->p > 0) || !(m->x0 > 0 && m->x0 < 1) || !(m->m > 0) || !(m->kT >= 0))
+        return fail(s, TDPD_EINVAL, "membrane: need p > 0, 0 < x0 < 1, m > 0, kT >= 0");
+    if (!(m->gammaT >= 0) || !(3.0f * m->gammaC >= m->gammaT))
+        return fail(s, TDPD_EINVAL, "membrane: need gammaT >= 0 and 3 gammaC >= gammaT");
+    s->reps[0].mem = *m;
+    s->reps[0].has_mem = true;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_add_particles(tdpd_sys *s, int n, const float *pos, const float *vel,
+                               const float *conc, const int32_t *type)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed || s->reps.size() != 1) return fail(s, TDPD_ESTATE, "particles are fixed after commit or batching");
+    HostRep &R = s->reps[0];
+    if (!R.rbcs.empty()) return fail(s, TDPD_ESTATE, "add free particles before membranes");
+    if (n < 0 || (n > 0 && (!pos || !vel || !type))) return fail(s, TDPD_EINVAL, "bad particle arrays");
+    const int ns = R.cfg.n_species;
+    if ((long)R.type.size() + n > TDPD_MAX_IDS) return fail(s, TDPD_EOVERFLOW, "more than %d particles", TDPD_MAX_IDS);
+    for (int i = 0; i < n; ++i) {
+        if (type[i] < 0 || type[i] >= R.cfg.n_types) return fail(s, TDPD_EINVAL, "particle %d: type %d out of range", i, type[i]);
+        for (int c = 0; c < 3; ++c) {
+            const float x = pos[3 * i + c];
+            if (!(x >= 0.0f && x < R.cfg.L[c])) return fail(s, TDPD_EINVAL, "particle %d: coordinate %d = %g outside [0, L)", i, c, x);
+            if (!std::isfinite(vel[3 * i + c])) return fail(s, TDPD_EINVAL, "particle %d: non-finite velocity", i);
+        }
+    }
+    R.pos.insert(R.pos.end(), pos, pos + 3 * (size_t)n);
+    R.vel.insert(R.vel.end(), vel, vel + 3 * (size_t)n);
+    if (conc) R.conc.insert(R.conc.end(), conc, conc + (size_t)n * ns);
+    else R.conc.insert(R.conc.end(), (size_t)n * ns, 0.0f);
+    R.type.insert(R.type.end(), type, type + n);
+    R.body.insert(R.body.end(), (size_t)n, -1);
+    R.n_free += n;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_add_rbc(tdpd_sys *s, int nv, const float *pos, const float *vel, const float *conc,
+                         int type, int ntri, const int32_t *tri, const float *rest, int *rbc_index)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed || s->reps.size() != 1) return fail(s, TDPD_ESTATE, "membranes are fixed after commit or batching");
+    HostRep &R = s->reps[0];
+    if (nv < 4 || nv > 1024 || !pos || !vel || !tri || ntri != 2 * nv - 4)
+        return fail(s, TDPD_EINVAL, "membrane needs 4..1024 vertices and 2*nv-4 triangles");
+    if (type < 0 || type >= R.cfg.n_types) return fail(s, TDPD_EINVAL, "membrane type out of range");
+    if ((long)R.type.size() + nv > TDPD_MAX_IDS) return fail(s, TDPD_EOVERFLOW, "more than %d particles", TDPD_MAX_IDS);
+    for (int i = 0; i < 3 * nv; ++i) {
+        const int c = i % 3;
+        if (!(pos[i] >= 0.0f && pos[i] < R.cfg.L[c])) return fail(s, TDPD_EINVAL, "vertex %d outside [0, L)", i / 3);
+    }
+    Topo T;
+    tdpd_status rc = build_topo(s, nv, ntri, tri, T);   // validate now
+    if (rc) return rc;
+    HostRbc H;
+    H.nv = nv;
+    H.ntri = ntri;
+    H.type = type;
+    H.tri.assign(tri, tri + 3 * ntri);
+    H.rest.assign(rest ? rest : pos, (rest ? rest : pos) + 3 * (size_t)nv);
+    const int b = (int)R.rbcs.size();
+    const int ns = R.cfg.n_species;
+    R.rbcs.push_back(std::move(H));
+    R.pos.insert(R.pos.end(), pos, pos + 3 * (size_t)nv);
+    R.vel.insert(R.vel.end(), vel, vel + 3 * (size_t)nv);
+    if (conc) R.conc.insert(R.conc.end(), conc, conc + (size_t)nv * ns);
+    else R.conc.insert(R.conc.end(), (size_t)nv * ns, 0.0f);
+    R.type.insert(R.type.end(), (size_t)nv, type);
+    R.body.insert(R.body.end(), (size_t)nv, b);
+    if (rbc_index) *rbc_index = b;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_batch_create(tdpd_sys **out, tdpd_sys *const *replicas, int n)
+{
+    if (!out || !replicas || n <= 0) return fail(nullptr, TDPD_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    tdpd_sys *s = new (std::nothrow) tdpd_sys;
+    if (!s) return fail(nullptr, TDPD_ENOMEM, "host allocation failed");
+    for (int k = 0; k < n; ++k) {
+        tdpd_sys *r = replicas[k];
+        if (!r || r->reps.size() != 1) {
+            delete s;
+            return fail(nullptr, TDPD_EINVAL, "replica %d is not a single-replica handle", k);
+        }
+        HostRep R = r->reps[0];
+        if (r->committed) {
+            const int m = (int)R.type.size();
+            tdpd_status rc = download(r, 0, R.pos.data(), R.vel.data(), R.conc.data(), nullptr, nullptr);
+            if (rc) {
+                delete s;
+                return fail(nullptr, rc, "replica %d: %s", k, r->err.c_str());
+            }
+            (void)m;
+            R.step = r->step;
+        }
+        s->reps.push_back(std::move(R));
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete s;
+        return fail(nullptr, TDPD_ECUDA, "stream creation: %s", cudaGetErrorString(e));
+    }
+    *out = s;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_stream(tdpd_sys *s, void *stream)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    s->user = (cudaStream_t)stream;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_commit(tdpd_sys *s) { return ensure(s); }
+
+tdpd_status tdpd_step(tdpd_sys *s, int n)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    if (n < 0) return fail(s, TDPD_EINVAL, "negative step count");
+    cudaStream_t st = exec_stream(s);
+    int left = n;
+    while (left >= GRAPH_LONG) {
+        CU(cudaGraphLaunch(s->glong[s->parity], st));
+        left -= GRAPH_LONG;
+    }
+    while (left > 0) {
+        CU(cudaGraphLaunch(s->g1[s->parity], st));
+        s->parity ^= 1;
+        --left;
+    }
+    s->step += n;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_step_timed(tdpd_sys *s, float *kernel_ms, int max_kernels, int *n_kernels)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    cudaStream_t st = exec_stream(s);
+    CU(cudaGraphLaunch(s->gtimed[s->parity], st));
+    CU(cudaStreamSynchronize(st));
+    s->parity ^= 1;
+    s->step += 1;
+    const int nk = s->n_ev - 1;
+    for (int k = 0; k < nk && k < max_kernels; ++k) CU(cudaEventElapsedTime(kernel_ms + k, s->ev[k], s->ev[k + 1]));
+    if (n_kernels) *n_kernels = nk;
+    return TDPD_OK;
+}
+
+const char *tdpd_kernel_name(const tdpd_sys *s, int k)
+{
+    if (!s) return nullptr;
+    const std::vector<int> ks = step_kernels(s);
+    return (k >= 0 && k < (int)ks.size()) ? KERNEL_NAMES[ks[k]] : nullptr;
+}
+
+tdpd_status tdpd_replica_status(tdpd_sys *s, int32_t *status)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    std::vector<uint32_t> w(s->reps.size());
+    CU(cudaMemcpyAsync(w.data(), s->errw, sizeof(uint32_t) * w.size(), cudaMemcpyDeviceToHost, exec_stream(s)));
+    CU(cudaStreamSynchronize(exec_stream(s)));
+    for (size_t r = 0; r < w.size(); ++r) status[r] = w[r] ? TDPD_ENONFINITE : TDPD_OK;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_sync(tdpd_sys *s)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    std::vector<int32_t> st(s->reps.size());
+    if ((rc = tdpd_replica_status(s, st.data()))) return rc;
+    for (size_t r = 0; r < st.size(); ++r)
+        if (st[r]) return fail(s, TDPD_ENONFINITE, "replica %zu produced a non-finite force", r);
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_state(tdpd_sys *s, int r, const float *pos, const float *vel, const float *conc)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    HostRep *R = rep_of(s, r);
+    if (!R || !pos || !vel) return fail(s, TDPD_EINVAL, "bad replica or array");
+    const int n = (int)R->type.size(), ns = s->ns;
+    for (int i = 0; i < 3 * n; ++i)
+        if (!(pos[i] >= 0.0f && pos[i] < R->cfg.L[i % 3]) || !std::isfinite(vel[i]))
+            return fail(s, TDPD_EINVAL, "particle %d: position outside the box or non-finite velocity", i / 3);
+    // other replicas keep their current device state
+    for (size_t q = 0; q < s->reps.size(); ++q) {
+        if ((int)q == r) continue;
+        HostRep &O = s->reps[q];
+        if ((rc = download(s, (int)q, O.pos.data(), O.vel.data(), O.conc.data(), nullptr, nullptr))) return rc;
+    }
+    if (!conc && (rc = download(s, r, nullptr, nullptr, R->conc.data(), nullptr, nullptr))) return rc;
+    std::memcpy(R->pos.data(), pos, sizeof(float) * 3 * n);
+    std::memcpy(R->vel.data(), vel, sizeof(float) * 3 * n);
+    if (conc) std::memcpy(R->conc.data(), conc, sizeof(float) * (size_t)n * ns);
+    return init_state(s);
+}
+
+tdpd_status tdpd_read_state(tdpd_sys *s, int r, float *pos, float *vel, float *conc)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    if (!rep_of(s, r)) return fail(s, TDPD_EINVAL, "bad replica");
+    return download(s, r, pos, vel, conc, nullptr, nullptr);
+}
+
+tdpd_status tdpd_read_forces(tdpd_sys *s, int r, float *force, float *flux)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    if (!rep_of(s, r)) return fail(s, TDPD_EINVAL, "bad replica");
+    return download(s, r, nullptr, nullptr, nullptr, force, flux);
+}
+
+tdpd_status tdpd_read_observables(tdpd_sys *s, int r, tdpd_obs *out)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    HostRep *R = rep_of(s, r);
+    if (!R || !out) return fail(s, TDPD_EINVAL, "bad replica or output");
+    cudaStream_t st = exec_stream(s);
+    launch_observables(s->buf[s->parity], s->d_reps, (int)s->reps.size(), s->ns, s->d_obs, st);
+    double h[OBS_K];
+    CU(cudaMemcpyAsync(h, s->d_obs + (size_t)r * OBS_K, sizeof h, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    std::memset(out, 0, sizeof *out);
+    out->step = s->step + (s->reps.size() > 1 ? R->step : 0);
+    out->n_particles = (int)R->type.size();
+    out->n_species = s->ns;
+    out->n_rbc = (int)R->rbcs.size();
+    const double nm = h[4];
+    out->n_mobile = (int)nm;
+    for (int c = 0; c < 3; ++c) out->momentum[c] = h[c];
+    const double p2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+    out->kT = nm > 1 ? (h[3] - p2 / nm) / (3.0 * (nm - 1.0)) : 0.0;
+    for (int k = 0; k < s->ns; ++k) out->mass[k] = h[5 + k];
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_read_rbc(tdpd_sys *s, int r, double *area, double *volume)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    HostRep *R = rep_of(s, r);
+    if (!R) return fail(s, TDPD_EINVAL, "bad replica");
+    const int nb = (int)R->rbcs.size();
+    if (nb == 0) return TDPD_OK;
+    std::vector<double2> av(nb);
+    CU(cudaMemcpyAsync(av.data(), s->d_av + s->rep_rbc0[r], sizeof(double2) * nb, cudaMemcpyDeviceToHost, exec_stream(s)));
+    CU(cudaStreamSynchronize(exec_stream(s)));
+    for (int b = 0; b < nb; ++b) {
+        if (area) area[b] = av[b].x;
+        if (volume) volume[b] = av[b].y;
+    }
+    return TDPD_OK;
+}
+
+int tdpd_num_replicas(const tdpd_sys *s) { return s ? (int)s->reps.size() : 0; }
+
+int tdpd_num_particles(const tdpd_sys *s, int r)
+{
+    if (!s || r < 0 || r >= (int)s->reps.size()) return -1;
+    return (int)s->reps[r].type.size();
+}
+
+int64_t tdpd_current_step(const tdpd_sys *s) { return s ? s->step : -1; }
+
+int tdpd_launches_per_step(const tdpd_sys *s)
+{
+    if (!s) return 0;
+    return (int)step_kernels(s).size();
+}
+
+const char *tdpd_last_error(const tdpd_sys *s) { return s ? s->err.c_str() : g_err.c_str(); }
+
+void tdpd_destroy(tdpd_sys *s)
+{
+    if (!s) return;
+    if (s->committed) cudaStreamSynchronize(exec_stream(s));
+    free_device(s);
+    if (s->own) cudaStreamDestroy(s->own);
+    if (s->cap) cudaStreamDestroy(s->cap);
+    delete s;
+}
+
+tdpd_status tdpd_debug_rng(uint64_t seed, int n, const uint32_t *i, const uint32_t *j,
+                           const uint32_t *step, const uint32_t *stream, uint32_t *bits,
+                           float *normal)
+{
+    tdpd_sys *s = nullptr;
+    if (n < 0 || (n > 0 && (!i || !j || !step || !stream || !bits || !normal)))
+        return fail(nullptr, TDPD_EINVAL, "bad arguments");
+    if (n == 0) return TDPD_OK;
+    uint32_t *d = nullptr;
+    float *g = nullptr;
+    const size_t sz = (size_t)n * sizeof(uint32_t);
+    CU(cudaMalloc(&d, 6 * sz));
+    cudaError_t e = cudaMalloc(&g, 2 * (size_t)n * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return fail(nullptr, TDPD_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+    cudaMemcpy(d, i, sz, cudaMemcpyHostToDevice);
+    cudaMemcpy(d + n, j, sz, cudaMemcpyHostToDevice);
+    cudaMemcpy(d + 2 * (size_t)n, step, sz, cudaMemcpyHostToDevice);
+    cudaMemcpy(d + 3 * (size_t)n, stream, sz, cudaMemcpyHostToDevice);
+    launch_debug_rng(seed, n, d, d + n, d + 2 * (size_t)n, d + 3 * (size_t)n, d + 4 * (size_t)n, g, 0);
+    e = cudaMemcpy(bits, d + 4 * (size_t)n, 2 * sz, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(normal, g, 2 * (size_t)n * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    cudaFree(g);
+    if (e != cudaSuccess) return fail(nullptr, TDPD_ECUDA, "debug rng: %s", cudaGetErrorString(e));
+    return TDPD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+// Membrane forces of the triangulated RBC model (Sec. 2.2, Eq. 10-16).
+//
+// k_mem_gather (K-Gather of Sec. 3.3): one CTA per membrane sums the
+//   triangle areas and signed tetrahedron volumes in FP64 with compensation,
+//   and the vertex centroid that becomes the next step's reference point.
+// k_mem_forces (K-Apply, bonds and bending): eight lanes per vertex; lane l
+//   takes the l-th entry of the vertex's one-ring fan and adds
+//     - the bond (v, nb[l]): WLC + POW, viscous and random parts,
+//     - the dihedral on edge (v, nb[l]) (v as an edge end),
+//     - the triangle (v, nb[l], nb[l+1]): area and volume constraints,
+//     - the dihedral on edge (nb[l], nb[l+1]) (v as the opposite vertex);
+//   a shuffle sums the lanes. Every vertex force is written once, no atomics.
+//
+// Coordinates are taken relative to a per-membrane reference point with the
+// minimum image, so a membrane may straddle the periodic boundary as long as
+// it spans less than half a box.
+#include "launch.h"
+
+namespace tdpd {
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 sub(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 add(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 scl(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b)
+{
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ float3 rel_pos(const RepParams &P, float4 x, float4 ref)
+{
+    return make_float3(min_image(x.x - ref.x, P.L[0], P.periodic[0]),
+                       min_image(x.y - ref.y, P.L[1], P.periodic[1]),
+                       min_image(x.z - ref.z, P.L[2], P.periodic[2]));
+}
+
+__device__ __forceinline__ double shfl_down_d(double x, int o)
+{
+    return __shfl_down_sync(0xffffffffu, x, o);
+}
+
+// Block-wide reduction of K compensated sums in a fixed order; result in
+// thread 0.
+template <int K>
+__device__ void block_ksum(KSum (&v)[K])
+{
+    __shared__ double sh[32][K][2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) {
+            KSum t;
+            t.s = shfl_down_d(v[k].s, o);
+            t.c = shfl_down_d(v[k].c, o);
+            if (lane + o < 32) ksum_merge(v[k], t);
+        }
+    if (lane == 0)
+        for (int k = 0; k < K; ++k) { sh[w][k][0] = v[k].s; sh[w][k][1] = v[k].c; }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int ww = 1; ww < nw; ++ww)
+            for (int k = 0; k < K; ++k) {
+                KSum t;
+                t.s = sh[ww][k][0];
+                t.c = sh[ww][k][1];
+                ksum_merge(v[k], t);
+            }
+}
+
+__global__ void __launch_bounds__(256) k_mem_gather(MemArgs A)
+{
+    const int b = blockIdx.x;
+    const RbcDev R = A.rbcs[b];
+    const TopoDev T = A.topos[R.topo];
+    const RepParams &P = A.reps[R.rep];
+    const float4 ref = A.ref_in[b];
+    KSum acc[5];
+    for (int k = 0; k < 5; ++k) acc[k].s = acc[k].c = 0.0;
+    for (int t = threadIdx.x; t < T.ntri; t += blockDim.x) {
+        const int *tv = A.tri + T.tri_off + 3 * t;
+        const float3 x0 = rel_pos(P, A.pos[A.inv[R.gbase + tv[0]]], ref);
+        const float3 x1 = rel_pos(P, A.pos[A.inv[R.gbase + tv[1]]], ref);
+        const float3 x2 = rel_pos(P, A.pos[A.inv[R.gbase + tv[2]]], ref);
+        const float3 n = cross(sub(x1, x0), sub(x2, x0));
+        acc[0].add(0.5 * (double)sqrtf(dot(n, n)));
+        acc[1].add((double)dot(x0, cross(x1, x2)) / 6.0);
+    }
+    for (int v = threadIdx.x; v < T.nv; v += blockDim.x) {
+        const float3 x = rel_pos(P, A.pos[A.inv[R.gbase + v]], ref);
+        acc[2].add(x.x);
+        acc[3].add(x.y);
+        acc[4].add(x.z);
+    }
+    block_ksum<5>(acc);
+    if (threadIdx.x == 0) {
+        A.av[b] = make_double2(acc[0].value(), acc[1].value());
+        const double inv = 1.0 / T.nv;
+        float4 nr = ref;
+        nr.x = (float)(ref.x + acc[2].value() * inv);
+        nr.y = (float)(ref.y + acc[3].value() * inv);
+        nr.z = (float)(ref.z + acc[4].value() * inv);
+        for (int c = 0; c < 3; ++c) {
+            float *pc = c == 0 ? &nr.x : (c == 1 ? &nr.y : &nr.z);
+            if (P.periodic[c]) {
+                if (*pc < 0.0f) *pc += P.L[c];
+                else if (*pc >= P.L[c]) *pc -= P.L[c];
+            }
+        }
+        A.ref_out[b] = nr;
+    }
+}
+
+// Gradient of the angle theta between the outward normals of triangles
+// (a, b, c) and (b, a, d) (positive on a convex fold). Returns sin and cos of
+// theta; role selects the vertex whose gradient is written to g.
+struct Dihedral {
+    float sin_t, cos_t;
+    float3 g;
+};
+
+__device__ __forceinline__ Dihedral dihedral(float3 xa, float3 xb, float3 xc, float3 xd, int role)
+{
+    const float3 e = sub(xb, xa);
+    const float3 n1 = cross(e, sub(xc, xa));
+    const float3 n2 = cross(sub(xa, xb), sub(xd, xb));
+    const float le2 = dot(e, e), n1s = dot(n1, n1), n2s = dot(n2, n2);
+    const float le = sqrtf(le2);
+    const float inv12 = rsqrtf(n1s * n2s);
+    Dihedral D;
+    D.cos_t = dot(n1, n2) * inv12;
+    D.sin_t = dot(cross(n1, n2), e) * inv12 / le;
+    const float3 u1 = scl(1.0f / n1s, n1), u2 = scl(1.0f / n2s, n2);
+    if (role == 0) {          // a
+        const float p1 = dot(sub(xc, xb), e) / le, p2 = dot(sub(xd, xb), e) / le;
+        D.g = scl(-1.0f, add(scl(p1, u1), scl(p2, u2)));
+    } else {                  // c
+        D.g = scl(-le, u1);
+    }
+    return D;
+}
+
+__global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
+{
+    const int b = blockIdx.y;
+    const RbcDev R = A.rbcs[b];
+    const TopoDev T = A.topos[R.topo];
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int lane8 = threadIdx.x & 7;
+    const bool live = v < T.nv;
+    const RepParams &P = A.reps[R.rep];
+    float3 f = make_float3(0.f, 0.f, 0.f);
+    int slot_v = 0;
+    if (live) {
+        const float4 ref = A.ref_in[b];
+        const double2 av = A.av[b];
+        const float cg = (float)(P.m_kg * (av.x - R.A0) / R.A0);
+        const float cv = (float)(P.m_kv * (av.y - R.V0) / R.V0);
+        const int off = A.ring_off[T.ring_off + v];
+        const int deg = A.ring_off[T.ring_off + v + 1] - off;
+        slot_v = A.inv[R.gbase + v];
+        const float3 xv = rel_pos(P, A.pos[slot_v], ref);
+        const float4 vv = A.vt[slot_v];
+        const uint32_t idv = (uint32_t)(R.gbase + v - P.pbase);
+        const uint32_t step = *A.step_ctr + P.step0;
+        for (int l = lane8; l < deg; l += 8) {
+            const RingEntry E = A.ring[off + l];
+            const RingEntry En = A.ring[off + (l + 1 == deg ? 0 : l + 1)];
+            const RingEntry Ep = A.ring[off + (l == 0 ? deg - 1 : l - 1)];
+            const int s_nl = A.inv[R.gbase + E.nb];
+            const float3 xl = rel_pos(P, A.pos[s_nl], ref);
+            const float3 xn = rel_pos(P, A.pos[A.inv[R.gbase + En.nb]], ref);
+            const float3 xp = rel_pos(P, A.pos[A.inv[R.gbase + Ep.nb]], ref);
+            const float3 xw = rel_pos(P, A.pos[A.inv[R.gbase + E.across]], ref);
+
+            // bond (v, nb[l]): Eq. 10-13
+            {
+                const float3 d = sub(xv, xl);
+                const float l2 = dot(d, d);
+                const float il = rsqrtf(l2);
+                const float len = l2 * il;
+                const float3 e = scl(il, d);
+                const float2 bp = A.bond[R.bond_off + E.edge];   // (l_m, k_p)
+                const float x = len / bp.x;
+                const float omx = 1.0f - x;
+                const float pw = P.m_m == 2.0f ? len * len : __powf(len, P.m_m);
+                const float dudl = P.m_wlc0 * (0.25f / (omx * omx) - 0.25f + x) - bp.y / pw;
+                f = add(f, scl(-dudl, e));
+                const float4 vl = A.vt[s_nl];
+                const float3 vij = make_float3(vv.x - vl.x, vv.y - vl.y, vv.z - vl.z);
+                const float ve = dot(vij, e);
+                f = add(f, add(scl(-P.m_gT, vij), scl(-P.m_gC * ve, e)));
+                const uint32_t idl = (uint32_t)(R.gbase + E.nb - P.pbase);
+                float z[10];
+#pragma unroll
+                for (int s = 0; s < 5; ++s) {
+                    const float2 g = normal2(pair_bits(idv, idl, P.seed_lo, P.seed_hi, step, 1u + s));
+                    z[2 * s] = g.x;
+                    z[2 * s + 1] = g.y;
+                }
+                const float tr = z[0] + z[4] + z[8];
+                // (W^S - tr/3 I) e with W^S the symmetric part of Z
+                const float s01 = 0.5f * (z[1] + z[3]), s02 = 0.5f * (z[2] + z[6]), s12 = 0.5f * (z[5] + z[7]);
+                const float t3 = tr * (1.0f / 3.0f);
+                const float3 we = make_float3((z[0] - t3) * e.x + s01 * e.y + s02 * e.z,
+                                              s01 * e.x + (z[4] - t3) * e.y + s12 * e.z,
+                                              s02 * e.x + s12 * e.y + (z[8] - t3) * e.z);
+                f = add(f, add(scl(P.m_rand_T, we), scl(P.m_rand_C * tr, e)));
+            }
+            // dihedral on edge (v, nb[l]): triangles (v, nb[l], nb[l+1]), (nb[l], v, nb[l-1])
+            {
+                const Dihedral D = dihedral(xv, xl, xn, xp, 0);
+                const float s = P.m_kb * (D.sin_t * P.m_cos0 - D.cos_t * P.m_sin0);
+                f = sub(f, scl(s, D.g));
+            }
+            // triangle (v, nb[l], nb[l+1]): Eq. 14-15
+            {
+                const float3 n = cross(sub(xl, xv), sub(xn, xv));
+                const float nn = sqrtf(dot(n, n));
+                const float At = 0.5f * nn;
+                const float a0 = A.a0j[R.a0j_off + E.tri];
+                const float ca = cg + P.m_kl * (At - a0) / a0;
+                const float3 gA = scl(0.5f / nn, cross(n, sub(xn, xl)));
+                const float3 gV = scl(1.0f / 6.0f, cross(xl, xn));
+                f = sub(f, add(scl(ca, gA), scl(cv, gV)));
+            }
+            // dihedral on edge (nb[l], nb[l+1]) with v opposite: (nb[l], nb[l+1], v), (nb[l+1], nb[l], w)
+            {
+                const Dihedral D = dihedral(xl, xn, xv, xw, 2);
+                const float s = P.m_kb * (D.sin_t * P.m_cos0 - D.cos_t * P.m_sin0);
+                f = sub(f, scl(s, D.g));
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        f.x += __shfl_xor_sync(0xffffffffu, f.x, o);
+        f.y += __shfl_xor_sync(0xffffffffu, f.y, o);
+        f.z += __shfl_xor_sync(0xffffffffu, f.z, o);
+    }
+    if (live && lane8 == 0) A.fext[slot_v] = make_float4(f.x, f.y, f.z, 0.0f);
+}
+
+void launch_mem_gather(const MemArgs &a, cudaStream_t st)
+{
+    if (a.n_rbc <= 0) return;
+    k_mem_gather<<<a.n_rbc, 256, 0, st>>>(a);
+}
+
+void launch_mem_forces(const MemArgs &a, cudaStream_t st)
+{
+    if (a.n_rbc <= 0) return;
+    dim3 g((a.max_nv * 8 + 255) / 256, a.n_rbc);
+    k_mem_forces<<<g, 256, 0, st>>>(a);
+}
+
+}  // namespace tdpd

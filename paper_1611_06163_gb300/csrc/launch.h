@@ -1,0 +1,68 @@
+// Host-side launchers of the device kernels (one translation unit each).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tdpd {
+
+struct Buffers {
+    float4 *pos, *vt, *vel, *frc;
+    float *C, *Ct, *Q;
+};
+
+struct PairArgs {
+    Buffers b;
+    const float4 *fext;          // membrane force per slot (membrane particles only)
+    const RepParams *reps;
+    const int *cell_start;       // [NC+1]
+    int *count;                  // [NC] histogram of the next binning (zeroed by scan)
+    int2 *cellrank;              // [N] (cell, rank) of the next binning
+    uint32_t *err;               // [n_rep] status bits
+    const uint32_t *step_ctr;    // absolute step of this evaluation
+    int n;                       // particles (slots)
+    int ns;                      // species (runtime value for the generic path)
+    int integrate;               // 0: forces only (commit / set_state); 1: full step
+};
+
+struct MemArgs {
+    const Buffers *unused;
+    const float4 *pos, *vt;
+    const int *inv;              // load index -> slot
+    const RepParams *reps;
+    const RbcDev *rbcs;
+    const TopoDev *topos;
+    const int *tri;
+    const int *ring_off;
+    const RingEntry *ring;
+    const float *a0j;
+    const float2 *bond;          // (l_m, k_p) per bond
+    const float4 *ref_in;        // per-membrane reference point
+    float4 *ref_out;             // next reference point (centroid)
+    double2 *av;                 // per-membrane (A, V)
+    float4 *fext;
+    const uint32_t *step_ctr;
+    int n_rbc, max_nv;
+};
+
+void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count, int2 *cellrank,
+                     cudaStream_t st);
+void launch_scan(int *count, int *cell_start, int n_cells, uint32_t *step_ctr, int inc,
+                 cudaStream_t st);
+void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *cell_start,
+                         int2 *keys, int n, cudaStream_t st);
+void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams *reps,
+                        const int2 *keys, const int2 *cellrank, const int *cell_start, int *inv,
+                        int n, int ns, int predict, cudaStream_t st);
+void launch_pair(const PairArgs &a, cudaStream_t st);
+void launch_mem_gather(const MemArgs &a, cudaStream_t st);
+void launch_mem_forces(const MemArgs &a, cudaStream_t st);
+void launch_observables(const Buffers &b, const RepParams *reps, int n_rep, int ns,
+                        double *out, cudaStream_t st);
+void launch_debug_rng(uint64_t seed, int n, const uint32_t *i, const uint32_t *j,
+                      const uint32_t *step, const uint32_t *stream, uint32_t *bits,
+                      float *normal, cudaStream_t st);
+
+}  // namespace tdpd

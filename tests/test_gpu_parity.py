@@ -1,0 +1,239 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs: random numbers, per-step forces and fluxes, 10-step trajectories,
+membrane forces, FP64 reductions, edge cases and batching."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_common import (B, make, normwise, elementwise, wrap_diff, forces_vs_oracle, run_vs_oracle,
+                        TOL_FORCE, TOL_TRAJ)
+from helpers import custom, membrane_only, small_sphere
+
+pytestmark = pytest.mark.gpu
+
+
+def test_rng_bits_identical_and_normals_close():
+    """Sec. 3.1 pairwise RNG: the device TEA bits equal the oracle's for the
+    same keys; the Box-Muller normals agree to single precision."""
+    bd = B()
+    rng = np.random.default_rng(1)
+    n = 20000
+    i = rng.integers(0, 2**24, n, dtype=np.uint32)
+    j = rng.integers(0, 2**24, n, dtype=np.uint32)
+    st = rng.integers(0, 2**32, n, dtype=np.uint32)
+    sm = rng.integers(0, 6, n, dtype=np.uint32)
+    seed = 0x1234_5678_9ABC_DEF0
+    bits, g = bd.tdpd_debug_rng(seed, i, j, st, sm)
+    ref_bits = np.array([oracle.uniform_pair(seed, int(a), int(b), int(c), int(d))[0]
+                         for a, b, c, d in zip(i, j, st, sm)], np.uint32)
+    assert np.array_equal(bits, ref_bits)
+    ref = np.array([oracle.normal_pair(seed, int(a), int(b), int(c), int(d))
+                    for a, b, c, d in zip(i, j, st, sm)])
+    err = np.abs(g - ref)
+    rad = np.sqrt(ref[:, 0] ** 2 + ref[:, 1] ** 2)[:, None] * np.ones((1, 2))
+    ok = rad > 0.05
+    assert err[ok].max() < 2e-5 * (1 + np.abs(ref[ok]).max())
+    assert err.max() < 5e-3
+    # symmetric in the pair
+    bits2, _ = bd.tdpd_debug_rng(seed, j, i, st, sm)
+    assert np.array_equal(bits, bits2)
+
+
+@pytest.mark.parametrize('ns', [1, 3])
+def test_pair_forces_small_box(ns):
+    """Eq. 3 + Eq. 6 at step 0 on a 6^3 box (3 cells per axis, ragged tail of
+    the last block) against the O(n^2) oracle."""
+    d = W.fluid_box(L=6.0, rho=4.0, n_species=ns, seed=11)
+    F, Q, Fo, Qo = forces_vs_oracle(d, mode=0)
+    assert normwise(F, Fo) < TOL_FORCE
+    assert normwise(Q, Qo) < TOL_FORCE
+    assert elementwise(F, Fo) < 5e-4
+
+
+def test_pair_forces_two_types_and_exponents():
+    """Unequal a/gamma/sigma and kappa per type pair, s_f = 0.41, s_c = 1.5."""
+    rng = np.random.default_rng(5)
+    L = (7.0, 6.0, 8.0)
+    n = int(3 * np.prod(L))
+    pos = rng.random((n, 3)) * np.asarray(L)
+    d = custom(pos, rng.normal(0, 1, (n, 3)), rng.random((n, 2)), L=L, ns=2, n_types=2,
+               types=rng.integers(0, 2, n), s_f=0.41, s_c=1.5)
+    d['a'][:] = [[25.0, 40.0], [40.0, 18.0]]
+    d['gamma'][:] = [[4.5, 6.0], [6.0, 3.0]]
+    d['sigma'][:] = np.sqrt(2 * d['gamma'])
+    d['kappa'][0, 1, :] = d['kappa'][1, 0, :] = [0.1, 0.5]
+    d['kappa'][1, 1, :] = [2.0, 0.0]
+    F, Q, Fo, Qo = forces_vs_oracle(d, mode=0)
+    assert normwise(F, Fo) < TOL_FORCE
+    assert normwise(Q, Qo) < TOL_FORCE
+
+
+def test_fluid_4k_forces_and_trajectory():
+    """Plain tDPD fluid (4000 particles, L=10, rho=4): forces at step 0 and the
+    state after 10 velocity-Verlet steps."""
+    d = W.fluid_box()
+    F, Q, Fo, Qo = forces_vs_oracle(d, mode=1)
+    assert normwise(F, Fo) < TOL_FORCE
+    assert normwise(Q, Qo) < TOL_FORCE
+    err, obs, o, _ = run_vs_oracle(d, 10)
+    for k, v in err.items():
+        assert v < TOL_TRAJ, (k, v, err)
+    ob = o.observables()
+    assert obs['kT'] == pytest.approx(ob['kT'], rel=1e-4)
+    assert np.allclose(obs['momentum'], ob['momentum'], atol=1e-3)
+    assert obs['mass'][0] == pytest.approx(ob['mass'][0], rel=1e-6)
+
+
+def test_single_rbc_forces_trajectory_and_fp64_reductions():
+    """500-vertex RBC in 24k solvent: forces (pair + membrane) at step 0, 10
+    steps, and the FP64 area/volume against the oracle."""
+    d = W.single_rbc()
+    F, Q, Fo, Qo = forces_vs_oracle(d, mode=1)
+    assert normwise(F, Fo) < TOL_FORCE
+    assert normwise(Q, Qo) < TOL_FORCE
+    mem = slice(d['particles']['pos'].shape[0], None)
+    assert normwise(F[mem], Fo[mem]) < TOL_FORCE
+    err, obs, o, (A, V) = run_vs_oracle(d, 10)
+    for k, v in err.items():
+        assert v < TOL_TRAJ, (k, v, err)
+    ob = o.observables()
+    assert abs(A[0] - ob['area'][0]) / ob['area'][0] < 1e-6
+    assert abs(V[0] - ob['volume'][0]) / ob['volume'][0] < 1e-6
+    assert obs['mass'][0] == pytest.approx(ob['mass'][0], rel=1e-6)
+
+
+@pytest.mark.parametrize('theta0', [0.0, 0.1])
+def test_membrane_forces_alone(theta0):
+    """Membrane-only system (no pair forces): bond + viscous + random + area +
+    volume + bending forces of a perturbed 162-vertex sphere."""
+    v, t = small_sphere(162, 3.0)
+    rng = np.random.default_rng(3)
+    u = v * 1.05 + rng.uniform(-0.1, 0.1, v.shape)
+    d = membrane_only(u, t, L=20.0, rest=v, vel=rng.normal(0, 1, v.shape), theta0=theta0)
+    d['a'][:] = 0.0
+    d['gamma'][:] = 0.0
+    d['sigma'][:] = 0.0
+    d['kappa'][:] = 0.0
+    F, Q, Fo, Qo = forces_vs_oracle(d, mode=1)
+    assert normwise(F, Fo) < TOL_FORCE
+    # conservative part alone (kT = 0 removes the random force; velocity zero)
+    d2 = membrane_only(u, t, L=20.0, rest=v, kT=0.0, theta0=theta0)
+    for k in ('a', 'gamma', 'sigma', 'kappa'):
+        d2[k][:] = 0.0
+    F2, _, Fo2, _ = forces_vs_oracle(d2, mode=1)
+    assert normwise(F2, Fo2) < TOL_FORCE
+    assert np.abs(F2.astype(np.float64).sum(0)).max() < 1e-4 * np.abs(Fo2).max()
+
+
+def test_membrane_straddling_periodic_boundary():
+    """A membrane split by the periodic boundary gives the same forces as the
+    oracle's unwrapped evaluation."""
+    v, t = small_sphere(162, 3.0)
+    rng = np.random.default_rng(4)
+    u = v * 1.03 + rng.uniform(-0.05, 0.05, v.shape)
+    d = membrane_only(u, t, L=16.0, rest=v)
+    r = d['rbcs'][0]
+    L = d['L'].astype(np.float64)
+    for key in ('pos', 'rest'):
+        x = r[key].astype(np.float64) - 8.0 + 0.7      # centre near the corner
+        x = x - np.floor(x / L) * L
+        r[key] = np.minimum(x.astype(np.float32), np.nextafter(L.astype(np.float32), 0))
+    F, Q, Fo, Qo = forces_vs_oracle(d, mode=1)
+    assert normwise(F, Fo) < TOL_FORCE
+
+
+def test_edge_positions_and_single_particle():
+    """Particles on cell and box boundaries (x = 0, x just below L), and a
+    one-particle box whose force is the body force alone."""
+    L = 6.0
+    top = float(np.nextafter(np.float32(L), np.float32(0)))
+    rng = np.random.default_rng(8)
+    n = 500
+    pos = rng.random((n, 3)) * L
+    pos[:40, 0] = 0.0
+    pos[40:80, 1] = top
+    pos[80:120, 2] = 2.0          # exactly on a cell face (3 cells of 2.0)
+    pos[120:160] = [0.0, top, 4.0]
+    pos[120:160, 0] += np.arange(40) * 0.01
+    d = custom(pos, rng.normal(0, 1, (n, 3)), rng.random((n, 1)), L=(L, L, L))
+    F, Q, Fo, Qo = forces_vs_oracle(d, mode=0)
+    assert normwise(F, Fo) < TOL_FORCE
+    assert normwise(Q, Qo) < TOL_FORCE
+    d1 = custom([[1.0, 2.0, 3.0]], [[0.1, 0.2, 0.3]], L=(5.0, 5.0, 5.0), body_force=(0.05, 0.0, -0.01))
+    F1, _, Fo1, _ = forces_vs_oracle(d1, mode=0)
+    assert np.allclose(F1, Fo1, atol=1e-7)
+    err, _, _, _ = run_vs_oracle(d1, 20)
+    assert err['vel'] < 1e-6
+
+
+def test_sums_vanish_on_gpu():
+    """P1 on the device: sum of pair forces and of fluxes vanish to rounding."""
+    d = W.fluid_box(L=8.0, rho=4.0, n_species=2, seed=13)
+    F, Q, Fo, _ = forces_vs_oracle(d, mode=1)
+    F = F.astype(np.float64)
+    scale = np.sqrt((Fo ** 2).sum(1)).mean()
+    assert np.abs(F.sum(0)).max() < 1e-5 * scale * math.sqrt(len(F))
+    assert np.abs(Q.astype(np.float64).sum(0)).max() < 1e-5 * np.abs(Q).mean() * math.sqrt(len(Q))
+
+
+def test_deterministic_and_set_state():
+    """Two runs of the same workload are bit-identical. After set_state the
+    forces are those of the new (r, v, C) at the current step -- in the
+    modified velocity Verlet scheme F_k was evaluated at the predicted v~ and
+    C~, so they are recomputed, and must match the oracle at that state."""
+    bd = B()
+    d = W.single_rbc(L=12.0, diameter=5.0, seed=21)
+    outs = []
+    for rep in range(2):
+        h = make(d)
+        bd.tdpd_step(h, 7)
+        outs.append(bd.tdpd_read_state(h, 0, 1) + bd.tdpd_read_forces(h, 0, 1))
+        if rep == 1:
+            p, v, c = bd.tdpd_read_state(h, 0, 1)
+            bd.tdpd_set_state(h, 0, p, v, c)
+            F1, Q1 = bd.tdpd_read_forces(h, 0, 1)
+            o = oracle.Oracle(d, mode=1)
+            o.set_state(p, v, c, step=7)
+            assert normwise(F1, o.F) < TOL_FORCE
+            assert normwise(Q1, o.Q) < TOL_FORCE
+            p2, v2, c2 = bd.tdpd_read_state(h, 0, 1)
+            assert np.array_equal(p, p2) and np.array_equal(v, v2) and np.array_equal(c, c2)
+        bd.tdpd_destroy(h)
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_batch_equals_replicas_alone():
+    """P12: replicas of uneven size stepped together in one batch give the
+    same bits as each stepped alone."""
+    bd = B()
+    reps = W.replica_ensemble(n_rep=5, seed=77, side_lo=8, side_hi=11)
+    hs = [bd.create_from(r) for r in reps]
+    batch = bd.tdpd_batch_create(hs)
+    bd.tdpd_step(batch, 6)
+    for k, r in enumerate(reps):
+        alone = make(r)
+        bd.tdpd_step(alone, 6)
+        a = bd.tdpd_read_state(alone, 0, 1) + bd.tdpd_read_forces(alone, 0, 1)
+        b = bd.tdpd_read_state(batch, k, 1) + bd.tdpd_read_forces(batch, k, 1)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+        bd.tdpd_destroy(alone)
+    st = bd.tdpd_replica_status(batch)
+    assert (st == 0).all()
+    bd.tdpd_destroy(batch)
+    for h in hs:
+        bd.tdpd_destroy(h)
+
+
+def test_replica_ensemble_matches_oracle():
+    """Replicas with membranes, per-replica permeability and body force."""
+    reps = W.replica_ensemble(n_rep=3, seed=5, side_lo=10, side_hi=12)
+    for r in reps:
+        F, Q, Fo, Qo = forces_vs_oracle(r, mode=1)
+        assert normwise(F, Fo) < TOL_FORCE
+        assert normwise(Q, Qo) < TOL_FORCE
