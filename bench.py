@@ -37,9 +37,22 @@ import workloads as W  # noqa: E402
 
 METRIC = 'tDPD particle-steps/s on 1 GB300 (% HBM roofline); batched vs plain at tol'
 UNIT = 'particle-steps/s'
-WORKLOAD = 'single RBC (500-vertex biconcave, WLC-POW, kb=20kT, area/volume constraints, ' \
-           'membrane viscosity) in tDPD solvent, 20^3 periodic box, rho=3, 24,500 particles, ' \
-           '1 species, permeability 0.1, dt=0.01'
+WORKLOADS = {
+    'single_rbc': ('single RBC (500-vertex biconcave, WLC-POW, kb=20kT, area/volume constraints, '
+                   'membrane viscosity) in tDPD solvent, 20^3 periodic box, rho=3, 24,500 particles, '
+                   '1 species, permeability 0.1, dt=0.01', lambda seed: [W.single_rbc(seed=1002 + seed)]),
+    'fluid_4k': ('plain tDPD fluid, 10^3 periodic box, rho=4, 4000 particles, 1 species',
+                 lambda seed: [W.fluid_box(seed=1001 + seed)]),
+    'fluid_786k': ('plain tDPD fluid, 64^3 periodic box, rho=3, 786,432 particles, 1 species '
+                   '(state larger than L2; profiling case)',
+                   lambda seed: [W.fluid_box(L=64.0, rho=3.0, seed=2001 + seed)]),
+    'channel': ('RBC suspension: 64x32x32 channel with frozen-particle walls, 40 RBCs, 2 species, '
+                'reaction k=0.01, body force 0.05',
+                lambda seed: [W.rbc_channel(seed=1003 + seed)]),
+    'ensemble': ('512 independent replicas (cubic boxes 8..16 at rho=3, 0..4 RBCs, log-uniform '
+                 'permeability, body force) batched in one graph-captured step',
+                 lambda seed: W.replica_ensemble(n_rep=512, seed=1004 + seed)),
+}
 
 
 def peaks():
@@ -133,7 +146,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    desc = W.single_rbc()
+    desc = WORKLOADS[args.workload][1](0)[0]
     n = W.n_mobile(desc)
     o = oracle.Oracle(desc, mode=1)
     for _ in range(args.warmup):
@@ -150,7 +163,7 @@ def run_reference(args):
         'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world,
         'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': 1e3 * total / args.steps,
         'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
-        'data': 'synthetic', 'config': {'workload': WORKLOAD, 'particles': n},
+        'data': 'synthetic', 'config': {'workload': WORKLOADS[args.workload][0], 'particles': n},
         'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': cores, 'kind': 'oracle',
                          'sample': 'full workload, %d oracle steps (FP64 cell list, OpenMP)' % args.steps},
         'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
@@ -170,10 +183,16 @@ def run_native(args):
     pkg.build()
     from paper_1611_06163_gb300 import binding as bd
 
-    desc = W.single_rbc(seed=1002 + rank)
-    n = W.n_mobile(desc)
+    descs = WORKLOADS[args.workload][1](rank)
+    n = sum(W.n_mobile(d) for d in descs)
     stream = torch.cuda.Stream()
-    h = bd.create_from(desc, stream_ptr=stream.cuda_stream)
+    if len(descs) == 1:
+        parts = []
+        h = bd.create_from(descs[0], stream_ptr=stream.cuda_stream)
+    else:
+        parts = [bd.create_from(d) for d in descs]
+        h = bd.tdpd_batch_create(parts)
+        bd.tdpd_set_stream(h, stream.cuda_stream)
     bd.tdpd_commit(h)
     nk = bd.tdpd_launches_per_step(h)
     names = [bd.tdpd_kernel_name(h, k) for k in range(nk)]
@@ -221,7 +240,7 @@ def run_native(args):
     # each), C~ (4 B per species), v, F (16 B each), C, Q (4 B per species);
     # write v, F (16 B each), C, Q (4 B per species); plus the (cell, rank)
     # of the next binning (8 B) = 112 + 16 * ns bytes
-    ns = int(desc['n_species'])
+    ns = int(descs[0]['n_species'])
     bytes_pp = 112 + 16 * ns
     hbm, src = peaks()
     achieved = bytes_pp * n / (pair_ms * 1e-3) / 1e9
@@ -233,6 +252,7 @@ def run_native(args):
     # end to end through the public API: host state in (pinned), one step,
     # observables out
     pos, vel, conc = bd.tdpd_read_state(h, 0, ns)
+    n0 = W.n_mobile(descs[0])
     hp = torch.from_numpy(pos).pin_memory()
     hv = torch.from_numpy(vel).pin_memory()
     hc = torch.from_numpy(conc).pin_memory()
@@ -245,23 +265,33 @@ def run_native(args):
         bd.tdpd_read_observables(h, 0)
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e = {'value': world * n * e2e_steps / e2e_s, 'unit': UNIT,
+    e2e = {'value': world * n0 * e2e_steps / e2e_s, 'unit': UNIT,
            'h2d_bytes_per_step': int(pos.nbytes + vel.nbytes + conc.nbytes),
            'd2h_bytes_per_step': 8 * (5 + 8),
            'path': 'tdpd_set_state (pinned host) + tdpd_step(1) + tdpd_read_observables'}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, steps, cores = oracle_rate(W.single_rbc(), seconds=args.cpu_seconds)
+        sample = descs[:8]
+        rate, steps, cores = 0.0, 0, 0
+        for d in sample:
+            r_, s_, cores = oracle_rate(d, seconds=args.cpu_seconds / len(sample))
+            rate += 1.0 / r_ * W.n_mobile(d)
+            steps += s_
+        rate = sum(W.n_mobile(d) for d in sample) / rate
         cpu = {'value': rate, 'unit': UNIT, 'cores': cores, 'kind': 'oracle',
-               'sample': 'full workload, %d FP64 oracle steps (cell list, OpenMP)' % steps}
+               'sample': '%s, %d FP64 oracle steps (cell list, OpenMP)' % (
+                   'full workload' if len(sample) == len(descs) else
+                   'first %d of %d replicas' % (len(sample), len(descs)), steps)}
     bd.tdpd_destroy(h)
+    for hp_ in parts:
+        bd.tdpd_destroy(hp_)
     if rank == 0:
         line = {
             'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world, 'steps': args.steps,
             'warmup': args.warmup, 'ms_per_step': total_ms / args.steps, 'higher_is_better': True,
             'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
-            'config': {'workload': WORKLOAD, 'particles': n, 'box': [20, 20, 20], 'rho': 3,
+            'config': {'workload': WORKLOADS[args.workload][0], 'name': args.workload, 'particles': n,
                        'l2': 'flushed between timed steps (256 MB write)',
                        'parallelism': 'replicas only' if world > 1 else 'single GPU'},
             'roofline': roof,
@@ -285,6 +315,7 @@ def main():
     ap.add_argument('--impl', default='native', choices=['native', 'reference'])
     ap.add_argument('--cpu-seconds', type=float, default=12.0)
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--workload', default='single_rbc', choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == 'reference':
         return run_reference(args)

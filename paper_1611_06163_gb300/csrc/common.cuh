@@ -19,6 +19,8 @@ namespace tdpd {
 constexpr int MAXT = TDPD_MAX_TYPES;
 constexpr int MAXS = TDPD_MAX_SPECIES;
 constexpr uint32_t ID_MASK = 0x00FFFFFFu;
+constexpr int SCAN_TILE_LOG2 = 12;            // 4096 cells per scan tile
+constexpr int SCAN_TILE = 1 << SCAN_TILE_LOG2;
 
 // Per-replica constants, read through the read-only path.
 struct RepParams {
@@ -27,6 +29,7 @@ struct RepParams {
     int nc[3];
     int periodic[3];
     int cell_base, n_cells;  // global cell index range of the replica
+    int m_stencil;           // cells have edge >= rcut / m_stencil
     int pbase, n;            // slot (and load-order) range of the replica
     float wall_lo, wall_hi;
     uint32_t seed_lo, seed_hi;
@@ -144,6 +147,15 @@ __device__ __forceinline__ int cell_of(const RepParams &P, float x, float y, flo
     return P.cell_base + (cz * P.nc[1] + cy) * P.nc[0] + cx;
 }
 
+// Count one particle (cell c >= 0) into its scan tile; lanes of a warp that
+// share a tile add once. Every lane of the warp must call it (c < 0: none).
+__device__ __forceinline__ void add_tile_count(int *tile_sum, int c)
+{
+    const int tile = c >= 0 ? (c >> SCAN_TILE_LOG2) : -1 - (int)(threadIdx.x & 31);
+    const unsigned same = __match_any_sync(0xffffffffu, tile);
+    if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(tile_sum + tile, __popc(same));
+}
+
 // Fold a coordinate back into [0, L) after a move of less than one box.
 __device__ __forceinline__ float wrap_coord(float x, float L)
 {
@@ -189,13 +201,15 @@ __device__ __forceinline__ float min_image(float d, float L, int periodic)
 }
 
 // ---------------------------------------------------- FP64 compensated sum
+// (sum, compensation) pair; merging two pairs adds the rounding error of the
+// leading sum exactly (Knuth's TwoSum), branch-free.
 struct KSum {
     double s, c;
     __device__ __forceinline__ void add(double x)
     {
-        double t = s + x;
-        if (fabs(s) >= fabs(x)) c += (s - t) + x;
-        else c += (x - t) + s;
+        const double t = s + x;
+        const double bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
         s = t;
     }
     __device__ __forceinline__ double value() const { return s + c; }
@@ -206,5 +220,40 @@ __device__ __forceinline__ void ksum_merge(KSum &a, const KSum &b)
     a.add(b.s);
     a.c += b.c;
 }
+
+// ------------------------------------------ float-float compensated sum
+// (hi, lo) with hi + lo carrying ~48 significant bits; additions use the
+// exact TwoSum of the leading parts. GB300 runs binary64 at a small fraction
+// of the binary32 rate, so long sums are carried in float-float and only the
+// last few partials are combined in binary64.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bp = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(b.hi, bp));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, e);
+    return FF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, float x) { return ff_add(a, FF{x, 0.0f}); }
+
+// x*x exactly as a float-float (the FMA recovers the rounding error)
+__device__ __forceinline__ FF ff_sqr(float x)
+{
+    const float p = __fmul_rn(x, x);
+    return FF{p, __fmaf_rn(x, x, -p)};
+}
+
+__device__ __forceinline__ FF ff_shfl_down(FF a, int o)
+{
+    return FF{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+
+__device__ __forceinline__ double ff_value(FF a) { return (double)a.hi + (double)a.lo; }
 
 }  // namespace tdpd

@@ -18,7 +18,6 @@ using namespace tdpd;
 
 namespace {
 
-constexpr int OBS_K = 5 + MAXS;
 constexpr int GRAPH_LONG = 16;   // steps per long graph (even: keeps the buffer parity)
 
 struct HostRbc {
@@ -42,6 +41,7 @@ struct HostRep {
     int n_free = 0;
     int64_t step = 0;
     int nc[3] = {0, 0, 0};
+    int m = 2;
 };
 
 struct Topo {
@@ -61,12 +61,17 @@ struct tdpd_sys {
     std::string err;
     cudaStream_t user = nullptr, own = nullptr, cap = nullptr;
     int N = 0, NC = 0, ns = 0, n_rbc = 0, max_nv = 0;
+    int lpp = 1;
     int parity = 0;
     int64_t step = 0;
     Buffers buf[2] = {};
     std::vector<void *> allocs;
     float4 *fext = nullptr;
     int *inv = nullptr, *count = nullptr, *cell_start = nullptr;
+    int *tile_sum[2] = {nullptr, nullptr};
+    int n_tiles = 0;
+    int4 *d_chunks = nullptr;
+    std::vector<int4> h_chunks;
     int2 *cellrank = nullptr, *keys = nullptr;
     uint32_t *errw = nullptr, *step_ctr = nullptr;
     RepParams *d_reps = nullptr;
@@ -240,6 +245,7 @@ RepParams make_params(const HostRep &R, int cell_base, int pbase, int n)
     }
     P.cell_base = cell_base;
     P.n_cells = R.nc[0] * R.nc[1] * R.nc[2];
+    P.m_stencil = R.m;
     P.pbase = pbase;
     P.n = n;
     P.wall_lo = c.wall_lo;
@@ -324,12 +330,14 @@ MemArgs mem_args(tdpd_sys *s, const Buffers &b, int ref_in)
     return m;
 }
 
-PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate)
+PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum)
 {
     PairArgs a{};
+    a.tile_sum = tile_sum;
     a.b = b; a.fext = s->fext; a.reps = s->d_reps; a.cell_start = s->cell_start; a.count = s->count;
     a.cellrank = s->cellrank; a.err = s->errw; a.step_ctr = s->step_ctr; a.n = s->N; a.ns = s->ns;
     a.integrate = integrate;
+    a.lpp = s->lpp;
     return a;
 }
 
@@ -350,7 +358,7 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
     int e = 0;
     auto mark = [&]() { if (ev) cudaEventRecordWithFlags(ev[e++], st, cudaEventRecordExternal); };
     mark();
-    launch_scan(s->count, s->cell_start, s->NC, s->step_ctr, 1, st);
+    launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[p], s->tile_sum[1 - p], s->step_ctr, 1, st);
     mark();
     launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st);
     mark();
@@ -363,7 +371,7 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         launch_mem_forces(m, st);
         mark();
     }
-    launch_pair(pair_args(s, nxt, 1), st);
+    launch_pair(pair_args(s, nxt, 1, s->tile_sum[1 - p]), st);
     mark();
 }
 
@@ -423,13 +431,15 @@ tdpd_status init_state(tdpd_sys *s)
     if (s->n_rbc && (rc = upload(s, s->d_ref[1], s->h_ref.data(), s->n_rbc))) return rc;
     CU(cudaMemsetAsync(s->buf[0].frc, 0, sizeof(float4) * N, st));
     CU(cudaMemsetAsync(s->buf[0].Q, 0, sizeof(float) * (size_t)N * ns, st));
-    CU(cudaMemsetAsync(s->count, 0, sizeof(int) * s->NC, st));
+    CU(cudaMemsetAsync(s->count, 0, sizeof(int) * (size_t)s->n_tiles * SCAN_TILE, st));
+    CU(cudaMemsetAsync(s->tile_sum[0], 0, sizeof(int) * s->n_tiles, st));
+    CU(cudaMemsetAsync(s->tile_sum[1], 0, sizeof(int) * s->n_tiles, st));
     CU(cudaMemsetAsync(s->errw, 0, sizeof(uint32_t) * s->reps.size(), st));
     CU(cudaMemsetAsync(s->fext, 0, sizeof(float4) * N, st));
     const uint32_t step32 = (uint32_t)s->step;
     if ((rc = upload(s, s->step_ctr, &step32, 1))) return rc;
-    launch_bin_init(s->buf[0], s->d_reps, N, s->count, s->cellrank, st);
-    launch_scan(s->count, s->cell_start, s->NC, s->step_ctr, 0, st);
+    launch_bin_init(s->buf[0], s->d_reps, N, s->count, s->tile_sum[0], s->cellrank, st);
+    launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[0], s->tile_sum[1], s->step_ctr, 0, st);
     launch_scatter_keys(s->buf[0], s->cellrank, s->cell_start, s->keys, N, st);
     launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0, st);
     if (s->n_rbc) {
@@ -437,10 +447,49 @@ tdpd_status init_state(tdpd_sys *s)
         launch_mem_gather(m, st);
         launch_mem_forces(m, st);
     }
-    launch_pair(pair_args(s, s->buf[1], 0), st);
+    launch_pair(pair_args(s, s->buf[1], 0, s->tile_sum[1]), st);
     CU(cudaGetLastError());
     s->parity = 1;
     return TDPD_OK;
+}
+
+// Pick the lanes per particle of the pair kernel by timing its forces-only
+// mode (idempotent apart from the next binning's counters) for each choice,
+// then rebuild the state with the winner.
+tdpd_status autotune(tdpd_sys *s)
+{
+    cudaStream_t st = exec_stream(s);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_lpp = s->lpp;
+    for (int lpp = 1; lpp <= 8; lpp *= 2) {
+        if (lpp > 1 && (long)s->N * lpp > 4000000L) break;
+        s->lpp = lpp;
+        const PairArgs a = pair_args(s, s->buf[1], 0, s->tile_sum[1]);
+        launch_pair(a, st);                       // warm-up
+        float tot = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            cudaEventRecord(e0, st);
+            launch_pair(a, st);
+            cudaEventRecord(e1, st);
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return fail(s, TDPD_ECUDA, "autotune: %s", cudaGetErrorString(e));
+            }
+            tot += ms;
+        }
+        if (tot < best) { best = tot; best_lpp = lpp; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->lpp = best_lpp;
+    return init_state(s);
 }
 
 tdpd_status capture(tdpd_sys *s, int p, int len, cudaGraphExec_t *out, cudaEvent_t *ev = nullptr)
@@ -476,10 +525,14 @@ tdpd_status commit(tdpd_sys *s)
         const int n = (int)R.type.size();
         if (n > TDPD_MAX_IDS) return fail(s, TDPD_EOVERFLOW, "replica %zu: %d particles exceed %d", r, n, TDPD_MAX_IDS);
         const float rcut = std::max(R.cfg.rc, R.cfg.rcc);
+        for (int c = 0; c < 3; ++c)
+            if ((double)R.cfg.L[c] < 3.0 * rcut * 1.0001)
+                return fail(s, TDPD_EINVAL, "replica %zu: box edge %g is shorter than 3 cut-offs (%g)", r, R.cfg.L[c], rcut);
+        // cells of edge >= rcut/m; a periodic axis needs 2m+1 distinct cells
+        R.m = 2;
         for (int c = 0; c < 3; ++c) {
-            R.nc[c] = (int)std::floor((double)R.cfg.L[c] / ((double)rcut * 1.0001));
-            if (R.nc[c] < 3)
-                return fail(s, TDPD_EINVAL, "replica %zu: box edge %g holds fewer than 3 cells of %g", r, R.cfg.L[c], rcut);
+            R.nc[c] = (int)std::floor((double)R.cfg.L[c] * R.m / ((double)rcut * 1.0001));
+            if (R.nc[c] < 2 * R.m + 1) return fail(s, TDPD_EINVAL, "replica %zu: too few cells", r);
         }
         const long ncells = (long)R.nc[0] * R.nc[1] * R.nc[2];
         if ((long)NC + ncells > (1L << 30)) return fail(s, TDPD_EOVERFLOW, "too many cells");
@@ -550,6 +603,16 @@ tdpd_status commit(tdpd_sys *s)
     }
     s->N = N;
     s->NC = NC;
+    s->n_tiles = (NC + SCAN_TILE - 1) / SCAN_TILE;
+    s->h_chunks.clear();
+    for (size_t r = 0; r < s->reps.size(); ++r) {
+        const int b0 = s->rep_pbase[r], n = (int)s->reps[r].type.size();
+        for (int k = 0; k < n || k == 0; k += OBS_CHUNK)
+            s->h_chunks.push_back(make_int4((int)r, b0 + k, b0 + std::min(n, k + OBS_CHUNK), 0));
+    }
+    // lanes per particle: enough threads to fill the GPU (~300k resident)
+    s->lpp = 1;
+    while (s->lpp < 8 && (long)N * s->lpp < 300000) s->lpp *= 2;
     s->n_rbc = (int)s->h_rbcs.size();
     s->max_nv = max_nv;
     if (N == 0) return fail(s, TDPD_ESTATE, "no particles loaded");
@@ -565,11 +628,20 @@ tdpd_status commit(tdpd_sys *s)
             return rc;
     }
     if ((rc = dalloc(s, &s->fext, N)) || (rc = dalloc(s, &s->inv, N)) || (rc = dalloc(s, &s->cellrank, N)) ||
-        (rc = dalloc(s, &s->keys, N)) || (rc = dalloc(s, &s->count, NC)) || (rc = dalloc(s, &s->cell_start, NC + 1)) ||
+        (rc = dalloc(s, &s->keys, N)) || (rc = dalloc(s, &s->count, (size_t)s->n_tiles * SCAN_TILE)) ||
+        (rc = dalloc(s, &s->cell_start, (size_t)s->n_tiles * SCAN_TILE + 1)) ||
+        (rc = dalloc(s, &s->tile_sum[0], s->n_tiles)) || (rc = dalloc(s, &s->tile_sum[1], s->n_tiles)) ||
+        (rc = dalloc(s, &s->d_chunks, s->h_chunks.size())) ||
         (rc = dalloc(s, &s->errw, s->reps.size())) || (rc = dalloc(s, &s->step_ctr, 1)) ||
-        (rc = dalloc(s, &s->d_reps, P.size())) || (rc = dalloc(s, &s->d_obs, OBS_K * s->reps.size())))
+        (rc = dalloc(s, &s->d_reps, P.size())) || (rc = dalloc(s, &s->d_obs, OBS_K * s->h_chunks.size())))
         return rc;
     if ((rc = upload(s, s->d_reps, P.data(), P.size()))) return rc;
+    if ((rc = upload(s, s->d_chunks, s->h_chunks.data(), s->h_chunks.size()))) return rc;
+    {
+        // the end of the last cell (and of the padding) is the particle count
+        std::vector<int> tail((size_t)s->n_tiles * SCAN_TILE + 1 - NC, N);
+        if ((rc = upload(s, s->cell_start + NC, tail.data(), tail.size()))) return rc;
+    }
     if (s->n_rbc) {
         std::vector<TopoDev> td;
         std::vector<int> tri, roff;
@@ -601,8 +673,8 @@ tdpd_status commit(tdpd_sys *s)
             return rc;
     }
     s->step = 0;
-    for (auto &R : s->reps) (void)R;
     if ((rc = init_state(s))) return rc;
+    if ((rc = autotune(s))) return rc;
     const int nk = (int)step_kernels(s).size();
     for (int k = 0; k <= nk; ++k) CU(cudaEventCreate(&s->ev[k]));
     s->n_ev = nk + 1;
@@ -979,10 +1051,16 @@ tdpd_status tdpd_read_observables(tdpd_sys *s, int r, tdpd_obs *out)
     HostRep *R = rep_of(s, r);
     if (!R || !out) return fail(s, TDPD_EINVAL, "bad replica or output");
     cudaStream_t st = exec_stream(s);
-    launch_observables(s->buf[s->parity], s->d_reps, (int)s->reps.size(), s->ns, s->d_obs, st);
-    double h[OBS_K];
-    CU(cudaMemcpyAsync(h, s->d_obs + (size_t)r * OBS_K, sizeof h, cudaMemcpyDeviceToHost, st));
+    int c0 = -1, c1 = -1;
+    for (size_t c = 0; c < s->h_chunks.size(); ++c)
+        if (s->h_chunks[c].x == r) { if (c0 < 0) c0 = (int)c; c1 = (int)c + 1; }
+    launch_observables(s->buf[s->parity], s->d_reps, s->d_chunks + c0, c1 - c0, s->ns, s->d_obs, st);
+    std::vector<double> part((size_t)(c1 - c0) * OBS_K);
+    CU(cudaMemcpyAsync(part.data(), s->d_obs, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
+    double h[OBS_K] = {};
+    for (int c = 0; c < c1 - c0; ++c)
+        for (int k = 0; k < OBS_K; ++k) h[k] += part[(size_t)c * OBS_K + k];
     std::memset(out, 0, sizeof *out);
     out->step = s->step + (s->reps.size() > 1 ? R->step : 0);
     out->n_particles = (int)R->type.size();

@@ -35,79 +35,61 @@ __device__ __forceinline__ float3 rel_pos(const RepParams &P, float4 x, float4 r
                        min_image(x.z - ref.z, P.L[2], P.periodic[2]));
 }
 
-__device__ __forceinline__ double shfl_down_d(double x, int o)
-{
-    return __shfl_down_sync(0xffffffffu, x, o);
-}
-
-// Block-wide reduction of K compensated sums in a fixed order; result in
-// thread 0.
-template <int K>
-__device__ void block_ksum(KSum (&v)[K])
-{
-    __shared__ double sh[32][K][2];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        for (int o = 16; o > 0; o >>= 1) {
-            KSum t;
-            t.s = shfl_down_d(v[k].s, o);
-            t.c = shfl_down_d(v[k].c, o);
-            if (lane + o < 32) ksum_merge(v[k], t);
-        }
-    if (lane == 0)
-        for (int k = 0; k < K; ++k) { sh[w][k][0] = v[k].s; sh[w][k][1] = v[k].c; }
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int ww = 1; ww < nw; ++ww)
-            for (int k = 0; k < K; ++k) {
-                KSum t;
-                t.s = sh[ww][k][0];
-                t.c = sh[ww][k][1];
-                ksum_merge(v[k], t);
-            }
-}
-
-__global__ void __launch_bounds__(256) k_mem_gather(MemArgs A)
+// K-Gather: each thread takes at most two triangles and one vertex; the
+// binary32 terms are reduced with compensated float-float sums (warp
+// shuffles, then one warp over the warp totals) and converted to binary64 once.
+__global__ void __launch_bounds__(1024) k_mem_gather(MemArgs A)
 {
     const int b = blockIdx.x;
     const RbcDev R = A.rbcs[b];
     const TopoDev T = A.topos[R.topo];
     const RepParams &P = A.reps[R.rep];
     const float4 ref = A.ref_in[b];
-    KSum acc[5];
-    for (int k = 0; k < 5; ++k) acc[k].s = acc[k].c = 0.0;
+    FF v[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = FF{0.0f, 0.0f};
     for (int t = threadIdx.x; t < T.ntri; t += blockDim.x) {
         const int *tv = A.tri + T.tri_off + 3 * t;
         const float3 x0 = rel_pos(P, A.pos[A.inv[R.gbase + tv[0]]], ref);
         const float3 x1 = rel_pos(P, A.pos[A.inv[R.gbase + tv[1]]], ref);
         const float3 x2 = rel_pos(P, A.pos[A.inv[R.gbase + tv[2]]], ref);
         const float3 n = cross(sub(x1, x0), sub(x2, x0));
-        acc[0].add(0.5 * (double)sqrtf(dot(n, n)));
-        acc[1].add((double)dot(x0, cross(x1, x2)) / 6.0);
+        v[0] = ff_add(v[0], 0.5f * sqrtf(dot(n, n)));
+        v[1] = ff_add(v[1], dot(x0, cross(x1, x2)) * (1.0f / 6.0f));
     }
-    for (int v = threadIdx.x; v < T.nv; v += blockDim.x) {
-        const float3 x = rel_pos(P, A.pos[A.inv[R.gbase + v]], ref);
-        acc[2].add(x.x);
-        acc[3].add(x.y);
-        acc[4].add(x.z);
+    for (int k = threadIdx.x; k < T.nv; k += blockDim.x) {
+        const float3 x = rel_pos(P, A.pos[A.inv[R.gbase + k]], ref);
+        v[2] = ff_add(v[2], x.x);
+        v[3] = ff_add(v[3], x.y);
+        v[4] = ff_add(v[4], x.z);
     }
-    block_ksum<5>(acc);
-    if (threadIdx.x == 0) {
-        A.av[b] = make_double2(acc[0].value(), acc[1].value());
+    __shared__ FF sh[32][5];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[k] = ff_add(v[k], ff_shfl_down(v[k], o));
+    if (lane == 0)
+        for (int k = 0; k < 5; ++k) sh[w][k] = v[k];
+    __syncthreads();
+    if (w != 0) return;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = lane < nw ? sh[lane][k] : FF{0.0f, 0.0f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[k] = ff_add(v[k], ff_shfl_down(v[k], o));
+    if (lane == 0) {
+        A.av[b] = make_double2(ff_value(v[0]), ff_value(v[1]));
         const double inv = 1.0 / T.nv;
-        float4 nr = ref;
-        nr.x = (float)(ref.x + acc[2].value() * inv);
-        nr.y = (float)(ref.y + acc[3].value() * inv);
-        nr.z = (float)(ref.z + acc[4].value() * inv);
-        for (int c = 0; c < 3; ++c) {
-            float *pc = c == 0 ? &nr.x : (c == 1 ? &nr.y : &nr.z);
+        float c3[3] = {(float)(ref.x + ff_value(v[2]) * inv), (float)(ref.y + ff_value(v[3]) * inv),
+                       (float)(ref.z + ff_value(v[4]) * inv)};
+        for (int c = 0; c < 3; ++c)
             if (P.periodic[c]) {
-                if (*pc < 0.0f) *pc += P.L[c];
-                else if (*pc >= P.L[c]) *pc -= P.L[c];
+                if (c3[c] < 0.0f) c3[c] += P.L[c];
+                else if (c3[c] >= P.L[c]) c3[c] -= P.L[c];
             }
-        }
-        A.ref_out[b] = nr;
+        A.ref_out[b] = make_float4(c3[0], c3[1], c3[2], 0.0f);
     }
 }
 
@@ -244,7 +226,7 @@ __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
 void launch_mem_gather(const MemArgs &a, cudaStream_t st)
 {
     if (a.n_rbc <= 0) return;
-    k_mem_gather<<<a.n_rbc, 256, 0, st>>>(a);
+    k_mem_gather<<<a.n_rbc, 1024, 0, st>>>(a);
 }
 
 void launch_mem_forces(const MemArgs &a, cudaStream_t st)

@@ -3,57 +3,45 @@
 
 namespace tdpd {
 
-// One CTA per replica: sums of v, |v|^2 and of the non-frozen count over the
-// non-frozen particles, and of each species over all particles. out holds,
-// per replica, [px, py, pz, v2, n_mobile, mass_0 .. mass_{ns-1}].
-template <int K>
-__device__ void block_reduce_ksum(KSum (&v)[K], double *out)
-{
-    __shared__ double sh[32][K][2];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = 0; k < K; ++k)
-        for (int o = 16; o > 0; o >>= 1) {
-            KSum t;
-            t.s = __shfl_down_sync(0xffffffffu, v[k].s, o);
-            t.c = __shfl_down_sync(0xffffffffu, v[k].c, o);
-            if (lane + o < 32) ksum_merge(v[k], t);
-        }
-    if (lane == 0)
-        for (int k = 0; k < K; ++k) { sh[w][k][0] = v[k].s; sh[w][k][1] = v[k].c; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int ww = 1; ww < nw; ++ww)
-            for (int k = 0; k < K; ++k) {
-                KSum t;
-                t.s = sh[ww][k][0];
-                t.c = sh[ww][k][1];
-                ksum_merge(v[k], t);
-            }
-        for (int k = 0; k < K; ++k) out[k] = v[k].value();
-    }
-}
-
-constexpr int OBS_K = 5 + MAXS;
-
+// One CTA per chunk of a replica's slots: compensated float-float sums of v,
+// |v|^2 (exact squares) and the non-frozen count over non-frozen particles,
+// and of each species over all particles; binary64 partials per chunk, which
+// the host adds in chunk order.
 __global__ void __launch_bounds__(256) k_observables(Buffers b, const RepParams *__restrict__ reps,
-                                                     int ns, double *out)
+                                                     const int4 *__restrict__ chunks, int ns,
+                                                     double *out)
 {
-    const RepParams &P = reps[blockIdx.x];
-    KSum acc[OBS_K];
-    for (int k = 0; k < OBS_K; ++k) acc[k].s = acc[k].c = 0.0;
-    for (int k = P.pbase + threadIdx.x; k < P.pbase + P.n; k += blockDim.x) {
+    const int4 ch = chunks[blockIdx.x];
+    const RepParams &P = reps[ch.x];
+    FF acc[OBS_K];
+#pragma unroll
+    for (int k = 0; k < OBS_K; ++k) acc[k] = FF{0.0f, 0.0f};
+    for (int k = ch.y + threadIdx.x; k < ch.z; k += blockDim.x) {
         const int type = (int)((uint32_t)wbits(b.pos[k].w) >> 24);
         if (!((P.frozen_mask >> type) & 1u)) {
             const float4 v = b.vel[k];
-            acc[0].add(v.x);
-            acc[1].add(v.y);
-            acc[2].add(v.z);
-            acc[3].add((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
-            acc[4].add(1.0);
+            acc[0] = ff_add(acc[0], v.x);
+            acc[1] = ff_add(acc[1], v.y);
+            acc[2] = ff_add(acc[2], v.z);
+            acc[3] = ff_add(ff_add(ff_add(acc[3], ff_sqr(v.x)), ff_sqr(v.y)), ff_sqr(v.z));
+            acc[4] = ff_add(acc[4], 1.0f);
         }
-        for (int s = 0; s < ns; ++s) acc[5 + s].add(b.C[(size_t)k * ns + s]);
+        for (int s = 0; s < ns; ++s) acc[5 + s] = ff_add(acc[5 + s], b.C[(size_t)k * ns + s]);
     }
-    block_reduce_ksum<OBS_K>(acc, out + (size_t)blockIdx.x * OBS_K);
+    __shared__ FF sh[8][OBS_K];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < OBS_K; ++k) acc[k] = ff_add(acc[k], ff_shfl_down(acc[k], o));
+    if (lane == 0)
+        for (int k = 0; k < OBS_K; ++k) sh[w][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < OBS_K) {
+        FF a = sh[0][threadIdx.x];
+        for (int ww = 1; ww < nw; ++ww) a = ff_add(a, sh[ww][threadIdx.x]);
+        out[(size_t)blockIdx.x * OBS_K + threadIdx.x] = ff_value(a);
+    }
 }
 
 __global__ void k_debug_rng(uint64_t seed, int n, const uint32_t *i, const uint32_t *j,
@@ -70,11 +58,11 @@ __global__ void k_debug_rng(uint64_t seed, int n, const uint32_t *i, const uint3
     normal[2 * k + 1] = g.y;
 }
 
-void launch_observables(const Buffers &b, const RepParams *reps, int n_rep, int ns, double *out,
-                        cudaStream_t st)
+void launch_observables(const Buffers &b, const RepParams *reps, const int4 *chunks, int n_chunks,
+                        int ns, double *out, cudaStream_t st)
 {
-    if (n_rep <= 0) return;
-    k_observables<<<n_rep, 256, 0, st>>>(b, reps, ns, out);
+    if (n_chunks <= 0) return;
+    k_observables<<<n_chunks, 256, 0, st>>>(b, reps, chunks, ns, out);
 }
 
 void launch_debug_rng(uint64_t seed, int n, const uint32_t *i, const uint32_t *j,

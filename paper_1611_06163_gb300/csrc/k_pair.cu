@@ -1,157 +1,325 @@
 // Pairwise tDPD force (Eq. 3) and Fickian flux (Eq. 6) over the cell list,
 // fused with the velocity-Verlet corrector and the binning of the next step.
 //
-// One thread owns one particle i (cell-sorted order) and sums its partners
-// over the 27 neighbouring cells, so F_i and Q_i are written once, without
-// atomics, in a fixed order. Each unordered pair is thus evaluated from both
-// sides; the pair random number is keyed on (min id, max id, step) so both
-// sides draw the same xi_ij and F_ij = -F_ji holds to rounding.
+// Layout of the work:
+//   - cells have edge >= rcut/m, so the partners of particle i lie in the
+//     (2m+1)^2 rows (dy, dz) of 2m+1 cells along x around its cell; a row is
+//     one contiguous range of the cell-sorted arrays (two at a periodic wrap);
+//   - LPP lanes share particle i and split its rows (lane s takes rows
+//     s, s+LPP, ...); a butterfly of shuffles sums their partial results in a
+//     fixed order, so small systems still fill the GPU;
+//   - the flux (about a quarter of the candidates) is summed inline by the
+//     lane that found it; the force pairs (a few per cent of the candidates,
+//     each needing a TEA draw) are pushed to a per-warp queue and evaluated
+//     32 at a time with every lane busy. Each owner adds its pairs' forces
+//     one by one in push order (that is, candidate order), so the sums do
+//     not depend on how particles are grouped into warps.
+// Every unordered pair is evaluated from both sides; the random number is
+// keyed on (min id, max id, step), so both sides draw the same xi_ij.
 #include "launch.h"
 
 namespace tdpd {
 
-template <int NS>
-__global__ void __launch_bounds__(128) k_pair(PairArgs A)
+namespace {
+
+constexpr int QCAP = 64;   // queue ring per warp (a push adds at most 32)
+
+struct __align__(16) QEntry {
+    int j;          // partner slot
+    uint32_t wj;    // partner id | type << 24
+    int owner;      // lane that owns particle i
+    int pad;
+    float dx, dy, dz, r2;
+};
+
+struct LaneInfo {
+    float4 vt;      // v~_i, w = bits(body)
+    uint32_t wi;    // id | type << 24
+    int rep;
+};
+
+struct WarpSmem {
+    QEntry q[QCAP];
+    float4 res[32];
+    float4 acc[32];
+    LaneInfo li[32];
+};
+
+// Force on the owner from one queued pair (zero if the pair is excluded).
+__device__ __forceinline__ float3 pair_force(const RepParams &P, const LaneInfo &I, const QEntry &E,
+                                             const float4 *__restrict__ vt, uint32_t step_ctr)
 {
+    const float4 vj = vt[E.j];
+    const int bi = wbits(I.vt.w), bj = wbits(vj.w);
+    if (P.exclude_same_body && bi >= 0 && bi == bj) return make_float3(0.f, 0.f, 0.f);
+    const float rinv = rsqrtf(E.r2);
+    const float r = E.r2 * rinv;
+    const float ex = E.dx * rinv, ey = E.dy * rinv, ez = E.dz * rinv;
+    const float w = 1.0f - r * P.inv_rc;
+    const float wR = P.sR_is1 ? w : __powf(w, P.sR);
+    const float ev = ex * (I.vt.x - vj.x) + ey * (I.vt.y - vj.y) + ez * (I.vt.z - vj.z);
+    const uint32_t step = step_ctr + P.step0;
+    const float xi = normal_cos(pair_bits(I.wi & ID_MASK, E.wj & ID_MASK, P.seed_lo, P.seed_hi, step, 0u));
+    const int T = P.ntypes;
+    const int tp = (int)(I.wi >> 24) * T + (int)(E.wj >> 24);
+    const float f = P.a[tp] * w - P.gamma[tp] * (wR * wR) * ev + P.sigma[tp] * wR * xi * P.inv_sqrt_dt;
+    return make_float3(f * ex, f * ey, f * ez);
+}
+
+// Evaluate queue entries [head, head+n) (n <= 32) and add each result to its
+// owner's accumulator in push order.
+__device__ __forceinline__ void drain(WarpSmem &W, int head, int n, const RepParams *__restrict__ reps,
+                                      const float4 *__restrict__ vt, uint32_t step_ctr, int lane)
+{
+    const bool act = lane < n;
+    int owner = 32 + lane;
+    if (act) {
+        const QEntry E = W.q[(head + lane) & (QCAP - 1)];
+        owner = E.owner;
+        const LaneInfo I = W.li[owner];
+        const float3 f = pair_force(reps[I.rep], I, E, vt, step_ctr);
+        W.res[lane] = make_float4(f.x, f.y, f.z, 0.f);
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, owner);
+    __syncwarp();
+    if (act && lane == __ffs(same) - 1) {
+        float4 a = W.acc[owner];
+        for (unsigned m = same; m; m &= m - 1) {
+            const float4 r = W.res[__ffs(m) - 1];
+            a.x += r.x;
+            a.y += r.y;
+            a.z += r.z;
+        }
+        W.acc[owner] = a;
+    }
+    __syncwarp();
+}
+
+}  // namespace
+
+template <int NS, int LPP>
+__global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
+{
+    __shared__ WarpSmem smem[4];
     const int ns = NS > 0 ? NS : A.ns;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n) return;
+    const int lane = threadIdx.x & 31;
+    WarpSmem &W = smem[threadIdx.x >> 5];
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / LPP;
+    const int sub = gt % LPP;
+    const bool valid = i < A.n;
     const float4 *__restrict__ pos = A.b.pos;
     const float4 *__restrict__ vt = A.b.vt;
     const float *__restrict__ Ct = A.b.Ct;
     const int *__restrict__ cs = A.cell_start;
+    const uint32_t step_ctr = *A.step_ctr;
 
-    const float4 pi = pos[i];
-    const float4 vi = vt[i];
-    const float4 vo = A.b.vel[i];
+    const int ic = valid ? i : 0;
+    const float4 pi = pos[ic];
+    const float4 vi = vt[ic];
+    const float4 vo = A.b.vel[ic];
     const int rep = wbits(vo.w);
     const RepParams &P = A.reps[rep];
     const uint32_t wi = (uint32_t)wbits(pi.w);
-    const uint32_t idi = wi & ID_MASK;
     const int ti = (int)(wi >> 24);
-    const int bi = wbits(vi.w);
-    const uint32_t step = *A.step_ctr + P.step0;
     const int T = P.ntypes;
+
+    W.li[lane].vt = vi;
+    W.li[lane].wi = wi;
+    W.li[lane].rep = rep;
+    W.acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     float ci[NS > 0 ? NS : MAXS];
     float q[NS > 0 ? NS : MAXS];
     for (int s = 0; s < ns; ++s) {
-        ci[s] = Ct[(size_t)i * ns + s];
+        ci[s] = Ct[(size_t)ic * ns + s];
         q[s] = 0.0f;
     }
-    float fx = 0.f, fy = 0.f, fz = 0.f;
 
+    const int m = P.m_stencil;
+    const int width = 2 * m + 1;
+    const int nrow = width * width;
     const int cx = cell_coord(pi.x, P.cell_scale[0], P.nc[0]);
     const int cy = cell_coord(pi.y, P.cell_scale[1], P.nc[1]);
     const int cz = cell_coord(pi.z, P.cell_scale[2], P.nc[2]);
-    const float rcut2 = P.rcut2, rc2 = P.rc2, rcc2 = P.rcc2;
+    const float rcut2 = P.rcut2, rc2 = P.rc2, rcc2 = P.rcc2, inv_rcc = P.inv_rcc;
+    const int sc2 = P.sc_is2;
+    const float s_c = P.s_c;
+    const float *kap_row = P.kappa + ti * T * ns;
 
-    for (int dz = -1; dz <= 1; ++dz) {
-        int z = cz + dz;
-        float sz = 0.f;
-        if (z < 0) { if (!P.periodic[2]) continue; z += P.nc[2]; sz = P.L[2]; }
-        else if (z >= P.nc[2]) { if (!P.periodic[2]) continue; z -= P.nc[2]; sz = -P.L[2]; }
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = cy + dy;
-            float sy = 0.f;
-            if (y < 0) { if (!P.periodic[1]) continue; y += P.nc[1]; sy = P.L[1]; }
-            else if (y >= P.nc[1]) { if (!P.periodic[1]) continue; y -= P.nc[1]; sy = -P.L[1]; }
-            for (int dx = -1; dx <= 1; ++dx) {
-                int x = cx + dx;
-                float sx = 0.f;
-                if (x < 0) { if (!P.periodic[0]) continue; x += P.nc[0]; sx = P.L[0]; }
-                else if (x >= P.nc[0]) { if (!P.periodic[0]) continue; x -= P.nc[0]; sx = -P.L[0]; }
-                const int c = P.cell_base + (z * P.nc[1] + y) * P.nc[0] + x;
-                const int jend = cs[c + 1];
-                for (int j = cs[c]; j < jend; ++j) {
-                    const float4 pj = pos[j];
-                    // difference first (exact for nearby coordinates), image shift after
-                    const float ddx = (pi.x - pj.x) + sx;
-                    const float ddy = (pi.y - pj.y) + sy;
-                    const float ddz = (pi.z - pj.z) + sz;
-                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (!(r2 < rcut2) || j == i || r2 == 0.0f) continue;
-                    const uint32_t wj = (uint32_t)wbits(pj.w);
-                    const int tj = (int)(wj >> 24);
-                    const float rinv = rsqrtf(r2);
-                    const float r = r2 * rinv;
-                    if (r2 < rcc2) {
-                        const float w = 1.0f - r * P.inv_rcc;
-                        const float wdc = P.sc_is2 ? w * w : __powf(w, P.s_c);
-                        const float *kap = P.kappa + (ti * T + tj) * ns;
-                        for (int s = 0; s < ns; ++s)
-                            q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
-                    }
-                    if (r2 < rc2) {
-                        const float4 vj = vt[j];
-                        const int bj = wbits(vj.w);
-                        if (P.exclude_same_body && bi >= 0 && bi == bj) continue;
-                        const float ex = ddx * rinv, ey = ddy * rinv, ez = ddz * rinv;
-                        const float w = 1.0f - r * P.inv_rc;
-                        const float wR = P.sR_is1 ? w : __powf(w, P.sR);
-                        const float ev = ex * (vi.x - vj.x) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
-                        const float xi = normal_cos(pair_bits(idi, wj & ID_MASK, P.seed_lo, P.seed_hi, step, 0u));
-                        const int tp = ti * T + tj;
-                        const float f = P.a[tp] * w - P.gamma[tp] * (wR * wR) * ev +
-                                        P.sigma[tp] * wR * xi * P.inv_sqrt_dt;
-                        fx += f * ex;
-                        fy += f * ey;
-                        fz += f * ez;
-                    }
+    __syncwarp();
+    int qhead = 0, qcount = 0;
+    // the row loop is warp-uniform: every lane runs the same number of
+    // iterations (up to the per-lane maximum), inactive lanes just vote
+    const int kmax = (nrow + LPP - 1) / LPP;
+    for (int k = 0; k < 64; ++k) {             // kmax <= 25; every lane leaves together
+        const bool more = valid && k < kmax;
+        if (!__any_sync(0xffffffffu, more)) break;
+        const int row = sub + k * LPP;
+        int jb[2] = {0, 0}, je[2] = {0, 0};
+        float sx[2] = {0.f, 0.f};
+        float sy = 0.f, sz = 0.f;
+        bool rok = more && row < nrow;
+        if (rok) {
+            const int dy = row % width - m, dz = row / width - m;
+            int y = cy + dy, z = cz + dz;
+            if (y < 0) { y += P.nc[1]; sy = P.L[1]; }
+            else if (y >= P.nc[1]) { y -= P.nc[1]; sy = -P.L[1]; }
+            if (z < 0) { if (P.periodic[2]) { z += P.nc[2]; sz = P.L[2]; } else rok = false; }
+            else if (z >= P.nc[2]) { if (P.periodic[2]) { z -= P.nc[2]; sz = -P.L[2]; } else rok = false; }
+            if (rok) {
+                const int base = P.cell_base + (z * P.nc[1] + y) * P.nc[0];
+                const int x0 = cx - m, x1 = cx + m, nx = P.nc[0];
+                if (x0 >= 0 && x1 < nx) {
+                    jb[0] = cs[base + x0];
+                    je[0] = cs[base + x1 + 1];
+                } else if (x0 < 0) {
+                    jb[0] = cs[base];
+                    je[0] = cs[base + x1 + 1];
+                    jb[1] = cs[base + nx + x0];
+                    je[1] = cs[base + nx];
+                    sx[1] = P.L[0];
+                } else {
+                    jb[0] = cs[base + x0];
+                    je[0] = cs[base + nx];
+                    jb[1] = cs[base];
+                    je[1] = cs[base + x1 - nx + 1];
+                    sx[1] = -P.L[0];
                 }
             }
         }
-    }
-
-    // ---- epilogue: membrane force, sources, corrector, next binning
-    if (bi >= 0) {
-        const float4 fm = A.fext[i];
-        fx += fm.x; fy += fm.y; fz += fm.z;
-    }
-    const bool frozen = (P.frozen_mask >> ti) & 1u;
-    if (!frozen) { fx += P.fbody[0]; fy += P.fbody[1]; fz += P.fbody[2]; }
-    if (P.k_react != 0.0f && ((P.react_mask >> ti) & 1u)) {
-        const float rate = P.k_react * ci[P.r_src];
-        q[P.r_src] -= rate;
-        q[P.r_dst] += rate;
-    }
-    if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(A.err + rep, 1u);
-
-    float4 vn = vo;
-    float *C = A.b.C, *Q = A.b.Q;
-    const float4 fo = A.b.frc[i];
-    if (A.integrate && !frozen) {
-        vn.x = __fmaf_rn(P.hdt, fo.x + fx, vo.x);
-        vn.y = __fmaf_rn(P.hdt, fo.y + fy, vo.y);
-        vn.z = __fmaf_rn(P.hdt, fo.z + fz, vo.z);
-        A.b.vel[i] = vn;
-        for (int s = 0; s < ns; ++s) {
-            const size_t k = (size_t)i * ns + s;
-            C[k] = __fmaf_rn(P.hdt, Q[k] + q[s], C[k]);
+#pragma unroll
+        for (int sg = 0; sg < 2; ++sg) {
+            const float px = pi.x + sx[sg], py = pi.y + sy, pz = pi.z + sz;
+            int j = jb[sg];
+            const int jend = je[sg];
+            while (true) {
+                const bool act = j < jend;
+                if (!__any_sync(0xffffffffu, act)) break;
+                bool push = false;
+                float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+                uint32_t wj = 0;
+                if (act) {
+                    const float4 pj = pos[j];
+                    dx = px - pj.x;
+                    dy = py - pj.y;
+                    dz = pz - pj.z;
+                    r2 = dx * dx + dy * dy + dz * dz;
+                    wj = (uint32_t)wbits(pj.w);
+                    if (r2 < rcut2 && r2 > 0.0f) {
+                        if (r2 < rcc2) {
+                            const float r = r2 * rsqrtf(r2);
+                            const float w = 1.0f - r * inv_rcc;
+                            const float wdc = sc2 ? w * w : __powf(w, s_c);
+                            const float *kap = kap_row + (int)(wj >> 24) * ns;
+                            for (int s = 0; s < ns; ++s)
+                                q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
+                        }
+                        push = r2 < rc2;
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, push);
+                if (push) {
+                    const int slot = (qhead + qcount + __popc(bal & ((1u << lane) - 1u))) & (QCAP - 1);
+                    int4 *e = reinterpret_cast<int4 *>(&W.q[slot]);
+                    e[0] = make_int4(j, (int)wj, lane, 0);
+                    e[1] = make_int4(__float_as_int(dx), __float_as_int(dy), __float_as_int(dz), __float_as_int(r2));
+                }
+                qcount += __popc(bal);
+                if (qcount >= 32) {
+                    __syncwarp();
+                    drain(W, qhead, 32, A.reps, vt, step_ctr, lane);
+                    qhead = (qhead + 32) & (QCAP - 1);
+                    qcount -= 32;
+                }
+                ++j;
+            }
         }
     }
-    const float4 fn = make_float4(fx, fy, fz, 0.0f);
-    A.b.frc[i] = fn;
-    for (int s = 0; s < ns; ++s) Q[(size_t)i * ns + s] = q[s];
-
-    float3 rn = make_float3(pi.x, pi.y, pi.z);
-    if (!frozen) {
-        bool flip;
-        rn = predict_pos(P, pi, vn, fn, flip);
+    if (qcount > 0) {
+        __syncwarp();
+        drain(W, qhead, qcount, A.reps, vt, step_ctr, lane);
     }
-    const int cell = cell_of(P, rn.x, rn.y, rn.z);
-    const int rank = atomicAdd(A.count + cell, 1);
-    A.cellrank[i] = make_int2(cell, rank);
+    __syncwarp();
+    const float4 fa = W.acc[lane];
+    float fx = fa.x, fy = fa.y, fz = fa.z;
+    // sum the LPP lanes of the particle (butterfly: every lane gets the total)
+#pragma unroll
+    for (int o = LPP / 2; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        for (int s = 0; s < ns; ++s) q[s] += __shfl_xor_sync(0xffffffffu, q[s], o);
+    }
+    int cell = -1;
+    if (valid && sub == 0) {
+        // ---- epilogue: membrane force, sources, corrector, next binning
+        const int bi = wbits(vi.w);
+        if (bi >= 0) {
+            const float4 fm = A.fext[i];
+            fx += fm.x; fy += fm.y; fz += fm.z;
+        }
+        const bool frozen = (P.frozen_mask >> ti) & 1u;
+        if (!frozen) { fx += P.fbody[0]; fy += P.fbody[1]; fz += P.fbody[2]; }
+        if (P.k_react != 0.0f && ((P.react_mask >> ti) & 1u)) {
+            const float rate = P.k_react * Ct[(size_t)i * ns + P.r_src];
+            for (int s = 0; s < ns; ++s) {
+                if (s == P.r_src) q[s] -= rate;
+                if (s == P.r_dst) q[s] += rate;
+            }
+        }
+        if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(A.err + rep, 1u);
+
+        float4 vn = vo;
+        float *C = A.b.C, *Q = A.b.Q;
+        const float4 fo = A.b.frc[i];
+        if (A.integrate && !frozen) {
+            vn.x = __fmaf_rn(P.hdt, fo.x + fx, vo.x);
+            vn.y = __fmaf_rn(P.hdt, fo.y + fy, vo.y);
+            vn.z = __fmaf_rn(P.hdt, fo.z + fz, vo.z);
+            A.b.vel[i] = vn;
+            for (int s = 0; s < ns; ++s) {
+                const size_t k = (size_t)i * ns + s;
+                C[k] = __fmaf_rn(P.hdt, Q[k] + q[s], C[k]);
+            }
+        }
+        const float4 fn = make_float4(fx, fy, fz, 0.0f);
+        A.b.frc[i] = fn;
+        for (int s = 0; s < ns; ++s) Q[(size_t)i * ns + s] = q[s];
+
+        float3 rn = make_float3(pi.x, pi.y, pi.z);
+        if (!frozen) {
+            bool flip;
+            rn = predict_pos(P, pi, vn, fn, flip);
+        }
+        cell = cell_of(P, rn.x, rn.y, rn.z);
+        const int rank = atomicAdd(A.count + cell, 1);
+        A.cellrank[i] = make_int2(cell, rank);
+    }
+    add_tile_count(A.tile_sum, cell);
+}
+
+template <int NS>
+static void launch_ns(const PairArgs &a, cudaStream_t st)
+{
+    const int t = 128;
+    const long threads = (long)a.n * a.lpp;
+    const int g = (int)((threads + t - 1) / t);
+    switch (a.lpp) {
+    case 1: k_pair<NS, 1><<<g, t, 0, st>>>(a); break;
+    case 2: k_pair<NS, 2><<<g, t, 0, st>>>(a); break;
+    case 4: k_pair<NS, 4><<<g, t, 0, st>>>(a); break;
+    default: k_pair<NS, 8><<<g, t, 0, st>>>(a); break;
+    }
 }
 
 void launch_pair(const PairArgs &a, cudaStream_t st)
 {
     if (a.n <= 0) return;
-    const int t = 128, g = (a.n + t - 1) / t;
     switch (a.ns) {
-    case 1: k_pair<1><<<g, t, 0, st>>>(a); break;
-    case 2: k_pair<2><<<g, t, 0, st>>>(a); break;
-    default: k_pair<0><<<g, t, 0, st>>>(a); break;
+    case 1: launch_ns<1>(a, st); break;
+    case 2: launch_ns<2>(a, st); break;
+    default: launch_ns<0>(a, st); break;
     }
 }
 

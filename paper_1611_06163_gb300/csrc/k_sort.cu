@@ -9,58 +9,77 @@
 namespace tdpd {
 
 __global__ void k_bin_init(Buffers b, const RepParams *__restrict__ reps, int n, int *count,
-                           int2 *cellrank)
+                           int *tile_sum, int2 *cellrank)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    float4 p = b.pos[k];
-    int r = wbits(b.vel[k].w);
-    const RepParams &P = reps[r];
-    int c = cell_of(P, p.x, p.y, p.z);
-    int rank = atomicAdd(count + c, 1);
-    cellrank[k] = make_int2(c, rank);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = -1;
+    if (k < n) {
+        const float4 p = b.pos[k];
+        const RepParams &P = reps[wbits(b.vel[k].w)];
+        c = cell_of(P, p.x, p.y, p.z);
+        const int rank = atomicAdd(count + c, 1);
+        cellrank[k] = make_int2(c, rank);
+    }
+    add_tile_count(tile_sum, c);
 }
 
-// Single-CTA exclusive scan of the cell histogram; clears it for the next
-// binning and advances the step counter.
-__global__ void __launch_bounds__(1024) k_scan(int *count, int *cell_start, int n_cells,
-                                               uint32_t *step_ctr, int inc)
+// Exclusive scan of the cell histogram over all replicas at once (replicas
+// occupy consecutive cells and consecutive slots, so one global scan gives
+// every replica's cell_start). One CTA per tile of SCAN_TILE cells; the tile
+// totals were accumulated by the binning, so each CTA finds its offset by
+// summing the totals of the tiles before it -- no inter-CTA waiting.
+__global__ void __launch_bounds__(1024) k_scan(int *count, int *cell_start, const int *tile_read,
+                                               int *tile_clear, uint32_t *step_ctr, int inc)
 {
     __shared__ int wsum[32];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int per = (n_cells + nt - 1) / nt;
-    const int beg = min(tid * per, n_cells), end = min(beg + per, n_cells);
-    int s = 0;
-    for (int c = beg; c < end; ++c) s += count[c];
-    // inclusive scan over the block
+    __shared__ int base_sh;
+    const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    // offset of this tile
+    int pre = 0;
+    for (int u = tid; u < t; u += blockDim.x) pre += tile_read[u];
+    for (int o = 16; o > 0; o >>= 1) pre += __shfl_down_sync(0xffffffffu, pre, o);
+    if (lane == 0) wsum[w] = pre;
+    __syncthreads();
+    if (w == 0) {
+        int v = wsum[lane];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) base_sh = v;
+    }
+    __syncthreads();
+    const int base = base_sh;
+    // four consecutive cells per thread
+    int4 *c4 = reinterpret_cast<int4 *>(count + (size_t)t * SCAN_TILE) + tid;
+    const int4 cnt = *c4;
+    const int s = cnt.x + cnt.y + cnt.z + cnt.w;
     int x = s;
-    const int lane = tid & 31, w = tid >> 5;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
+    __syncthreads();
     if (lane == 31) wsum[w] = x;
     __syncthreads();
     if (w == 0) {
-        int v = lane < (nt >> 5) ? wsum[lane] : 0;
+        int v = wsum[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, v, o);
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
             if (lane >= o) v += y;
         }
         wsum[lane] = v;
     }
     __syncthreads();
-    int run = x - s + (w > 0 ? wsum[w - 1] : 0);
-    for (int c = beg; c < end; ++c) {
-        int v = count[c];
-        cell_start[c] = run;
-        run += v;
-        count[c] = 0;
-    }
-    if (tid == nt - 1) cell_start[n_cells] = run;
-    if (tid == 0 && inc) *step_ctr += 1u;
+    const int e = base + x - s + (w > 0 ? wsum[w - 1] : 0);
+    int4 out;
+    out.x = e;
+    out.y = e + cnt.x;
+    out.z = out.y + cnt.y;
+    out.w = out.z + cnt.z;
+    reinterpret_cast<int4 *>(cell_start + (size_t)t * SCAN_TILE)[tid] = out;
+    *c4 = make_int4(0, 0, 0, 0);
+    if (tid == 0) tile_clear[t] = 0;
+    if (t == 0 && tid == 0 && inc) *step_ctr += 1u;
 }
 
 __global__ void k_scatter_keys(const float4 *__restrict__ pos, const int2 *__restrict__ cellrank,
@@ -127,17 +146,18 @@ __global__ void k_rank_gather(Buffers cur, Buffers nxt, const RepParams *__restr
 
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
-void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count, int2 *cellrank,
-                     cudaStream_t st)
+void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum,
+                     int2 *cellrank, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_bin_init<<<nblk(n, 256), 256, 0, st>>>(b, reps, n, count, cellrank);
+    k_bin_init<<<nblk(n, 256), 256, 0, st>>>(b, reps, n, count, tile_sum, cellrank);
 }
 
-void launch_scan(int *count, int *cell_start, int n_cells, uint32_t *step_ctr, int inc,
-                 cudaStream_t st)
+void launch_scan(int *count, int *cell_start, int n_tiles, const int *tile_read, int *tile_clear,
+                 uint32_t *step_ctr, int inc, cudaStream_t st)
 {
-    k_scan<<<1, 1024, 0, st>>>(count, cell_start, n_cells, step_ctr, inc);
+    static_assert(SCAN_TILE == 4 * 1024, "one CTA of 1024 threads scans four cells per thread");
+    k_scan<<<n_tiles, 1024, 0, st>>>(count, cell_start, tile_read, tile_clear, step_ctr, inc);
 }
 
 void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *cell_start,

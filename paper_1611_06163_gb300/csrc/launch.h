@@ -8,6 +8,9 @@
 
 namespace tdpd {
 
+constexpr int OBS_K = 5 + MAXS;   // px, py, pz, sum v^2, n_mobile, species totals
+constexpr int OBS_CHUNK = 8192;   // slots per observables CTA
+
 struct Buffers {
     float4 *pos, *vt, *vel, *frc;
     float *C, *Ct, *Q;
@@ -20,11 +23,13 @@ struct PairArgs {
     const int *cell_start;       // [NC+1]
     int *count;                  // [NC] histogram of the next binning (zeroed by scan)
     int2 *cellrank;              // [N] (cell, rank) of the next binning
+    int *tile_sum;               // [n_tiles] particles per scan tile of the next binning
     uint32_t *err;               // [n_rep] status bits
     const uint32_t *step_ctr;    // absolute step of this evaluation
     int n;                       // particles (slots)
     int ns;                      // species (runtime value for the generic path)
     int integrate;               // 0: forces only (commit / set_state); 1: full step
+    int lpp;                     // lanes per particle: 1, 2, 4 or 8
 };
 
 struct MemArgs {
@@ -47,10 +52,12 @@ struct MemArgs {
     int n_rbc, max_nv;
 };
 
-void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count, int2 *cellrank,
-                     cudaStream_t st);
-void launch_scan(int *count, int *cell_start, int n_cells, uint32_t *step_ctr, int inc,
-                 cudaStream_t st);
+void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum,
+                     int2 *cellrank, cudaStream_t st);
+// exclusive scan of count[0, n_tiles * SCAN_TILE) into cell_start; reads the
+// tile totals tile_read, clears tile_clear and count for the next binning
+void launch_scan(int *count, int *cell_start, int n_tiles, const int *tile_read, int *tile_clear,
+                 uint32_t *step_ctr, int inc, cudaStream_t st);
 void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *cell_start,
                          int2 *keys, int n, cudaStream_t st);
 void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams *reps,
@@ -59,8 +66,9 @@ void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams 
 void launch_pair(const PairArgs &a, cudaStream_t st);
 void launch_mem_gather(const MemArgs &a, cudaStream_t st);
 void launch_mem_forces(const MemArgs &a, cudaStream_t st);
-void launch_observables(const Buffers &b, const RepParams *reps, int n_rep, int ns,
-                        double *out, cudaStream_t st);
+// chunks: (replica, first slot, end slot); out: OBS_K doubles per chunk
+void launch_observables(const Buffers &b, const RepParams *reps, const int4 *chunks, int n_chunks,
+                        int ns, double *out, cudaStream_t st);
 void launch_debug_rng(uint64_t seed, int n, const uint32_t *i, const uint32_t *j,
                       const uint32_t *step, const uint32_t *stream, uint32_t *bits,
                       float *normal, cudaStream_t st);

@@ -149,15 +149,15 @@ def test_membrane_straddling_periodic_boundary():
 def test_edge_positions_and_single_particle():
     """Particles on cell and box boundaries (x = 0, x just below L), and a
     one-particle box whose force is the body force alone."""
-    L = 6.0
+    L = 7.0                       # 8 cells of 0.875 (edge >= rcc/2) per axis
     top = float(np.nextafter(np.float32(L), np.float32(0)))
     rng = np.random.default_rng(8)
-    n = 500
+    n = 900
     pos = rng.random((n, 3)) * L
     pos[:40, 0] = 0.0
     pos[40:80, 1] = top
-    pos[80:120, 2] = 2.0          # exactly on a cell face (3 cells of 2.0)
-    pos[120:160] = [0.0, top, 4.0]
+    pos[80:120, 2] = 2.625        # exactly on a cell face
+    pos[120:160] = [0.0, top, 4.375]
     pos[120:160, 0] += np.arange(40) * 0.01
     d = custom(pos, rng.normal(0, 1, (n, 3)), rng.random((n, 1)), L=(L, L, L))
     F, Q, Fo, Qo = forces_vs_oracle(d, mode=0)
@@ -237,3 +237,48 @@ def test_replica_ensemble_matches_oracle():
         F, Q, Fo, Qo = forces_vs_oracle(r, mode=1)
         assert normwise(F, Fo) < TOL_FORCE
         assert normwise(Q, Qo) < TOL_FORCE
+
+
+def test_channel_walls_reaction_full_size():
+    """RBC suspension in a z-walled channel (236k particles, 40 membranes,
+    frozen wall particles, bounce-back, 2 species with A->B reaction, body
+    force): forces at step 0 and 10 steps against the oracle."""
+    d = W.rbc_channel()
+    F, Q, Fo, Qo = forces_vs_oracle(d, mode=1)
+    assert normwise(F, Fo) < TOL_FORCE
+    assert normwise(Q, Qo) < TOL_FORCE
+    err, obs, o, (A, V) = run_vs_oracle(d, 10)
+    for k, v in err.items():
+        assert v < TOL_TRAJ, (k, v, err)
+    ob = o.observables()
+    assert np.allclose(A, ob['area'], rtol=1e-6)
+    assert np.allclose(V, ob['volume'], rtol=1e-6)
+    # species total changes only through the reaction (flux conserves it)
+    assert np.allclose(obs['mass'], ob['mass'], rtol=1e-5)
+
+
+def test_ensemble_512_sampled_against_oracle():
+    """The full 512-replica ensemble batched in one handle: the forces of a
+    sample of replicas (smallest, largest, with and without membranes) match
+    the oracle run on each replica alone."""
+    bd = B()
+    reps = W.replica_ensemble(n_rep=512)
+    hs = [bd.create_from(r) for r in reps]
+    batch = bd.tdpd_batch_create(hs)
+    for h in hs:
+        bd.tdpd_destroy(h)
+    try:
+        bd.tdpd_commit(batch)
+        sizes = [W.n_particles(r) for r in reps]
+        nrbc = [len(r['rbcs']) for r in reps]
+        pick = {int(np.argmin(sizes)), int(np.argmax(sizes)), nrbc.index(0), nrbc.index(max(nrbc)), 255}
+        for k in sorted(pick):
+            F, Q = bd.tdpd_read_forces(batch, k, 1)
+            o = oracle.Oracle(reps[k], mode=1)
+            assert normwise(F, o.F) < TOL_FORCE, k
+            assert normwise(Q, o.Q) < TOL_FORCE, k
+        bd.tdpd_step(batch, 3)
+        bd.tdpd_sync(batch)
+        assert (bd.tdpd_replica_status(batch) == 0).all()
+    finally:
+        bd.tdpd_destroy(batch)
