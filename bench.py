@@ -184,6 +184,8 @@ def run_native(args):
     from paper_1611_06163_gb300 import binding as bd
 
     descs = WORKLOADS[args.workload][1](rank)
+    for d in descs:
+        d['cells_per_cutoff'] = args.cells_per_cutoff
     n = sum(W.n_mobile(d) for d in descs)
     stream = torch.cuda.Stream()
     if len(descs) == 1:
@@ -316,6 +318,8 @@ def main():
     ap.add_argument('--cpu-seconds', type=float, default=12.0)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='single_rbc', choices=sorted(WORKLOADS))
+    ap.add_argument('--cells-per-cutoff', type=int, default=0,
+                    help='cell-list stencil width m (cells of edge >= rcut/m); 0 = library default')
     args = ap.parse_args()
     if args.impl == 'reference':
         return run_reference(args)

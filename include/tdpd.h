@@ -70,6 +70,8 @@ typedef struct {
     float body_force[3];        /* added to every non-frozen particle */
     uint32_t frozen_types;      /* bit t: particles of type t are not moved */
     int32_t exclude_same_body;  /* 1: no Eq. 3 forces within one membrane */
+    int32_t cells_per_cutoff;   /* cell-list stencil: cells of edge >= max(rc, rcc)/m,
+                                 * m = 2 or 3; 0 selects 2 */
 } tdpd_config;
 
 /* Membrane constants (Sec. 2.2). Bond l_m = l0/x0 and k_p are set per bond

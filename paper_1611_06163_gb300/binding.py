@@ -35,7 +35,8 @@ class tdpd_config(C.Structure):
                 ('n_types', C.c_int32), ('n_species', C.c_int32), ('seed', C.c_uint64),
                 ('dt', C.c_float), ('lam', C.c_float), ('rc', C.c_float), ('s_f', C.c_float),
                 ('rcc', C.c_float), ('s_c', C.c_float), ('body_force', C.c_float * 3),
-                ('frozen_types', C.c_uint32), ('exclude_same_body', C.c_int32)]
+                ('frozen_types', C.c_uint32), ('exclude_same_body', C.c_int32),
+                ('cells_per_cutoff', C.c_int32)]
 
 
 class tdpd_membrane(C.Structure):
@@ -281,6 +282,7 @@ def config_from(desc) -> tdpd_config:
     c.body_force[:] = [float(x) for x in desc['body_force']]
     c.frozen_types = int(desc['frozen_types'])
     c.exclude_same_body = int(desc['exclude_same_body'])
+    c.cells_per_cutoff = int(desc.get('cells_per_cutoff', 0))
     return c
 
 

@@ -26,6 +26,7 @@ constexpr int SCAN_TILE = 1 << SCAN_TILE_LOG2;
 struct RepParams {
     float L[3];
     float cell_scale[3];     // cells per unit length (nc / L)
+    float h[3];              // cell edge (L / nc)
     int nc[3];
     int periodic[3];
     int cell_base, n_cells;  // global cell index range of the replica

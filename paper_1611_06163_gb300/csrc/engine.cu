@@ -240,6 +240,7 @@ RepParams make_params(const HostRep &R, int cell_base, int pbase, int n)
         P.L[k] = c.L[k];
         P.nc[k] = R.nc[k];
         P.cell_scale[k] = (float)((double)R.nc[k] / (double)c.L[k]);
+        P.h[k] = (float)((double)c.L[k] / (double)R.nc[k]);
         P.periodic[k] = c.periodic[k];
         P.fbody[k] = c.body_force[k];
     }
@@ -529,7 +530,7 @@ tdpd_status commit(tdpd_sys *s)
             if ((double)R.cfg.L[c] < 3.0 * rcut * 1.0001)
                 return fail(s, TDPD_EINVAL, "replica %zu: box edge %g is shorter than 3 cut-offs (%g)", r, R.cfg.L[c], rcut);
         // cells of edge >= rcut/m; a periodic axis needs 2m+1 distinct cells
-        R.m = 2;
+        R.m = R.cfg.cells_per_cutoff > 0 ? R.cfg.cells_per_cutoff : 2;
         for (int c = 0; c < 3; ++c) {
             R.nc[c] = (int)std::floor((double)R.cfg.L[c] * R.m / ((double)rcut * 1.0001));
             if (R.nc[c] < 2 * R.m + 1) return fail(s, TDPD_EINVAL, "replica %zu: too few cells", r);
@@ -747,6 +748,7 @@ tdpd_status check_config(tdpd_sys *s, const tdpd_config *c)
     if (!(c->rc > 0) || !(c->rcc >= 0)) return fail(s, TDPD_EINVAL, "cut-offs: rc > 0, rcc >= 0");
     if (!(c->s_f > 0) || !(c->s_c > 0)) return fail(s, TDPD_EINVAL, "weight exponents must be positive");
     if (c->frozen_types >> c->n_types) return fail(s, TDPD_EINVAL, "frozen_types names a type >= n_types");
+    if (c->cells_per_cutoff < 0 || c->cells_per_cutoff > 3) return fail(s, TDPD_EINVAL, "cells_per_cutoff must be 0, 1, 2 or 3");
     return TDPD_OK;
 }
 

@@ -146,30 +146,48 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
     const int sc2 = P.sc_is2;
     const float s_c = P.s_c;
     const float *kap_row = P.kappa + ti * T * ns;
+    // one species: the kappa row of type ti in registers
+    float kr[MAXT] = {0.f, 0.f, 0.f, 0.f};
+    if (NS == 1)
+        for (int t = 0; t < T; ++t) kr[t] = kap_row[t];
+    // offsets of particle i inside its own cell, for trimming the rows
+    const float hx = P.h[0], hy = P.h[1], hz = P.h[2];
+    const float oy = pi.y - (float)cy * hy, oz = pi.z - (float)cz * hz;
+    const float eps = 1e-4f * fmaxf(hx, fmaxf(hy, hz));
+    const float rtrim2 = rcut2 * 1.0002f;
 
     __syncwarp();
     int qhead = 0, qcount = 0;
-    // the row loop is warp-uniform: every lane runs the same number of
-    // iterations (up to the per-lane maximum), inactive lanes just vote
+    // rows are split round-robin over the LPP lanes of the particle; the loop
+    // trip counts are warp-uniform (maxima over the warp)
     const int kmax = (nrow + LPP - 1) / LPP;
-    for (int k = 0; k < 64; ++k) {             // kmax <= 25; every lane leaves together
-        const bool more = valid && k < kmax;
-        if (!__any_sync(0xffffffffu, more)) break;
+    const int kw = __reduce_max_sync(0xffffffffu, valid ? kmax : 0);
+    for (int k = 0; k < kw; ++k) {
         const int row = sub + k * LPP;
         int jb[2] = {0, 0}, je[2] = {0, 0};
         float sx[2] = {0.f, 0.f};
         float sy = 0.f, sz = 0.f;
-        bool rok = more && row < nrow;
+        bool rok = valid && row < nrow;
         if (rok) {
             const int dy = row % width - m, dz = row / width - m;
+            // distance from particle i to the slab of the row's cells, minus a
+            // margin for the rounding of the cell assignment
+            const float ay = dy == 0 ? 0.f : (dy > 0 ? (float)dy * hy - oy : oy - (float)(dy + 1) * hy);
+            const float az = dz == 0 ? 0.f : (dz > 0 ? (float)dz * hz - oz : oz - (float)(dz + 1) * hz);
+            const float by = fmaxf(ay - eps, 0.f), bz = fmaxf(az - eps, 0.f);
+            const float rem = rtrim2 - by * by - bz * bz;
             int y = cy + dy, z = cz + dz;
+            if (rem <= 0.f) rok = false;
             if (y < 0) { y += P.nc[1]; sy = P.L[1]; }
             else if (y >= P.nc[1]) { y -= P.nc[1]; sy = -P.L[1]; }
             if (z < 0) { if (P.periodic[2]) { z += P.nc[2]; sz = P.L[2]; } else rok = false; }
             else if (z >= P.nc[2]) { if (P.periodic[2]) { z -= P.nc[2]; sz = -P.L[2]; } else rok = false; }
             if (rok) {
+                const float rx = sqrtf(rem) + eps;
+                const int x0 = max(cx - m, __float2int_rd((pi.x - rx) * P.cell_scale[0]));
+                const int x1 = min(cx + m, __float2int_rd((pi.x + rx) * P.cell_scale[0]));
                 const int base = P.cell_base + (z * P.nc[1] + y) * P.nc[0];
-                const int x0 = cx - m, x1 = cx + m, nx = P.nc[0];
+                const int nx = P.nc[0];
                 if (x0 >= 0 && x1 < nx) {
                     jb[0] = cs[base + x0];
                     je[0] = cs[base + x1 + 1];
@@ -191,15 +209,15 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
 #pragma unroll
         for (int sg = 0; sg < 2; ++sg) {
             const float px = pi.x + sx[sg], py = pi.y + sy, pz = pi.z + sz;
-            int j = jb[sg];
-            const int jend = je[sg];
-            while (true) {
-                const bool act = j < jend;
-                if (!__any_sync(0xffffffffu, act)) break;
+            const int j0 = jb[sg];
+            const int len = je[sg] - j0;
+            const int nit = __reduce_max_sync(0xffffffffu, len);
+            for (int t = 0; t < nit; ++t) {
+                const int j = j0 + t;
                 bool push = false;
                 float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
                 uint32_t wj = 0;
-                if (act) {
+                if (t < len) {
                     const float4 pj = pos[j];
                     dx = px - pj.x;
                     dy = py - pj.y;
@@ -211,9 +229,18 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
                             const float r = r2 * rsqrtf(r2);
                             const float w = 1.0f - r * inv_rcc;
                             const float wdc = sc2 ? w * w : __powf(w, s_c);
-                            const float *kap = kap_row + (int)(wj >> 24) * ns;
-                            for (int s = 0; s < ns; ++s)
-                                q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
+                            const int tj = (int)(wj >> 24);
+                            if (NS == 1) {
+                                float kap = kr[0];
+                                if (tj == 1) kap = kr[1];
+                                else if (tj == 2) kap = kr[2];
+                                else if (tj == 3) kap = kr[3];
+                                q[0] -= kap * wdc * (ci[0] - Ct[j]);
+                            } else {
+                                const float *kap = kap_row + tj * ns;
+                                for (int s = 0; s < ns; ++s)
+                                    q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
+                            }
                         }
                         push = r2 < rc2;
                     }
@@ -232,7 +259,6 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
                     qhead = (qhead + 32) & (QCAP - 1);
                     qcount -= 32;
                 }
-                ++j;
             }
         }
     }
