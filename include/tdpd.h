@@ -196,6 +196,51 @@ tdpd_status tdpd_debug_rng(uint64_t seed, int n, const uint32_t *i, const uint32
                            const uint32_t *step, const uint32_t *stream,
                            uint32_t *bits, float *normal);
 
+/* ------------------------------------------------ allocation-free variant */
+
+/* Limits of tdpd_pair_forces_noalloc; its scratch is a fixed device array of
+ * at most TDPD_NOALLOC_SCRATCH_BYTES that every GPU which loads this library
+ * holds until the process exits. */
+#define TDPD_NOALLOC_MAX_PARTICLES 16384
+#define TDPD_NOALLOC_MAX_CELLS 16384
+#define TDPD_NOALLOC_MAX_SPECIES 4
+#define TDPD_NOALLOC_SCRATCH_BYTES (5u << 20)
+
+/* Pair force and flux of one periodic box, computed without allocating or
+ * freeing any memory. The paper has no counterpart: this serves callers that
+ * cannot call cudaMalloc -- a host program that hands all device memory to its
+ * own pool allocator, or a per-step callback inside another simulation
+ * engine, where an allocation would synchronise the device or is not allowed.
+ * Such a caller owns every buffer it passes; everything else this call needs
+ * lives in one fixed scratch array inside the library.
+ *
+ * Computes, for n free particles (no membranes) of a box with every axis
+ * periodic, the force F^C + F^D + F^R (Eq. 3) plus body force and the flux
+ * Q^D (Eq. 6) plus reaction source at step number `step`, with the same
+ * kernels and random numbers as tdpd_commit followed by tdpd_read_forces.
+ *   cfg        host; box, species, cut-offs, seed (every axis periodic)
+ *   pair_coef  host float[n_types*n_types*3]: a, gamma, sigma per type pair
+ *   kappa      host float[n_types*n_types*n_species]
+ *   pos, vel   device float[n*3]; positions in [0, L)
+ *   conc       device float[n*n_species]
+ *   type       device int32[n]
+ *   force      device float[n*3] (written), flux device float[n*n_species] (written)
+ *   stream     cudaStream_t on which the work is enqueued (NULL: default stream)
+ * Limits: n <= TDPD_NOALLOC_MAX_PARTICLES, cells (edge >= max(rc, rcc)/m) <=
+ * TDPD_NOALLOC_MAX_CELLS, n_species <= TDPD_NOALLOC_MAX_SPECIES; larger inputs
+ * return TDPD_EINVAL with the reason in tdpd_last_error(NULL), before any
+ * device work. The call only enqueues (no synchronisation, no device-side
+ * status is returned). The first call on a device looks up the scratch
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. Every call on a device
+ * reuses the same scratch, which keeps the previous call's contents (the call
+ * clears what must start at zero): calls whose work overlaps on the GPU --
+ * from several streams or threads -- race and must be serialised by the caller. */
+tdpd_status tdpd_pair_forces_noalloc(const tdpd_config *cfg, const float *pair_coef,
+                                     const float *kappa, int n, const float *pos, const float *vel,
+                                     const float *conc, const int32_t *type, uint32_t step,
+                                     float *force, float *flux, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,7 @@ def _load():
         'tdpd_debug_rng': ([C.c_uint64, I, P, P, P, P, P, P], I),
         'tdpd_step_timed': ([P, P, I, C.POINTER(I)], I),
         'tdpd_kernel_name': ([P, I], C.c_char_p),
+        'tdpd_pair_forces_noalloc': ([C.POINTER(tdpd_config), P, P, I, P, P, P, P, C.c_uint32, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -266,6 +267,19 @@ def tdpd_debug_rng(seed, i, j, step, stream):
     _chk(None, lib.tdpd_debug_rng(seed, n, _ptr(i), _ptr(j), _ptr(step), _ptr(stream),
                                   _ptr(bits), _ptr(normal)))
     return bits.reshape(n, 2), normal.reshape(n, 2)
+
+
+def tdpd_pair_forces_noalloc(cfg, pair_coef, kappa, n, pos_ptr, vel_ptr, conc_ptr, type_ptr, step,
+                             force_ptr, flux_ptr, stream_ptr=None):
+    """Allocation-free pair force + flux; the array arguments are device
+    pointers (integers), pair_coef/kappa host arrays (see tdpd.h)."""
+    pc = np.ascontiguousarray(pair_coef, np.float32)
+    kp = np.ascontiguousarray(kappa, np.float32)
+    _chk(None, lib.tdpd_pair_forces_noalloc(C.byref(cfg), _ptr(pc), _ptr(kp), int(n),
+                                            C.c_void_p(pos_ptr), C.c_void_p(vel_ptr),
+                                            C.c_void_p(conc_ptr), C.c_void_p(type_ptr), int(step),
+                                            C.c_void_p(force_ptr), C.c_void_p(flux_ptr),
+                                            C.c_void_p(stream_ptr) if stream_ptr else None))
 
 
 # ------------------------------------------------------ workload marshalling

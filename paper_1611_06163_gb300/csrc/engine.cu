@@ -304,6 +304,30 @@ RepParams make_params(const HostRep &R, int cell_base, int pbase, int n)
     return P;
 }
 
+}  // namespace
+
+RepParams tdpd::build_rep_params(const tdpd_config &c, const float *pair_coef, const float *kappa,
+                                 const int nc[3], int m, int cell_base, int pbase, int n)
+{
+    HostRep R;
+    R.cfg = c;
+    const int T = c.n_types, S = c.n_species;
+    for (int i = 0; i < T; ++i)
+        for (int j = 0; j < T; ++j) {
+            R.a[i * MAXT + j] = pair_coef[(i * T + j) * 3];
+            R.gamma[i * MAXT + j] = pair_coef[(i * T + j) * 3 + 1];
+            R.sigma[i * MAXT + j] = pair_coef[(i * T + j) * 3 + 2];
+            for (int k = 0; k < S; ++k) R.kappa[(i * MAXT + j) * MAXS + k] = kappa[(i * T + j) * S + k];
+        }
+    for (int k = 0; k < 3; ++k) R.nc[k] = nc[k];
+    R.m = m;
+    return make_params(R, cell_base, pbase, n);
+}
+
+void tdpd::set_thread_error(const char *msg) { g_err = msg; }
+
+namespace {
+
 tdpd_status free_device(tdpd_sys *s)
 {
     for (int p = 0; p < 2; ++p) {

@@ -69,6 +69,13 @@ void launch_mem_forces(const MemArgs &a, cudaStream_t st);
 // chunks: (replica, first slot, end slot); out: OBS_K doubles per chunk
 void launch_observables(const Buffers &b, const RepParams *reps, const int4 *chunks, int n_chunks,
                         int ns, double *out, cudaStream_t st);
+// Per-replica constants from a configuration and compact coefficient tables
+// (pair_coef [T*T*3] = a, gamma, sigma; kappa [T*T*S]) for a given cell grid.
+RepParams build_rep_params(const tdpd_config &c, const float *pair_coef, const float *kappa,
+                           const int nc[3], int m, int cell_base, int pbase, int n);
+// Message returned by tdpd_last_error(NULL) on this thread.
+void set_thread_error(const char *msg);
+
 void launch_debug_rng(uint64_t seed, int n, const uint32_t *i, const uint32_t *j,
                       const uint32_t *step, const uint32_t *stream, uint32_t *bits,
                       float *normal, cudaStream_t st);
