@@ -6,9 +6,10 @@ single-RBC workload: a 500-vertex biconcave membrane in tDPD solvent, 20^3
 periodic box at density 3, 24,500 particles. The metric is particle-steps/s.
 
 Native arm (default): libtdpd.so through its C ABI. Each timed step is one
-captured graph replay with CUDA event nodes around every kernel; an L2 flush
-(a write larger than the 129 MB L2) separates the timed steps. The pair
-kernel's duration comes from those events, on the stream it runs on.
+replay of the captured step graph; an L2 flush (a write larger than the
+129 MB L2) separates the timed steps. An equal number of replays of the
+instrumented graph (CUDA event nodes around each kernel, on the kernels'
+stream) follows inside the timed region and gives the per-kernel durations.
 Reference arm (--impl reference): the FP64 CPU oracle on the host cores.
 
 N > 1 (torchrun): replicas only -- every rank advances its own copy of the
@@ -62,6 +63,14 @@ def peaks():
         return float(p['hbm_gbs']), 'measured'
     except Exception:
         return 6800.0, 'fallback'
+
+
+def sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, 'MEASURED_PEAKS.json')) as f:
+            return float(json.load(f)['sm_max_mhz'])
+    except Exception:
+        return 2070.0
 
 
 def dist_env():
@@ -122,6 +131,20 @@ class Clocks:
             return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['unsampled']}
         return {'sm_mhz': statistics.median(sm), 'sm_max_mhz': max(mx), 'reasons': sorted(reasons),
                 'samples': len(sm)}
+
+
+def combine_ranks(total_ms, n_particles, steps, world, device):
+    """Whole-job throughput of independent replicas: particle-steps summed over
+    the ranks, divided by the slowest rank's time. Returns (max ms, value)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+        c = torch.tensor([float(n_particles)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        total_ms, n_particles = float(t.item()), float(c.item())
+    return total_ms, n_particles * steps / (total_ms * 1e-3)
 
 
 def oracle_rate(desc, seconds=12.0, max_steps=400):
@@ -217,38 +240,58 @@ def run_native(args):
     with Clocks(local) as clk:
         t_wall = time.perf_counter()
         with torch.cuda.stream(stream):
+            # production graph replays (one step each), L2 flushed in between
             for k in range(args.steps):
                 flush.fill_(float(k))            # evict the previous step's state from L2
                 ev[k][0].record(stream)
-                kms.append(bd.tdpd_step_timed(h))   # graph replay + per-kernel events; syncs
+                bd.tdpd_step(h, 1)
                 ev[k][1].record(stream)
+            # the same number of replays of the instrumented graph (event
+            # nodes around each kernel, on the kernels' stream) for the
+            # per-kernel durations; event nodes serialise the kernels, so
+            # these replays are not part of the step time
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                kms.append(bd.tdpd_step_timed(h))
         barrier()
         t_wall = time.perf_counter() - t_wall
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     bd.tdpd_sync(h)
-    if world > 1:
-        t = torch.tensor([total_ms], device='cuda', dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n * args.steps / (total_ms * 1e-3)
+    total_ms, value = combine_ranks(total_ms, n, args.steps, world, 'cuda')
 
     # dominant kernel: the pair force + flux + update
     K = np.array(kms)
     mean_k = K.mean(axis=0)
     ipair = names.index('pair')
     pair_ms = float(mean_k[ipair])
-    # algorithmic bytes per particle of the pair kernel: read r, v~ (16 B
-    # each), C~ (4 B per species), v, F (16 B each), C, Q (4 B per species);
-    # write v, F (16 B each), C, Q (4 B per species); plus the (cell, rank)
-    # of the next binning (8 B) = 112 + 16 * ns bytes
+    # The pair kernel is bound by instruction issue, not by memory: its roof
+    # is the lane-operation rate 152 SMs x 128 lanes x the maximum SM clock.
+    # Algorithmic operations per particle-step: every
+    # ordered pair inside the flux cut-off costs 20 + 4 (ns - 1) lane
+    # operations, every pair inside the force cut-off another 110 (TEA-8 draw,
+    # Box-Muller, Eq. 3); pair counts are the workload's mean density times
+    # the cut-off spheres. Algorithmic bytes: read r, v~ (16 B each), C~ (4 B
+    # per species), v, F (16 B each), C, Q (4 B per species); write v, F, C, Q;
+    # plus the next binning's (cell, rank) 8 B = 112 + 16 ns bytes.
     ns = int(descs[0]['n_species'])
+    n_all = sum(W.n_particles(d) for d in descs)
+    vol = sum(float(np.prod(d['L'])) for d in descs)
+    rho = n_all / vol
+    d0 = descs[0]
+    n_flux = rho * 4.0 / 3.0 * math.pi * float(d0['rcc']) ** 3
+    n_force = rho * 4.0 / 3.0 * math.pi * float(d0['rc']) ** 3
+    ops_pp = n_flux * (20 + 4 * (ns - 1)) + n_force * 110
     bytes_pp = 112 + 16 * ns
     hbm, src = peaks()
-    achieved = bytes_pp * n / (pair_ms * 1e-3) / 1e9
-    roof = {'bound': 'hbm', 'achieved': achieved, 'peak': hbm, 'unit': 'GB/s',
-            'frac': achieved / hbm, 'traffic': None, 'peak_source': src,
-            'kernel': 'k_pair', 'bytes_per_particle': bytes_pp,
+    alu_peak = 152 * 128 * sm_max_mhz() * 1e6 / 1e12
+    alu = ops_pp * n_all / (pair_ms * 1e-3) / 1e12
+    gbs = bytes_pp * n_all / (pair_ms * 1e-3) / 1e9
+    roof = {'bound': 'alu', 'achieved': alu, 'peak': alu_peak, 'unit': 'Tops/s', 'frac': alu / alu_peak,
+            'traffic': None, 'peak_source': 'derived: 152 SMs x 128 lanes x %.0f MHz (measured max clock)' % sm_max_mhz(),
+            'kernel': 'k_pair', 'ops_per_particle': ops_pp,
+            'hbm': {'achieved': gbs, 'peak': hbm, 'unit': 'GB/s', 'frac': gbs / hbm, 'peak_source': src,
+                    'bytes_per_particle': bytes_pp},
             'kernel_ms': {nm: float(m) for nm, m in zip(names, mean_k)}}
 
     # end to end through the public API: host state in (pinned), one step,
@@ -271,6 +314,40 @@ def run_native(args):
            'h2d_bytes_per_step': int(pos.nbytes + vel.nbytes + conc.nbytes),
            'd2h_bytes_per_step': 8 * (5 + 8),
            'path': 'tdpd_set_state (pinned host) + tdpd_step(1) + tdpd_read_observables'}
+
+    # batched vs plain: the same replicas advanced one after another, each by
+    # its own handle, against the batch (both back to back on one stream)
+    compare = None
+    if args.compare_sequential and len(descs) > 1:
+        K = max(1, args.compare_steps)
+        singles = []
+        for d in descs:
+            hs_ = bd.create_from(d, stream_ptr=stream.cuda_stream)
+            bd.tdpd_commit(hs_)
+            singles.append(hs_)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            bd.tdpd_step(h, K)                         # warm
+            for hs_ in singles:
+                bd.tdpd_step(hs_, K)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            bd.tdpd_step(h, K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_batch = e0.elapsed_time(e1)
+            e0.record(stream)
+            for hs_ in singles:
+                bd.tdpd_step(hs_, K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_seq = e0.elapsed_time(e1)
+        for hs_ in singles:
+            bd.tdpd_destroy(hs_)
+        compare = {'steps': K, 'replicas': len(descs),
+                   'batched': n * K / (t_batch * 1e-3), 'sequential': n * K / (t_seq * 1e-3),
+                   'ratio': t_seq / t_batch, 'unit': UNIT,
+                   'accuracy': 'identical kernels; a replica in the batch gives the same bits as alone'}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -299,8 +376,9 @@ def run_native(args):
             'roofline': roof,
             'cpu_baseline': cpu,
             'e2e': e2e,
-            'gpu_launches': nk * args.steps,
+            'gpu_launches': 2 * nk * args.steps,
             'clocks': clk.summary(),
+            'batched_vs_plain': compare,
             'wall_s': t_wall,
         }
         print(json.dumps(line), flush=True)
@@ -318,6 +396,9 @@ def main():
     ap.add_argument('--cpu-seconds', type=float, default=12.0)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='single_rbc', choices=sorted(WORKLOADS))
+    ap.add_argument('--compare-sequential', action='store_true',
+                    help='ensemble only: also time the replicas one after another')
+    ap.add_argument('--compare-steps', type=int, default=20)
     ap.add_argument('--cells-per-cutoff', type=int, default=0,
                     help='cell-list stencil width m (cells of edge >= rcut/m); 0 = library default')
     args = ap.parse_args()

@@ -92,6 +92,9 @@ typedef struct {
     double kT;                          /* sum |v - vbar|^2 / (3 (n_mobile-1)) */
     double momentum[3];                 /* sum v over non-frozen particles */
     double mass[TDPD_MAX_SPECIES];      /* sum C_s over all particles */
+    int32_t n_membrane;                 /* membrane vertices */
+    int32_t pad_;
+    double mass_membrane[TDPD_MAX_SPECIES]; /* sum C_s over membrane vertices */
 } tdpd_obs;
 
 /* ---------------------------------------------------------------- set-up */
@@ -195,6 +198,47 @@ void tdpd_destroy(tdpd_sys *s);
 tdpd_status tdpd_debug_rng(uint64_t seed, int n, const uint32_t *i, const uint32_t *j,
                            const uint32_t *step, const uint32_t *stream,
                            uint32_t *bits, float *normal);
+
+/* ------------------------------------------------------ surrogate network */
+
+/* A learned surrogate of parameter sweeps (no counterpart in the paper, which
+ * runs each parameter point as a plain simulation): an ensemble of
+ * 4 -> 64 -> 64 -> 2 perceptrons with GELU hidden layers (erf form), weights
+ * used rounded to bfloat16 with float accumulation, inputs and outputs
+ * standardised by the training set's mean and population deviation, trained
+ * by full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared
+ * error of the standardised outputs. The members' spread is the uncertainty.
+ * Parameter vector per member (TDPD_MLP_NPARAM floats): W1[64][4], b1[64],
+ * W2[64][64], b2[64], W3[2][64], b3[2], row-major (output, input). Errors
+ * are reported through tdpd_last_error(NULL). */
+#define TDPD_MLP_IN 4
+#define TDPD_MLP_HIDDEN 64
+#define TDPD_MLP_OUT 2
+#define TDPD_MLP_NPARAM 4610
+
+typedef struct tdpd_mlp tdpd_mlp;
+
+tdpd_status tdpd_mlp_create(tdpd_mlp **out, int members);
+/* float master weights of every member, host float[members * NPARAM];
+ * resets the Adam moments. */
+tdpd_status tdpd_mlp_set_params(tdpd_mlp *m, const float *params);
+tdpd_status tdpd_mlp_get_params(tdpd_mlp *m, float *params);
+/* Training set: host X float[n*4], Y float[n*2] (raw units); fixes the
+ * standardisation used by training and prediction. */
+tdpd_status tdpd_mlp_set_data(tdpd_mlp *m, int n, const float *X, const float *Y);
+/* Loss of each member on the training set and its gradient with respect to
+ * the (bfloat16-rounded) parameters: loss double[members], grad float[members
+ * * NPARAM] (either may be NULL). */
+tdpd_status tdpd_mlp_loss_grad(tdpd_mlp *m, double *loss, float *grad);
+/* steps full-batch Adam steps of every member; loss (may be NULL) receives
+ * each member's loss after the last step. */
+tdpd_status tdpd_mlp_train(tdpd_mlp *m, int steps, float lr, double *loss);
+/* Ensemble prediction for host X float[n*4] (raw units): mean float[n*2],
+ * rel_spread float[n*2] = sample standard deviation / |mean| across members
+ * (may be NULL), member_out float[members*n*2] (may be NULL). */
+tdpd_status tdpd_mlp_predict(tdpd_mlp *m, int n, const float *X, float *mean, float *rel_spread,
+                             float *member_out);
+void tdpd_mlp_destroy(tdpd_mlp *m);
 
 /* ------------------------------------------------ allocation-free variant */
 

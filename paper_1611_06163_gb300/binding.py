@@ -47,7 +47,9 @@ class tdpd_membrane(C.Structure):
 class tdpd_obs(C.Structure):
     _fields_ = [('step', C.c_int64), ('n_particles', C.c_int32), ('n_mobile', C.c_int32),
                 ('n_species', C.c_int32), ('n_rbc', C.c_int32), ('kT', C.c_double),
-                ('momentum', C.c_double * 3), ('mass', C.c_double * MAX_SPECIES)]
+                ('momentum', C.c_double * 3), ('mass', C.c_double * MAX_SPECIES),
+                ('n_membrane', C.c_int32), ('pad_', C.c_int32),
+                ('mass_membrane', C.c_double * MAX_SPECIES)]
 
 
 def _load():
@@ -84,6 +86,14 @@ def _load():
         'tdpd_debug_rng': ([C.c_uint64, I, P, P, P, P, P, P], I),
         'tdpd_step_timed': ([P, P, I, C.POINTER(I)], I),
         'tdpd_kernel_name': ([P, I], C.c_char_p),
+        'tdpd_mlp_create': ([C.POINTER(P), I], I),
+        'tdpd_mlp_set_params': ([P, P], I),
+        'tdpd_mlp_get_params': ([P, P], I),
+        'tdpd_mlp_set_data': ([P, I, P, P], I),
+        'tdpd_mlp_loss_grad': ([P, P, P], I),
+        'tdpd_mlp_train': ([P, I, F, P], I),
+        'tdpd_mlp_predict': ([P, I, P, P, P, P], I),
+        'tdpd_mlp_destroy': ([P], None),
         'tdpd_pair_forces_noalloc': ([C.POINTER(tdpd_config), P, P, I, P, P, P, P, C.c_uint32, P, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -237,7 +247,8 @@ def tdpd_read_observables(h, replica=0):
     _chk(h, lib.tdpd_read_observables(h, replica, C.byref(o)))
     return dict(step=o.step, n_particles=o.n_particles, n_mobile=o.n_mobile, n_species=o.n_species,
                 n_rbc=o.n_rbc, kT=o.kT, momentum=np.array(o.momentum[:]),
-                mass=np.array(o.mass[:o.n_species]))
+                mass=np.array(o.mass[:o.n_species]), n_membrane=o.n_membrane,
+                mass_membrane=np.array(o.mass_membrane[:o.n_species]))
 
 
 def tdpd_read_rbc(h, replica, n_rbc):
@@ -280,6 +291,60 @@ def tdpd_pair_forces_noalloc(cfg, pair_coef, kappa, n, pos_ptr, vel_ptr, conc_pt
                                             C.c_void_p(conc_ptr), C.c_void_p(type_ptr), int(step),
                                             C.c_void_p(force_ptr), C.c_void_p(flux_ptr),
                                             C.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+MLP_NPARAM = 4610
+
+
+def tdpd_mlp_create(members):
+    h = C.c_void_p()
+    _chk(None, lib.tdpd_mlp_create(C.byref(h), int(members)))
+    return h
+
+
+def tdpd_mlp_set_params(h, params):
+    p = _f32(params)
+    _chk(None, lib.tdpd_mlp_set_params(h, _ptr(p)))
+
+
+def tdpd_mlp_get_params(h, members):
+    p = np.zeros((members, MLP_NPARAM), np.float32)
+    _chk(None, lib.tdpd_mlp_get_params(h, _ptr(p)))
+    return p
+
+
+def tdpd_mlp_set_data(h, X, Y):
+    X = _f32(X)
+    Y = _f32(Y)
+    _chk(None, lib.tdpd_mlp_set_data(h, X.shape[0], _ptr(X), _ptr(Y)))
+
+
+def tdpd_mlp_loss_grad(h, members):
+    loss = np.zeros(members)
+    grad = np.zeros((members, MLP_NPARAM), np.float32)
+    _chk(None, lib.tdpd_mlp_loss_grad(h, _ptr(loss), _ptr(grad)))
+    return loss, grad
+
+
+def tdpd_mlp_train(h, steps, lr, members):
+    loss = np.zeros(members)
+    _chk(None, lib.tdpd_mlp_train(h, int(steps), float(lr), _ptr(loss)))
+    return loss
+
+
+def tdpd_mlp_predict(h, X, members):
+    X = _f32(X)
+    n = X.shape[0]
+    mean = np.zeros((n, 2), np.float32)
+    spread = np.zeros((n, 2), np.float32)
+    each = np.zeros((members, n, 2), np.float32)
+    _chk(None, lib.tdpd_mlp_predict(h, n, _ptr(X), _ptr(mean), _ptr(spread), _ptr(each)))
+    return mean, spread, each
+
+
+def tdpd_mlp_destroy(h):
+    if h:
+        lib.tdpd_mlp_destroy(h)
 
 
 # ------------------------------------------------------ workload marshalling

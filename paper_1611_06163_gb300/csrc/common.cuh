@@ -82,6 +82,16 @@ struct RingEntry {
     int across;   // vertex opposite v across the edge (nb[l], nb[l+1])
 };
 
+// Programmatic dependent launch: let the next kernel in the stream begin
+// launching, then wait until the previous kernel has finished and its writes
+// are visible. Both are no-ops for a kernel launched without the attribute.
+// Every step kernel calls this before its first global-memory access.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ int wbits(float w) { return __float_as_int(w); }
 __device__ __forceinline__ float bitsw(int b) { return __int_as_float(b); }
 

@@ -1097,7 +1097,11 @@ tdpd_status tdpd_read_observables(tdpd_sys *s, int r, tdpd_obs *out)
     for (int c = 0; c < 3; ++c) out->momentum[c] = h[c];
     const double p2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
     out->kT = nm > 1 ? (h[3] - p2 / nm) / (3.0 * (nm - 1.0)) : 0.0;
-    for (int k = 0; k < s->ns; ++k) out->mass[k] = h[5 + k];
+    out->n_membrane = (int)h[5];
+    for (int k = 0; k < s->ns; ++k) {
+        out->mass[k] = h[6 + k];
+        out->mass_membrane[k] = h[6 + MAXS + k];
+    }
     return TDPD_OK;
 }
 

@@ -40,6 +40,7 @@ __device__ __forceinline__ float3 rel_pos(const RepParams &P, float4 x, float4 r
 // shuffles, then one warp over the warp totals) and converted to binary64 once.
 __global__ void __launch_bounds__(1024) k_mem_gather(MemArgs A)
 {
+    pdl_enter();
     const int b = blockIdx.x;
     const RbcDev R = A.rbcs[b];
     const TopoDev T = A.topos[R.topo];
@@ -124,6 +125,7 @@ __device__ __forceinline__ Dihedral dihedral(float3 xa, float3 xb, float3 xc, fl
 
 __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
 {
+    pdl_enter();
     const int b = blockIdx.y;
     const RbcDev R = A.rbcs[b];
     const TopoDev T = A.topos[R.topo];
@@ -226,14 +228,14 @@ __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
 void launch_mem_gather(const MemArgs &a, cudaStream_t st)
 {
     if (a.n_rbc <= 0) return;
-    k_mem_gather<<<a.n_rbc, 1024, 0, st>>>(a);
+    launch_pdl(k_mem_gather, a.n_rbc, 1024, st, a);
 }
 
 void launch_mem_forces(const MemArgs &a, cudaStream_t st)
 {
     if (a.n_rbc <= 0) return;
     dim3 g((a.max_nv * 8 + 255) / 256, a.n_rbc);
-    k_mem_forces<<<g, 256, 0, st>>>(a);
+    launch_pdl(k_mem_forces, g, 256, st, a);
 }
 
 }  // namespace tdpd

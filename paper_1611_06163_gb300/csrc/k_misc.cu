@@ -11,6 +11,7 @@ __global__ void __launch_bounds__(256) k_observables(Buffers b, const RepParams 
                                                      const int4 *__restrict__ chunks, int ns,
                                                      double *out)
 {
+    pdl_enter();
     const int4 ch = chunks[blockIdx.x];
     const RepParams &P = reps[ch.x];
     FF acc[OBS_K];
@@ -26,7 +27,15 @@ __global__ void __launch_bounds__(256) k_observables(Buffers b, const RepParams 
             acc[3] = ff_add(ff_add(ff_add(acc[3], ff_sqr(v.x)), ff_sqr(v.y)), ff_sqr(v.z));
             acc[4] = ff_add(acc[4], 1.0f);
         }
-        for (int s = 0; s < ns; ++s) acc[5 + s] = ff_add(acc[5 + s], b.C[(size_t)k * ns + s]);
+        const bool mem = wbits(b.vt[k].w) >= 0;
+        if (mem) acc[5] = ff_add(acc[5], 1.0f);
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s)
+            if (s < ns) {
+                const float c = b.C[(size_t)k * ns + s];
+                acc[6 + s] = ff_add(acc[6 + s], c);
+                if (mem) acc[6 + MAXS + s] = ff_add(acc[6 + MAXS + s], c);
+            }
     }
     __shared__ FF sh[8][OBS_K];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;

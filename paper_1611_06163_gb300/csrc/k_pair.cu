@@ -100,6 +100,7 @@ __device__ __forceinline__ void drain(WarpSmem &W, int head, int n, const RepPar
 template <int NS, int LPP>
 __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
 {
+    pdl_enter();
     __shared__ WarpSmem smem[4];
     const int ns = NS > 0 ? NS : A.ns;
     const int lane = threadIdx.x & 31;
@@ -332,10 +333,10 @@ static void launch_ns(const PairArgs &a, cudaStream_t st)
     const long threads = (long)a.n * a.lpp;
     const int g = (int)((threads + t - 1) / t);
     switch (a.lpp) {
-    case 1: k_pair<NS, 1><<<g, t, 0, st>>>(a); break;
-    case 2: k_pair<NS, 2><<<g, t, 0, st>>>(a); break;
-    case 4: k_pair<NS, 4><<<g, t, 0, st>>>(a); break;
-    default: k_pair<NS, 8><<<g, t, 0, st>>>(a); break;
+    case 1: launch_pdl(k_pair<NS, 1>, g, t, st, a); break;
+    case 2: launch_pdl(k_pair<NS, 2>, g, t, st, a); break;
+    case 4: launch_pdl(k_pair<NS, 4>, g, t, st, a); break;
+    default: launch_pdl(k_pair<NS, 8>, g, t, st, a); break;
     }
 }
 

@@ -11,6 +11,7 @@ namespace tdpd {
 __global__ void k_bin_init(Buffers b, const RepParams *__restrict__ reps, int n, int *count,
                            int *tile_sum, int2 *cellrank)
 {
+    pdl_enter();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     int c = -1;
     if (k < n) {
@@ -31,6 +32,7 @@ __global__ void k_bin_init(Buffers b, const RepParams *__restrict__ reps, int n,
 __global__ void __launch_bounds__(1024) k_scan(int *count, int *cell_start, const int *tile_read,
                                                int *tile_clear, uint32_t *step_ctr, int inc)
 {
+    pdl_enter();
     __shared__ int wsum[32];
     __shared__ int base_sh;
     const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(1024) k_scan(int *count, int *cell_start, cons
 __global__ void k_scatter_keys(const float4 *__restrict__ pos, const int2 *__restrict__ cellrank,
                                const int *__restrict__ cell_start, int2 *keys, int n)
 {
+    pdl_enter();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int2 cr = cellrank[k];
@@ -101,6 +104,7 @@ __global__ void k_rank_gather(Buffers cur, Buffers nxt, const RepParams *__restr
                               const int *__restrict__ cell_start, int *inv, int n, int ns_rt,
                               int predict)
 {
+    pdl_enter();
     const int ns = NS > 0 ? NS : ns_rt;
     int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= n) return;
@@ -150,21 +154,21 @@ void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count,
                      int2 *cellrank, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_bin_init<<<nblk(n, 256), 256, 0, st>>>(b, reps, n, count, tile_sum, cellrank);
+    launch_pdl(k_bin_init, nblk(n, 256), 256, st, b, reps, n, count, tile_sum, cellrank);
 }
 
 void launch_scan(int *count, int *cell_start, int n_tiles, const int *tile_read, int *tile_clear,
                  uint32_t *step_ctr, int inc, cudaStream_t st)
 {
     static_assert(SCAN_TILE == 4 * 1024, "one CTA of 1024 threads scans four cells per thread");
-    k_scan<<<n_tiles, 1024, 0, st>>>(count, cell_start, tile_read, tile_clear, step_ctr, inc);
+    launch_pdl(k_scan, n_tiles, 1024, st, count, cell_start, tile_read, tile_clear, step_ctr, inc);
 }
 
 void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *cell_start,
                          int2 *keys, int n, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_scatter_keys<<<nblk(n, 256), 256, 0, st>>>(cur.pos, cellrank, cell_start, keys, n);
+    launch_pdl(k_scatter_keys, nblk(n, 256), 256, st, cur.pos, cellrank, cell_start, keys, n);
 }
 
 void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams *reps,
@@ -174,9 +178,9 @@ void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams 
     if (n <= 0) return;
     const int g = nblk(n, 256);
     switch (ns) {
-    case 1: k_rank_gather<1><<<g, 256, 0, st>>>(cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict); break;
-    case 2: k_rank_gather<2><<<g, 256, 0, st>>>(cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict); break;
-    default: k_rank_gather<0><<<g, 256, 0, st>>>(cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict); break;
+    case 1: launch_pdl(k_rank_gather<1>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict); break;
+    case 2: launch_pdl(k_rank_gather<2>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict); break;
+    default: launch_pdl(k_rank_gather<0>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict); break;
     }
 }
 

@@ -8,7 +8,25 @@
 
 namespace tdpd {
 
-constexpr int OBS_K = 5 + MAXS;   // px, py, pz, sum v^2, n_mobile, species totals
+// Launch with programmatic stream serialization, so the kernel may start
+// while its predecessor drains (it waits in pdl_enter for the results).
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+constexpr int OBS_K = 6 + 2 * MAXS;  // px, py, pz, sum v^2, n_mobile, n_membrane, species totals (all, membrane)
 constexpr int OBS_CHUNK = 8192;   // slots per observables CTA
 
 struct Buffers {

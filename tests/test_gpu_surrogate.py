@@ -1,0 +1,75 @@
+"""The surrogate steering a parameter sweep: trained on batched simulations,
+validated against fresh plain simulations, with fallback to the simulation
+when the ensemble is unsure, and compared with the sweep done without it."""
+
+import time
+
+import numpy as np
+import pytest
+
+from gpu_common import B
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 400            # t = 2 at the membrane time step 0.005
+
+
+def test_surrogate_validation_fallback_and_sweep_gain():
+    B()
+    from paper_1611_06163_gb300 import surrogate as SG
+    train = SG.sample_points(384, 101)
+    val = SG.sample_points(128, 102)
+    pool = SG.sample_points(2048, 103)
+    Ytr = SG.simulate(train, np.arange(384), STEPS)
+    ok_tr = np.isfinite(Ytr).all(1)
+    assert ok_tr.mean() > 0.99                 # replicas that went non-finite are rare
+    model = SG.Surrogate(members=5, seed=7)
+    try:
+        loss = model.fit(SG.features(train)[ok_tr], Ytr[ok_tr], steps=2500, lr=3e-3)
+        assert (loss < 0.1).all(), loss
+
+        # validation against 128 fresh plain simulations
+        Yval = SG.simulate(val, np.arange(128), STEPS)
+        okv = np.isfinite(Yval).all(1)
+        mean, spread = model.predict(SG.features(val))
+        rel = np.abs(mean - Yval)[okv] / np.abs(Yval[okv])
+        assert np.median(rel[:, 0]) < 0.10 and np.median(rel[:, 1]) < 0.10, np.median(rel, 0)
+        vals, fell = SG.predict_with_fallback(model, val, np.arange(128), STEPS, threshold=0.05)
+        # fallen-back points carry the simulation's own value (same seeds: same bits)
+        if fell.any():
+            again = SG.simulate(val, np.arange(128)[fell], STEPS)
+            assert np.array_equal(np.isnan(vals[fell]), np.isnan(again))
+            assert np.allclose(vals[fell][np.isfinite(again)], again[np.isfinite(again)])
+        ok = ~fell & okv
+        if ok.any():
+            assert np.median(np.abs(vals[ok] - Yval[ok]) / np.abs(Yval[ok])) < 0.10
+
+        # sweep: the pool's largest release rate
+        t0 = time.perf_counter()
+        pm, ps = model.predict(SG.features(pool))
+        t_pred = time.perf_counter() - t0
+        top = np.argsort(-pm[:, 0])[:16]
+        t0 = time.perf_counter()
+        found = np.nanmax(SG.simulate(pool, top, STEPS)[:, 0])
+        t_top = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        truth = SG.simulate(pool, np.arange(2048), STEPS)[:, 0]
+        assert np.isfinite(truth).mean() > 0.99
+        top = top[np.isfinite(truth[top])]
+        truth = np.where(np.isfinite(truth), truth, -np.inf)
+        t_all = time.perf_counter() - t0
+        print('sweep: surrogate %d sims (+%d training) found %.4g, brute force %d sims best %.4g; '
+              'predict %.3f s, top-16 sims %.2f s, all sims %.2f s'
+              % (16, 384, found, 2048, truth.max(), t_pred, t_top, t_all))
+        fin = np.isfinite(truth)
+        # without the network: the same number of simulations (training + 16)
+        # spent on randomly chosen points of the pool
+        rng = np.random.default_rng(104)
+        rand_best = np.max(truth[rng.choice(np.flatnonzero(fin), 384 + 16, replace=False)])
+        print('random %d sims best %.4g' % (400, rand_best))
+        assert found >= 0.85 * truth.max()
+        assert found >= rand_best * 0.98
+        # the network's ranking is informative: most of its top 16 are in the pool's top 10 %
+        assert np.mean(truth[top] >= np.quantile(truth[fin], 0.90)) >= 0.5
+    finally:
+        model.close()

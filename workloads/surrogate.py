@@ -27,10 +27,10 @@ def init_params(seed, n_members=1):
 
 def sample_points(n, seed):
     """Parameter points: permeability log-uniform in [0.01, 1], body force
-    U[0, 0.1], membranes per box 0..4, kappa log-uniform in [0.3, 3]."""
+    U[0, 0.1], membranes per box 1..4, kappa log-uniform in [0.3, 3]."""
     rng = np.random.default_rng(np.random.SeedSequence(int(seed)))
     return dict(permeability=10.0 ** rng.uniform(-2.0, 0.0, n),
                 body_force=rng.uniform(0.0, 0.1, n),
-                n_rbc=rng.integers(0, 5, n),
+                n_rbc=rng.integers(1, 5, n),
                 kappa=10.0 ** rng.uniform(math.log10(0.3), math.log10(3.0), n),
                 seeds=rng.integers(1, 2**62, n))
