@@ -139,6 +139,16 @@ tdpd_status tdpd_batch_create(tdpd_sys **out, tdpd_sys *const *replicas, int n);
  * the library's own stream. */
 tdpd_status tdpd_set_stream(tdpd_sys *s, void *cuda_stream);
 
+/* Lanes of the pair kernel that share one particle (1, 2, 4, 8, 16 or 32),
+ * or 0 (the default) to time every choice at commit and keep the fastest.
+ * The lanes split the particle's neighbour rows, so the order in which its
+ * pair terms are summed, and with it the last bits of F and Q, depends on
+ * this number; two handles with the same lanes (for instance a batch and its
+ * replicas alone) give the same bits. Must be called before tdpd_commit;
+ * TDPD_EINVAL for another value, TDPD_ESTATE after commit. No counterpart in
+ * the paper (a scheduling choice of this implementation). */
+tdpd_status tdpd_set_lanes(tdpd_sys *s, int lanes);
+
 /* Upload, bin and compute the forces F(0), Q(0) of the loaded state. Called
  * implicitly by the first step or read; afterwards no particles can be added. */
 tdpd_status tdpd_commit(tdpd_sys *s);

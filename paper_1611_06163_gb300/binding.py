@@ -68,6 +68,7 @@ def _load():
         'tdpd_add_rbc': ([P, I, P, P, P, I, I, P, P, C.POINTER(I)], I),
         'tdpd_batch_create': ([C.POINTER(P), P, I], I),
         'tdpd_set_stream': ([P, P], I),
+        'tdpd_set_lanes': ([P, I], I),
         'tdpd_commit': ([P], I),
         'tdpd_step': ([P, I], I),
         'tdpd_sync': ([P], I),
@@ -177,6 +178,10 @@ def tdpd_batch_create(handles):
 
 def tdpd_set_stream(h, stream_ptr):
     _chk(h, lib.tdpd_set_stream(h, C.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+def tdpd_set_lanes(h, lanes):
+    _chk(h, lib.tdpd_set_lanes(h, int(lanes)))
 
 
 def tdpd_commit(h):

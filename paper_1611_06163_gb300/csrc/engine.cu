@@ -62,6 +62,7 @@ struct tdpd_sys {
     cudaStream_t user = nullptr, own = nullptr, cap = nullptr;
     int N = 0, NC = 0, ns = 0, n_rbc = 0, max_nv = 0;
     int lpp = 1;
+    int lanes_fixed = 0;   // 0: timed at commit
     int parity = 0;
     int64_t step = 0;
     Buffers buf[2] = {};
@@ -489,7 +490,7 @@ tdpd_status autotune(tdpd_sys *s)
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_lpp = s->lpp;
-    for (int lpp = 1; lpp <= 8; lpp *= 2) {
+    for (int lpp = 1; lpp <= 32; lpp *= 2) {
         if (lpp > 1 && (long)s->N * lpp > 4000000L) break;
         s->lpp = lpp;
         const PairArgs a = pair_args(s, s->buf[1], 0, s->tile_sum[1]);
@@ -699,7 +700,8 @@ tdpd_status commit(tdpd_sys *s)
     }
     s->step = 0;
     if ((rc = init_state(s))) return rc;
-    if ((rc = autotune(s))) return rc;
+    if (s->lanes_fixed > 0) s->lpp = s->lanes_fixed;
+    else if ((rc = autotune(s))) return rc;
     const int nk = (int)step_kernels(s).size();
     for (int k = 0; k <= nk; ++k) CU(cudaEventCreate(&s->ev[k]));
     s->n_ev = nk + 1;
@@ -962,6 +964,16 @@ tdpd_status tdpd_set_stream(tdpd_sys *s, void *stream)
 {
     if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
     s->user = (cudaStream_t)stream;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_lanes(tdpd_sys *s, int lanes)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed) return fail(s, TDPD_ESTATE, "lanes are fixed after commit");
+    if (lanes < 0 || lanes > 32 || (lanes & (lanes - 1)))
+        return fail(s, TDPD_EINVAL, "lanes must be 0 (timed) or 1, 2, 4, 8, 16, 32");
+    s->lanes_fixed = lanes;
     return TDPD_OK;
 }
 

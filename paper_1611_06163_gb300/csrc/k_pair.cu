@@ -213,13 +213,12 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
             const int j0 = jb[sg];
             const int len = je[sg] - j0;
             const int nit = __reduce_max_sync(0xffffffffu, len);
-            for (int t = 0; t < nit; ++t) {
-                const int j = j0 + t;
+            // one candidate j whose position and first concentration are loaded
+            auto visit = [&](bool live, int j, const float4 &pj, float cj0) {
                 bool push = false;
                 float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
                 uint32_t wj = 0;
-                if (t < len) {
-                    const float4 pj = pos[j];
+                if (live) {
                     dx = px - pj.x;
                     dy = py - pj.y;
                     dz = pz - pj.z;
@@ -236,10 +235,11 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
                                 if (tj == 1) kap = kr[1];
                                 else if (tj == 2) kap = kr[2];
                                 else if (tj == 3) kap = kr[3];
-                                q[0] -= kap * wdc * (ci[0] - Ct[j]);
+                                q[0] -= kap * wdc * (ci[0] - cj0);
                             } else {
                                 const float *kap = kap_row + tj * ns;
-                                for (int s = 0; s < ns; ++s)
+                                q[0] -= kap[0] * wdc * (ci[0] - cj0);
+                                for (int s = 1; s < ns; ++s)
                                     q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
                             }
                         }
@@ -260,6 +260,18 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
                     qhead = (qhead + 32) & (QCAP - 1);
                     qcount -= 32;
                 }
+            };
+            // two candidates per trip: both loads are in flight before either
+            // is used; the visits keep the order of t, so each lane's queue
+            // entries come in the same order as one candidate per trip
+            for (int t = 0; t < nit; t += 2) {
+                const bool l0 = t < len, l1 = t + 1 < len;
+                float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
+                float c0 = 0.f, c1 = 0.f;
+                if (l0) { p0 = pos[j0 + t]; c0 = Ct[(size_t)(j0 + t) * ns]; }
+                if (l1) { p1 = pos[j0 + t + 1]; c1 = Ct[(size_t)(j0 + t + 1) * ns]; }
+                visit(l0, j0 + t, p0, c0);
+                if (t + 1 < nit) visit(l1, j0 + t + 1, p1, c1);
             }
         }
     }
@@ -336,7 +348,9 @@ static void launch_ns(const PairArgs &a, cudaStream_t st)
     case 1: launch_pdl(k_pair<NS, 1>, g, t, st, a); break;
     case 2: launch_pdl(k_pair<NS, 2>, g, t, st, a); break;
     case 4: launch_pdl(k_pair<NS, 4>, g, t, st, a); break;
-    default: launch_pdl(k_pair<NS, 8>, g, t, st, a); break;
+    case 8: launch_pdl(k_pair<NS, 8>, g, t, st, a); break;
+    case 16: launch_pdl(k_pair<NS, 16>, g, t, st, a); break;
+    default: launch_pdl(k_pair<NS, 32>, g, t, st, a); break;
     }
 }
 

@@ -70,3 +70,4 @@ def test_host_validation_without_gpu():
     cfg.dt = -1.0
     with pytest.raises(bd.TdpdError):
         bd.tdpd_create(cfg)
+

@@ -214,9 +214,11 @@ def test_batch_equals_replicas_alone():
     reps = W.replica_ensemble(n_rep=5, seed=77, side_lo=8, side_hi=11)
     hs = [bd.create_from(r) for r in reps]
     batch = bd.tdpd_batch_create(hs)
+    bd.tdpd_set_lanes(batch, 8)
     bd.tdpd_step(batch, 6)
     for k, r in enumerate(reps):
-        alone = make(r)
+        alone = bd.create_from(r)
+        bd.tdpd_set_lanes(alone, 8)
         bd.tdpd_step(alone, 6)
         a = bd.tdpd_read_state(alone, 0, 1) + bd.tdpd_read_forces(alone, 0, 1)
         b = bd.tdpd_read_state(batch, k, 1) + bd.tdpd_read_forces(batch, k, 1)
@@ -282,3 +284,28 @@ def test_ensemble_512_sampled_against_oracle():
         assert (bd.tdpd_replica_status(batch) == 0).all()
     finally:
         bd.tdpd_destroy(batch)
+
+
+def test_every_lane_count_matches_oracle():
+    """The pair kernel at 1..32 lanes per particle (rows split over the lanes,
+    partial sums combined by a butterfly) gives F(0), Q(0) within the per-step
+    tolerance of the oracle; invalid lane counts are refused."""
+    bd = B()
+    d = W.single_rbc(L=10.0, diameter=5.0, seed=31)
+    o = oracle.Oracle(d, mode=1)
+    h = bd.create_from(d)
+    for bad in (3, 64, -1):
+        with pytest.raises(bd.TdpdError) as e:
+            bd.tdpd_set_lanes(h, bad)
+        assert e.value.status == 1 and 'lanes' in str(e.value)
+    bd.tdpd_destroy(h)
+    for lanes in (1, 2, 4, 8, 16, 32):
+        h = bd.create_from(d)
+        bd.tdpd_set_lanes(h, lanes)
+        bd.tdpd_commit(h)
+        F, Q = bd.tdpd_read_forces(h, 0, 1)
+        with pytest.raises(bd.TdpdError):
+            bd.tdpd_set_lanes(h, 4)                # fixed after commit
+        bd.tdpd_destroy(h)
+        assert normwise(F, o.F) < TOL_FORCE, lanes
+        assert normwise(Q, o.Q) < TOL_FORCE, lanes
