@@ -60,6 +60,8 @@ struct tdpd_sys {
     bool committed = false;
     std::string err;
     cudaStream_t user = nullptr, own = nullptr, cap = nullptr;
+    cudaStream_t side = nullptr;                 // membrane branch of a captured step
+    cudaEvent_t fork = nullptr, join = nullptr;
     int N = 0, NC = 0, ns = 0, n_rbc = 0, max_nv = 0;
     int lpp = 1;
     int lanes_fixed = 0;   // 0: timed at commit
@@ -67,7 +69,7 @@ struct tdpd_sys {
     int64_t step = 0;
     Buffers buf[2] = {};
     std::vector<void *> allocs;
-    float4 *fext = nullptr;
+    float4 *fext = nullptr, *mx = nullptr, *mv = nullptr;   // load order
     int *inv = nullptr, *count = nullptr, *cell_start = nullptr;
     int *tile_sum[2] = {nullptr, nullptr};
     int n_tiles = 0;
@@ -339,6 +341,11 @@ tdpd_status free_device(tdpd_sys *s)
     }
     for (int k = 0; k < s->n_ev; ++k) cudaEventDestroy(s->ev[k]);
     s->n_ev = 0;
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->join) cudaEventDestroy(s->join);
+    if (s->side) cudaStreamDestroy(s->side);
+    s->fork = s->join = nullptr;
+    s->side = nullptr;
     for (void *p : s->allocs) cudaFree(p);
     s->allocs.clear();
     return TDPD_OK;
@@ -346,13 +353,14 @@ tdpd_status free_device(tdpd_sys *s)
 
 const char *const KERNEL_NAMES[] = {"scan", "scatter_keys", "rank_gather", "mem_gather", "mem_forces", "pair"};
 
-MemArgs mem_args(tdpd_sys *s, const Buffers &b, int ref_in)
+MemArgs mem_args(tdpd_sys *s, int ref_in, int inc)
 {
     MemArgs m{};
-    m.pos = b.pos; m.vt = b.vt; m.inv = s->inv; m.reps = s->d_reps; m.rbcs = s->d_rbcs;
+    m.mx = s->mx; m.mv = s->mv; m.reps = s->d_reps; m.rbcs = s->d_rbcs;
     m.topos = s->d_topos; m.tri = s->d_tri; m.ring_off = s->d_ring_off; m.ring = s->d_ring;
     m.a0j = s->d_a0j; m.bond = s->d_bond; m.ref_in = s->d_ref[ref_in]; m.ref_out = s->d_ref[1 - ref_in];
-    m.av = s->d_av; m.fext = s->fext; m.step_ctr = s->step_ctr; m.n_rbc = s->n_rbc; m.max_nv = s->max_nv;
+    m.av = s->d_av; m.fext = s->fext; m.n_rbc = s->n_rbc; m.max_nv = s->max_nv;
+    m.mem_ctr = s->step_ctr + 1; m.inc = inc;
     return m;
 }
 
@@ -360,7 +368,7 @@ PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum)
 {
     PairArgs a{};
     a.tile_sum = tile_sum;
-    a.b = b; a.fext = s->fext; a.reps = s->d_reps; a.cell_start = s->cell_start; a.count = s->count;
+    a.b = b; a.fext = s->fext; a.mx = s->mx; a.mv = s->mv; a.reps = s->d_reps; a.cell_start = s->cell_start; a.count = s->count;
     a.cellrank = s->cellrank; a.err = s->errw; a.step_ctr = s->step_ctr; a.n = s->N; a.ns = s->ns;
     a.integrate = integrate;
     a.lpp = s->lpp;
@@ -383,6 +391,20 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
     const Buffers &cur = s->buf[p], &nxt = s->buf[1 - p];
     int e = 0;
     auto mark = [&]() { if (ev) cudaEventRecordWithFlags(ev[e++], st, cudaEventRecordExternal); };
+    // The membrane kernels read the predicted vertices the last pair kernel
+    // wrote in load order, so they need not wait for the sort: in a plain
+    // step they run on a side stream beside scan, scatter and gather, and the
+    // pair kernel joins both. The timed step keeps one stream, so that the
+    // events bracket one kernel each.
+    const bool branch = s->n_rbc && !ev;
+    if (branch) {
+        cudaEventRecord(s->fork, st);
+        cudaStreamWaitEvent(s->side, s->fork, 0);
+        const MemArgs m = mem_args(s, 1 - p, 1);
+        launch_mem_gather(m, s->side, false);
+        launch_mem_forces(m, s->side);
+        cudaEventRecord(s->join, s->side);
+    }
     mark();
     launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[p], s->tile_sum[1 - p], s->step_ctr, 1, st);
     mark();
@@ -390,13 +412,14 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
     mark();
     launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st);
     mark();
-    if (s->n_rbc) {
-        const MemArgs m = mem_args(s, nxt, 1 - p);
-        launch_mem_gather(m, st);
+    if (s->n_rbc && ev) {
+        const MemArgs m = mem_args(s, 1 - p, 1);
+        launch_mem_gather(m, st, true);
         mark();
         launch_mem_forces(m, st);
         mark();
     }
+    if (branch) cudaStreamWaitEvent(st, s->join, 0);
     launch_pair(pair_args(s, nxt, 1, s->tile_sum[1 - p]), st);
     mark();
 }
@@ -462,15 +485,16 @@ tdpd_status init_state(tdpd_sys *s)
     CU(cudaMemsetAsync(s->tile_sum[1], 0, sizeof(int) * s->n_tiles, st));
     CU(cudaMemsetAsync(s->errw, 0, sizeof(uint32_t) * s->reps.size(), st));
     CU(cudaMemsetAsync(s->fext, 0, sizeof(float4) * N, st));
-    const uint32_t step32 = (uint32_t)s->step;
-    if ((rc = upload(s, s->step_ctr, &step32, 1))) return rc;
+    const uint32_t step32[2] = {(uint32_t)s->step, (uint32_t)s->step};   // sort, membrane
+    if ((rc = upload(s, s->step_ctr, step32, 2))) return rc;
     launch_bin_init(s->buf[0], s->d_reps, N, s->count, s->tile_sum[0], s->cellrank, st);
     launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[0], s->tile_sum[1], s->step_ctr, 0, st);
     launch_scatter_keys(s->buf[0], s->cellrank, s->cell_start, s->keys, N, st);
     launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0, st);
     if (s->n_rbc) {
-        const MemArgs m = mem_args(s, s->buf[1], 1);
-        launch_mem_gather(m, st);
+        launch_mem_stage(s->buf[1], s->inv, s->mx, s->mv, 0, N, st);
+        const MemArgs m = mem_args(s, 1, 0);
+        launch_mem_gather(m, st, true);
         launch_mem_forces(m, st);
     }
     launch_pair(pair_args(s, s->buf[1], 0, s->tile_sum[1]), st);
@@ -653,12 +677,13 @@ tdpd_status commit(tdpd_sys *s)
             (rc = dalloc(s, &B.Ct, (size_t)N * ns)) || (rc = dalloc(s, &B.Q, (size_t)N * ns)))
             return rc;
     }
-    if ((rc = dalloc(s, &s->fext, N)) || (rc = dalloc(s, &s->inv, N)) || (rc = dalloc(s, &s->cellrank, N)) ||
+    if ((rc = dalloc(s, &s->fext, N)) || (rc = dalloc(s, &s->mx, N)) || (rc = dalloc(s, &s->mv, N)) ||
+        (rc = dalloc(s, &s->inv, N)) || (rc = dalloc(s, &s->cellrank, N)) ||
         (rc = dalloc(s, &s->keys, N)) || (rc = dalloc(s, &s->count, (size_t)s->n_tiles * SCAN_TILE)) ||
         (rc = dalloc(s, &s->cell_start, (size_t)s->n_tiles * SCAN_TILE + 1)) ||
         (rc = dalloc(s, &s->tile_sum[0], s->n_tiles)) || (rc = dalloc(s, &s->tile_sum[1], s->n_tiles)) ||
         (rc = dalloc(s, &s->d_chunks, s->h_chunks.size())) ||
-        (rc = dalloc(s, &s->errw, s->reps.size())) || (rc = dalloc(s, &s->step_ctr, 1)) ||
+        (rc = dalloc(s, &s->errw, s->reps.size())) || (rc = dalloc(s, &s->step_ctr, 2)) ||
         (rc = dalloc(s, &s->d_reps, P.size())) || (rc = dalloc(s, &s->d_obs, OBS_K * s->h_chunks.size())))
         return rc;
     if ((rc = upload(s, s->d_reps, P.data(), P.size()))) return rc;
@@ -705,6 +730,9 @@ tdpd_status commit(tdpd_sys *s)
     const int nk = (int)step_kernels(s).size();
     for (int k = 0; k <= nk; ++k) CU(cudaEventCreate(&s->ev[k]));
     s->n_ev = nk + 1;
+    CU(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
     for (int p = 0; p < 2; ++p) {
         if ((rc = capture(s, p, 1, &s->g1[p]))) return rc;
         if ((rc = capture(s, p, GRAPH_LONG, &s->glong[p]))) return rc;

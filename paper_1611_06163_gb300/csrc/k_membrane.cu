@@ -11,6 +11,11 @@
 //     - the dihedral on edge (nb[l], nb[l+1]) (v as the opposite vertex);
 //   a shuffle sums the lanes. Every vertex force is written once, no atomics.
 //
+// Both kernels read the vertices' predicted positions and v~ from arrays in
+// load order (written by the previous step's pair kernel, or by k_mem_stage
+// for a loaded state) and write the force in load order, so they do not
+// depend on the cell sort and run beside it.
+//
 // Coordinates are taken relative to a per-membrane reference point with the
 // minimum image, so a membrane may straddle the periodic boundary as long as
 // it spans less than half a box.
@@ -42,6 +47,7 @@ __global__ void __launch_bounds__(1024) k_mem_gather(MemArgs A)
 {
     pdl_enter();
     const int b = blockIdx.x;
+    if (A.inc && b == 0 && threadIdx.x == 0) *A.mem_ctr += 1u;   // read by k_mem_forces only
     const RbcDev R = A.rbcs[b];
     const TopoDev T = A.topos[R.topo];
     const RepParams &P = A.reps[R.rep];
@@ -51,15 +57,15 @@ __global__ void __launch_bounds__(1024) k_mem_gather(MemArgs A)
     for (int k = 0; k < 5; ++k) v[k] = FF{0.0f, 0.0f};
     for (int t = threadIdx.x; t < T.ntri; t += blockDim.x) {
         const int *tv = A.tri + T.tri_off + 3 * t;
-        const float3 x0 = rel_pos(P, A.pos[A.inv[R.gbase + tv[0]]], ref);
-        const float3 x1 = rel_pos(P, A.pos[A.inv[R.gbase + tv[1]]], ref);
-        const float3 x2 = rel_pos(P, A.pos[A.inv[R.gbase + tv[2]]], ref);
+        const float3 x0 = rel_pos(P, A.mx[R.gbase + tv[0]], ref);
+        const float3 x1 = rel_pos(P, A.mx[R.gbase + tv[1]], ref);
+        const float3 x2 = rel_pos(P, A.mx[R.gbase + tv[2]], ref);
         const float3 n = cross(sub(x1, x0), sub(x2, x0));
         v[0] = ff_add(v[0], 0.5f * sqrtf(dot(n, n)));
         v[1] = ff_add(v[1], dot(x0, cross(x1, x2)) * (1.0f / 6.0f));
     }
     for (int k = threadIdx.x; k < T.nv; k += blockDim.x) {
-        const float3 x = rel_pos(P, A.pos[A.inv[R.gbase + k]], ref);
+        const float3 x = rel_pos(P, A.mx[R.gbase + k], ref);
         v[2] = ff_add(v[2], x.x);
         v[3] = ff_add(v[3], x.y);
         v[4] = ff_add(v[4], x.z);
@@ -134,7 +140,6 @@ __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
     const bool live = v < T.nv;
     const RepParams &P = A.reps[R.rep];
     float3 f = make_float3(0.f, 0.f, 0.f);
-    int slot_v = 0;
     if (live) {
         const float4 ref = A.ref_in[b];
         const double2 av = A.av[b];
@@ -142,20 +147,18 @@ __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
         const float cv = (float)(P.m_kv * (av.y - R.V0) / R.V0);
         const int off = A.ring_off[T.ring_off + v];
         const int deg = A.ring_off[T.ring_off + v + 1] - off;
-        slot_v = A.inv[R.gbase + v];
-        const float3 xv = rel_pos(P, A.pos[slot_v], ref);
-        const float4 vv = A.vt[slot_v];
+        const float3 xv = rel_pos(P, A.mx[R.gbase + v], ref);
+        const float4 vv = A.mv[R.gbase + v];
         const uint32_t idv = (uint32_t)(R.gbase + v - P.pbase);
-        const uint32_t step = *A.step_ctr + P.step0;
+        const uint32_t step = *A.mem_ctr + P.step0;
         for (int l = lane8; l < deg; l += 8) {
             const RingEntry E = A.ring[off + l];
             const RingEntry En = A.ring[off + (l + 1 == deg ? 0 : l + 1)];
             const RingEntry Ep = A.ring[off + (l == 0 ? deg - 1 : l - 1)];
-            const int s_nl = A.inv[R.gbase + E.nb];
-            const float3 xl = rel_pos(P, A.pos[s_nl], ref);
-            const float3 xn = rel_pos(P, A.pos[A.inv[R.gbase + En.nb]], ref);
-            const float3 xp = rel_pos(P, A.pos[A.inv[R.gbase + Ep.nb]], ref);
-            const float3 xw = rel_pos(P, A.pos[A.inv[R.gbase + E.across]], ref);
+            const float3 xl = rel_pos(P, A.mx[R.gbase + E.nb], ref);
+            const float3 xn = rel_pos(P, A.mx[R.gbase + En.nb], ref);
+            const float3 xp = rel_pos(P, A.mx[R.gbase + Ep.nb], ref);
+            const float3 xw = rel_pos(P, A.mx[R.gbase + E.across], ref);
 
             // bond (v, nb[l]): Eq. 10-13
             {
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
                 const float pw = P.m_m == 2.0f ? len * len : __powf(len, P.m_m);
                 const float dudl = P.m_wlc0 * (0.25f / (omx * omx) - 0.25f + x) - bp.y / pw;
                 f = add(f, scl(-dudl, e));
-                const float4 vl = A.vt[s_nl];
+                const float4 vl = A.mv[R.gbase + E.nb];
                 const float3 vij = make_float3(vv.x - vl.x, vv.y - vl.y, vv.z - vl.z);
                 const float ve = dot(vij, e);
                 f = add(f, add(scl(-P.m_gT, vij), scl(-P.m_gC * ve, e)));
@@ -222,13 +225,33 @@ __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
         f.y += __shfl_xor_sync(0xffffffffu, f.y, o);
         f.z += __shfl_xor_sync(0xffffffffu, f.z, o);
     }
-    if (live && lane8 == 0) A.fext[slot_v] = make_float4(f.x, f.y, f.z, 0.0f);
+    if (live && lane8 == 0) A.fext[R.gbase + v] = make_float4(f.x, f.y, f.z, 0.0f);
 }
 
-void launch_mem_gather(const MemArgs &a, cudaStream_t st)
+// Copy the membrane vertices of a binned state (slot order) into the
+// load-order arrays the membrane kernels read.
+__global__ void k_mem_stage(const float4 *__restrict__ pos, const float4 *__restrict__ vt,
+                            const int *__restrict__ inv, float4 *mx, float4 *mv, int g0, int g1)
+{
+    const int g = g0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= g1) return;
+    const int slot = inv[g];
+    mx[g] = pos[slot];
+    mv[g] = vt[slot];
+}
+
+void launch_mem_stage(const Buffers &b, const int *inv, float4 *mx, float4 *mv, int g0, int g1,
+                      cudaStream_t st)
+{
+    if (g1 <= g0) return;
+    k_mem_stage<<<(g1 - g0 + 255) / 256, 256, 0, st>>>(b.pos, b.vt, inv, mx, mv, g0, g1);
+}
+
+void launch_mem_gather(const MemArgs &a, cudaStream_t st, bool pdl)
 {
     if (a.n_rbc <= 0) return;
-    launch_pdl(k_mem_gather, a.n_rbc, 1024, st, a);
+    if (pdl) launch_pdl(k_mem_gather, a.n_rbc, 1024, st, a);
+    else k_mem_gather<<<a.n_rbc, 1024, 0, st>>>(a);
 }
 
 void launch_mem_forces(const MemArgs &a, cudaStream_t st)

@@ -23,6 +23,7 @@ namespace tdpd {
 namespace {
 
 constexpr int QCAP = 64;   // queue ring per warp (a push adds at most 32)
+constexpr int UNR = 2;     // candidates loaded per trip of the row loop
 
 struct __align__(16) QEntry {
     int j;          // partner slot
@@ -98,7 +99,7 @@ __device__ __forceinline__ void drain(WarpSmem &W, int head, int n, const RepPar
 }  // namespace
 
 template <int NS, int LPP>
-__global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
+__global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
 {
     pdl_enter();
     __shared__ WarpSmem smem[4];
@@ -215,37 +216,31 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
             const int nit = __reduce_max_sync(0xffffffffu, len);
             // one candidate j whose position and first concentration are loaded
             auto visit = [&](bool live, int j, const float4 &pj, float cj0) {
-                bool push = false;
-                float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-                uint32_t wj = 0;
-                if (live) {
-                    dx = px - pj.x;
-                    dy = py - pj.y;
-                    dz = pz - pj.z;
-                    r2 = dx * dx + dy * dy + dz * dz;
-                    wj = (uint32_t)wbits(pj.w);
-                    if (r2 < rcut2 && r2 > 0.0f) {
-                        if (r2 < rcc2) {
-                            const float r = r2 * rsqrtf(r2);
-                            const float w = 1.0f - r * inv_rcc;
-                            const float wdc = sc2 ? w * w : __powf(w, s_c);
-                            const int tj = (int)(wj >> 24);
-                            if (NS == 1) {
-                                float kap = kr[0];
-                                if (tj == 1) kap = kr[1];
-                                else if (tj == 2) kap = kr[2];
-                                else if (tj == 3) kap = kr[3];
-                                q[0] -= kap * wdc * (ci[0] - cj0);
-                            } else {
-                                const float *kap = kap_row + tj * ns;
-                                q[0] -= kap[0] * wdc * (ci[0] - cj0);
-                                for (int s = 1; s < ns; ++s)
-                                    q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
-                            }
-                        }
-                        push = r2 < rc2;
-                    }
+                const float dx = px - pj.x, dy = py - pj.y, dz = pz - pj.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const uint32_t wj = (uint32_t)wbits(pj.w);
+                const bool near = live && r2 > 0.0f;
+                // flux without a branch: the terms of candidates outside r_cc
+                // (or of dead lanes) are computed and dropped by the select
+                const bool inc = near && r2 < rcc2;
+                const float r = r2 * rsqrtf(r2);
+                const float w = 1.0f - r * inv_rcc;
+                const float wdc = sc2 ? w * w : __powf(w, s_c);
+                const int tj = (int)(wj >> 24);
+                if (NS == 1) {
+                    float kap = kr[0];
+                    kap = tj == 1 ? kr[1] : kap;
+                    kap = tj == 2 ? kr[2] : kap;
+                    kap = tj == 3 ? kr[3] : kap;
+                    const float qn = q[0] - kap * wdc * (ci[0] - cj0);
+                    q[0] = inc ? qn : q[0];
+                } else if (inc) {
+                    const float *kap = kap_row + tj * ns;
+                    q[0] -= kap[0] * wdc * (ci[0] - cj0);
+                    for (int s = 1; s < ns; ++s)
+                        q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
                 }
+                const bool push = near && r2 < rc2;
                 const unsigned bal = __ballot_sync(0xffffffffu, push);
                 if (push) {
                     const int slot = (qhead + qcount + __popc(bal & ((1u << lane) - 1u))) & (QCAP - 1);
@@ -261,17 +256,24 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
                     qcount -= 32;
                 }
             };
-            // two candidates per trip: both loads are in flight before either
-            // is used; the visits keep the order of t, so each lane's queue
-            // entries come in the same order as one candidate per trip
-            for (int t = 0; t < nit; t += 2) {
-                const bool l0 = t < len, l1 = t + 1 < len;
-                float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
-                float c0 = 0.f, c1 = 0.f;
-                if (l0) { p0 = pos[j0 + t]; c0 = Ct[(size_t)(j0 + t) * ns]; }
-                if (l1) { p1 = pos[j0 + t + 1]; c1 = Ct[(size_t)(j0 + t + 1) * ns]; }
-                visit(l0, j0 + t, p0, c0);
-                if (t + 1 < nit) visit(l1, j0 + t + 1, p1, c1);
+            // UNR candidates per trip: their loads are all in flight before
+            // the first is used; the visits keep the order of t, so each
+            // lane's queue entries come in the same order as one per trip
+            for (int t = 0; t < nit; t += UNR) {
+                float4 pp[UNR];
+                float cc[UNR];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    pp[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    cc[u] = 0.f;
+                    if (t + u < len) {
+                        pp[u] = pos[j0 + t + u];
+                        cc[u] = Ct[(size_t)(j0 + t + u) * ns];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UNR; ++u)
+                    if (u == 0 || t + u < nit) visit(t + u < len, j0 + t + u, pp[u], cc[u]);
             }
         }
     }
@@ -294,8 +296,9 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
     if (valid && sub == 0) {
         // ---- epilogue: membrane force, sources, corrector, next binning
         const int bi = wbits(vi.w);
+        const int gi = P.pbase + (int)(wi & ID_MASK);     // load index
         if (bi >= 0) {
-            const float4 fm = A.fext[i];
+            const float4 fm = A.fext[gi];
             fx += fm.x; fy += fm.y; fz += fm.z;
         }
         const bool frozen = (P.frozen_mask >> ti) & 1u;
@@ -327,9 +330,20 @@ __global__ void __launch_bounds__(128, 8) k_pair(PairArgs A)
         for (int s = 0; s < ns; ++s) Q[(size_t)i * ns + s] = q[s];
 
         float3 rn = make_float3(pi.x, pi.y, pi.z);
+        float4 vtn = vn;
         if (!frozen) {
             bool flip;
             rn = predict_pos(P, pi, vn, fn, flip);
+            if (flip) { vtn.x = -vtn.x; vtn.y = -vtn.y; vtn.z = -vtn.z; }
+            vtn.x = __fmaf_rn(P.ldt, fn.x, vtn.x);
+            vtn.y = __fmaf_rn(P.ldt, fn.y, vtn.y);
+            vtn.z = __fmaf_rn(P.ldt, fn.z, vtn.z);
+        }
+        if (bi >= 0) {
+            // the next step's membrane kernels start from these (the same
+            // arithmetic as the predictor of the gather), before the sort
+            A.mx[gi] = make_float4(rn.x, rn.y, rn.z, 0.0f);
+            A.mv[gi] = vtn;
         }
         cell = cell_of(P, rn.x, rn.y, rn.z);
         const int rank = atomicAdd(A.count + cell, 1);

@@ -36,7 +36,8 @@ struct Buffers {
 
 struct PairArgs {
     Buffers b;
-    const float4 *fext;          // membrane force per slot (membrane particles only)
+    const float4 *fext;          // membrane force by load index (membrane particles only)
+    float4 *mx, *mv;             // out: next predicted position and v~ of membrane particles
     const RepParams *reps;
     const int *cell_start;       // [NC+1]
     int *count;                  // [NC] histogram of the next binning (zeroed by scan)
@@ -51,9 +52,7 @@ struct PairArgs {
 };
 
 struct MemArgs {
-    const Buffers *unused;
-    const float4 *pos, *vt;
-    const int *inv;              // load index -> slot
+    const float4 *mx, *mv;       // vertex position and v~ by load index
     const RepParams *reps;
     const RbcDev *rbcs;
     const TopoDev *topos;
@@ -65,8 +64,9 @@ struct MemArgs {
     const float4 *ref_in;        // per-membrane reference point
     float4 *ref_out;             // next reference point (centroid)
     double2 *av;                 // per-membrane (A, V)
-    float4 *fext;
-    const uint32_t *step_ctr;
+    float4 *fext;                // membrane force by load index
+    uint32_t *mem_ctr;           // step counter of the membrane kernels
+    int inc;                     // k_mem_gather advances mem_ctr first
     int n_rbc, max_nv;
 };
 
@@ -82,7 +82,10 @@ void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams 
                         const int2 *keys, const int2 *cellrank, const int *cell_start, int *inv,
                         int n, int ns, int predict, cudaStream_t st);
 void launch_pair(const PairArgs &a, cudaStream_t st);
-void launch_mem_gather(const MemArgs &a, cudaStream_t st);
+// pdl: launched as a programmatic dependent of the previous kernel on st
+void launch_mem_gather(const MemArgs &a, cudaStream_t st, bool pdl);
+void launch_mem_stage(const Buffers &b, const int *inv, float4 *mx, float4 *mv, int g0, int g1,
+                      cudaStream_t st);
 void launch_mem_forces(const MemArgs &a, cudaStream_t st);
 // chunks: (replica, first slot, end slot); out: OBS_K doubles per chunk
 void launch_observables(const Buffers &b, const RepParams *reps, const int4 *chunks, int n_chunks,
