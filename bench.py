@@ -312,7 +312,7 @@ def run_native(args):
     e2e_s = time.perf_counter() - t0
     e2e = {'value': world * n0 * e2e_steps / e2e_s, 'unit': UNIT,
            'h2d_bytes_per_step': int(pos.nbytes + vel.nbytes + conc.nbytes),
-           'd2h_bytes_per_step': 8 * (5 + 8),
+           'd2h_bytes_per_step': 8 * (6 + 2 * bd.MAX_SPECIES),   # the binary64 totals tdpd_read_observables copies
            'path': 'tdpd_set_state (pinned host) + tdpd_step(1) + tdpd_read_observables'}
 
     # batched vs plain: the same replicas advanced one after another, each by

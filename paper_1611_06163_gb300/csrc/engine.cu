@@ -86,7 +86,17 @@ struct tdpd_sys {
     float2 *d_bond = nullptr;
     float4 *d_ref[2] = {nullptr, nullptr};
     double2 *d_av = nullptr;
-    double *d_obs = nullptr;
+    double *d_obs = nullptr, *d_obs_tot = nullptr;
+    unsigned *d_obs_done = nullptr;
+    float *d_in = nullptr;              // uploaded x, v, C of a loaded state (load order)
+    int4 *d_wstat = nullptr;            // fixed bits of each particle (load order)
+    cudaGraphExec_t ginit = nullptr;    // forces of a loaded state
+    // pinned host staging of loaded states and observables (async copies);
+    // stage_done marks the end of the last copies out of it
+    unsigned char *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    double *h_obs = nullptr;
+    cudaEvent_t stage_done = nullptr;
     std::vector<int> rep_pbase, rep_rbc0;
     std::vector<RbcDev> h_rbcs;
     std::vector<Topo> topos;
@@ -339,6 +349,8 @@ tdpd_status free_device(tdpd_sys *s)
         if (s->gtimed[p]) cudaGraphExecDestroy(s->gtimed[p]);
         s->g1[p] = s->glong[p] = s->gtimed[p] = nullptr;
     }
+    if (s->ginit) cudaGraphExecDestroy(s->ginit);
+    s->ginit = nullptr;
     for (int k = 0; k < s->n_ev; ++k) cudaEventDestroy(s->ev[k]);
     s->n_ev = 0;
     if (s->fork) cudaEventDestroy(s->fork);
@@ -348,6 +360,12 @@ tdpd_status free_device(tdpd_sys *s)
     s->side = nullptr;
     for (void *p : s->allocs) cudaFree(p);
     s->allocs.clear();
+    if (s->stage_done) cudaEventSynchronize(s->stage_done), cudaEventDestroy(s->stage_done);
+    if (s->h_stage) cudaFreeHost(s->h_stage);
+    s->stage_done = nullptr;
+    s->h_stage = nullptr;
+    s->h_obs = nullptr;
+    s->h_stage_bytes = 0;
     return TDPD_OK;
 }
 
@@ -424,83 +442,113 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
     mark();
 }
 
-// Upload every replica's load-order state into buffer 0, bin and sort it into
-// buffer 1 and compute the forces of the current step there.
-tdpd_status init_state(tdpd_sys *s)
+constexpr size_t OBS_STAGE = (sizeof(double) * OBS_K + 15) / 16 * 16;
+
+// Pinned staging area: observables, the step counters, the membranes'
+// reference points, then x[3N], v[3N], C[N*ns] in load order.
+uint32_t *stage_ctr(tdpd_sys *s) { return reinterpret_cast<uint32_t *>(s->h_stage + OBS_STAGE); }
+float4 *stage_ref(tdpd_sys *s) { return reinterpret_cast<float4 *>(s->h_stage + OBS_STAGE + 16); }
+float *stage_in(tdpd_sys *s) { return reinterpret_cast<float *>(stage_ref(s) + s->n_rbc); }
+size_t stage_bytes(int N, int ns, int n_rbc)
 {
-    cudaStream_t st = exec_stream(s);
+    return OBS_STAGE + 16 + sizeof(float4) * n_rbc + sizeof(float) * (size_t)N * (6 + ns);
+}
+
+// Reference point of membrane b (centroid of its unwrapped vertices) from the
+// load-order positions p of its replica.
+float4 membrane_ref(const tdpd_sys *s, int b, const float *p)
+{
+    const RbcDev &D = s->h_rbcs[b];
+    const HostRep &R = s->reps[D.rep];
+    const int first = D.gbase - s->rep_pbase[D.rep];
+    std::vector<double> x;
+    unwrap(R, s->topos[D.topo], p + 3 * (size_t)first, x);
+    double c[3] = {0, 0, 0};
+    for (int v = 0; v < D.nv; ++v)
+        for (int k = 0; k < 3; ++k) c[k] += x[3 * v + k];
+    float cf[3];
+    for (int k = 0; k < 3; ++k) {
+        double y = c[k] / D.nv;
+        if (R.cfg.periodic[k]) y -= R.cfg.L[k] * std::floor(y / R.cfg.L[k]);
+        cf[k] = (float)y;
+    }
+    return make_float4(cf[0], cf[1], cf[2], 0.f);
+}
+
+// Forces of a freshly loaded state: pack the uploaded load-order arrays into
+// buffer 0 (F = Q = 0), bin and sort into buffer 1, pair forces there (no
+// integration). The membrane kernels read the packed vertices in load order,
+// so outside the timed set-up they run on the side stream beside the sort.
+void enqueue_init(tdpd_sys *s, cudaStream_t st, bool branch)
+{
     const int N = s->N, ns = s->ns;
-    std::vector<float4> pos(N), vel(N), vt(N);
-    std::vector<float> C((size_t)N * ns);
-    int rb0 = 0;
-    for (size_t r = 0; r < s->reps.size(); ++r) {
-        const HostRep &R = s->reps[r];
-        const int base = s->rep_pbase[r];
-        const int n = (int)R.type.size();
-        for (int i = 0; i < n; ++i) {
-            const int g = base + i;
-            const uint32_t w = (uint32_t)i | ((uint32_t)R.type[i] << 24);
-            pos[g] = make_float4(R.pos[3 * i], R.pos[3 * i + 1], R.pos[3 * i + 2], 0.f);
-            std::memcpy(&pos[g].w, &w, 4);
-            vel[g] = make_float4(R.vel[3 * i], R.vel[3 * i + 1], R.vel[3 * i + 2], 0.f);
-            int rr = (int)r;
-            std::memcpy(&vel[g].w, &rr, 4);
-            vt[g] = vel[g];
-            int body = R.body[i] >= 0 ? rb0 + R.body[i] : -1;
-            std::memcpy(&vt[g].w, &body, 4);
-            for (int k = 0; k < ns; ++k) C[(size_t)g * ns + k] = R.conc[(size_t)i * ns + k];
-        }
-        rb0 += (int)R.rbcs.size();
+    cudaMemsetAsync(s->count, 0, sizeof(int) * (size_t)s->n_tiles * SCAN_TILE, st);
+    cudaMemsetAsync(s->tile_sum[0], 0, sizeof(int) * s->n_tiles, st);
+    cudaMemsetAsync(s->tile_sum[1], 0, sizeof(int) * s->n_tiles, st);
+    cudaMemsetAsync(s->errw, 0, sizeof(uint32_t) * s->reps.size(), st);
+    cudaMemsetAsync(s->fext, 0, sizeof(float4) * N, st);
+    launch_pack_state(s->d_in, s->d_wstat, s->buf[0], s->mx, s->mv, N, ns, st);
+    branch = branch && s->n_rbc;
+    if (branch) {
+        cudaEventRecord(s->fork, st);
+        cudaStreamWaitEvent(s->side, s->fork, 0);
+        const MemArgs m = mem_args(s, 1, 0);
+        launch_mem_gather(m, s->side, false);
+        launch_mem_forces(m, s->side);
+        cudaEventRecord(s->join, s->side);
     }
-    // membrane reference points: centroid of the unwrapped vertices
-    s->h_ref.assign(s->n_rbc, make_float4(0, 0, 0, 0));
-    for (int b = 0; b < s->n_rbc; ++b) {
-        const RbcDev &D = s->h_rbcs[b];
-        const HostRep &R = s->reps[D.rep];
-        const int first = D.gbase - s->rep_pbase[D.rep];
-        std::vector<double> x;
-        unwrap(R, s->topos[D.topo], &R.pos[3 * (size_t)first], x);
-        double c[3] = {0, 0, 0};
-        for (int v = 0; v < D.nv; ++v)
-            for (int k = 0; k < 3; ++k) c[k] += x[3 * v + k];
-        float cf[3];
-        for (int k = 0; k < 3; ++k) {
-            double y = c[k] / D.nv;
-            if (R.cfg.periodic[k]) y -= R.cfg.L[k] * std::floor(y / R.cfg.L[k]);
-            cf[k] = (float)y;
-        }
-        s->h_ref[b] = make_float4(cf[0], cf[1], cf[2], 0.f);
-    }
-    tdpd_status rc;
-    if ((rc = upload(s, s->buf[0].pos, pos.data(), N))) return rc;
-    if ((rc = upload(s, s->buf[0].vel, vel.data(), N))) return rc;
-    if ((rc = upload(s, s->buf[0].vt, vt.data(), N))) return rc;
-    if ((rc = upload(s, s->buf[0].C, C.data(), (size_t)N * ns))) return rc;
-    if ((rc = upload(s, s->buf[0].Ct, C.data(), (size_t)N * ns))) return rc;
-    if (s->n_rbc && (rc = upload(s, s->d_ref[1], s->h_ref.data(), s->n_rbc))) return rc;
-    CU(cudaMemsetAsync(s->buf[0].frc, 0, sizeof(float4) * N, st));
-    CU(cudaMemsetAsync(s->buf[0].Q, 0, sizeof(float) * (size_t)N * ns, st));
-    CU(cudaMemsetAsync(s->count, 0, sizeof(int) * (size_t)s->n_tiles * SCAN_TILE, st));
-    CU(cudaMemsetAsync(s->tile_sum[0], 0, sizeof(int) * s->n_tiles, st));
-    CU(cudaMemsetAsync(s->tile_sum[1], 0, sizeof(int) * s->n_tiles, st));
-    CU(cudaMemsetAsync(s->errw, 0, sizeof(uint32_t) * s->reps.size(), st));
-    CU(cudaMemsetAsync(s->fext, 0, sizeof(float4) * N, st));
-    const uint32_t step32[2] = {(uint32_t)s->step, (uint32_t)s->step};   // sort, membrane
-    if ((rc = upload(s, s->step_ctr, step32, 2))) return rc;
     launch_bin_init(s->buf[0], s->d_reps, N, s->count, s->tile_sum[0], s->cellrank, st);
     launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[0], s->tile_sum[1], s->step_ctr, 0, st);
     launch_scatter_keys(s->buf[0], s->cellrank, s->cell_start, s->keys, N, st);
     launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0, st);
-    if (s->n_rbc) {
-        launch_mem_stage(s->buf[1], s->inv, s->mx, s->mv, 0, N, st);
+    if (s->n_rbc && !branch) {
         const MemArgs m = mem_args(s, 1, 0);
         launch_mem_gather(m, st, true);
         launch_mem_forces(m, st);
     }
+    if (branch) cudaStreamWaitEvent(st, s->join, 0);
     launch_pair(pair_args(s, s->buf[1], 0, s->tile_sum[1]), st);
+}
+
+// Device part of loading a state whose reference points are staged and whose
+// load-order arrays are staged (upload_in) or already in d_in.
+tdpd_status init_device(tdpd_sys *s, bool upload_in)
+{
+    cudaStream_t st = exec_stream(s);
+    tdpd_status rc;
+    if (upload_in && (rc = upload(s, s->d_in, stage_in(s), (size_t)s->N * (6 + s->ns)))) return rc;
+    if (s->n_rbc && (rc = upload(s, s->d_ref[1], stage_ref(s), s->n_rbc))) return rc;
+    uint32_t *ctr = stage_ctr(s);
+    ctr[0] = ctr[1] = (uint32_t)s->step;                 // sort, membrane
+    if ((rc = upload(s, s->step_ctr, ctr, 2))) return rc;
+    CU(cudaEventRecord(s->stage_done, st));
+    if (s->ginit) CU(cudaGraphLaunch(s->ginit, st));
+    else enqueue_init(s, st, false);
     CU(cudaGetLastError());
     s->parity = 1;
     return TDPD_OK;
+}
+
+// Load every replica's host state (load order) and compute its forces.
+tdpd_status init_state(tdpd_sys *s)
+{
+    const int N = s->N, ns = s->ns;
+    CU(cudaEventSynchronize(s->stage_done));          // the pinned area is free
+    float *x3 = stage_in(s), *v3 = x3 + 3 * (size_t)N, *c = v3 + 3 * (size_t)N;
+    for (size_t r = 0; r < s->reps.size(); ++r) {
+        const HostRep &R = s->reps[r];
+        const size_t base = s->rep_pbase[r], n = R.type.size();
+        std::memcpy(x3 + 3 * base, R.pos.data(), sizeof(float) * 3 * n);
+        std::memcpy(v3 + 3 * base, R.vel.data(), sizeof(float) * 3 * n);
+        std::memcpy(c + base * ns, R.conc.data(), sizeof(float) * n * ns);
+    }
+    s->h_ref.resize(s->n_rbc);
+    for (int b = 0; b < s->n_rbc; ++b) {
+        const RbcDev &D = s->h_rbcs[b];
+        s->h_ref[b] = membrane_ref(s, b, s->reps[D.rep].pos.data());
+        stage_ref(s)[b] = s->h_ref[b];
+    }
+    return init_device(s, true);
 }
 
 // Pick the lanes per particle of the pair kernel by timing its forces-only
@@ -723,6 +771,28 @@ tdpd_status commit(tdpd_sys *s)
             (rc = upload(s, s->d_bond, bond.data(), bond.size())))
             return rc;
     }
+    {
+        s->h_stage_bytes = stage_bytes(N, ns, s->n_rbc);
+        void *hp = nullptr;
+        CU(cudaMallocHost(&hp, s->h_stage_bytes));
+        s->h_stage = static_cast<unsigned char *>(hp);
+        s->h_obs = reinterpret_cast<double *>(s->h_stage);
+        CU(cudaEventCreateWithFlags(&s->stage_done, cudaEventDisableTiming));
+        if ((rc = dalloc(s, &s->d_obs_tot, OBS_K)) || (rc = dalloc(s, &s->d_obs_done, 1)) || (rc = dalloc(s, &s->d_in, (size_t)N * (6 + ns))) ||
+            (rc = dalloc(s, &s->d_wstat, N)))
+            return rc;
+        std::vector<int4> ws(N);
+        int rb0 = 0;
+        for (size_t r = 0; r < s->reps.size(); ++r) {
+            const HostRep &R = s->reps[r];
+            for (size_t i = 0; i < R.type.size(); ++i)
+                ws[s->rep_pbase[r] + i] = make_int4((int)((uint32_t)i | ((uint32_t)R.type[i] << 24)), (int)r,
+                                                    R.body[i] >= 0 ? rb0 + R.body[i] : -1, 0);
+            rb0 += (int)R.rbcs.size();
+        }
+        if ((rc = upload(s, s->d_wstat, ws.data(), N))) return rc;
+        CU(cudaMemsetAsync(s->d_obs_done, 0, sizeof(unsigned), exec_stream(s)));
+    }
     s->step = 0;
     if ((rc = init_state(s))) return rc;
     if (s->lanes_fixed > 0) s->lpp = s->lanes_fixed;
@@ -733,6 +803,16 @@ tdpd_status commit(tdpd_sys *s)
     CU(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
+    {
+        cudaGraph_t g;
+        CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+        enqueue_init(s, s->cap, true);
+        cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+        if (e != cudaSuccess) return fail(s, TDPD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&s->ginit, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(s, TDPD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
     for (int p = 0; p < 2; ++p) {
         if ((rc = capture(s, p, 1, &s->g1[p]))) return rc;
         if ((rc = capture(s, p, GRAPH_LONG, &s->glong[p]))) return rc;
@@ -1078,9 +1158,27 @@ tdpd_status tdpd_set_state(tdpd_sys *s, int r, const float *pos, const float *ve
     HostRep *R = rep_of(s, r);
     if (!R || !pos || !vel) return fail(s, TDPD_EINVAL, "bad replica or array");
     const int n = (int)R->type.size(), ns = s->ns;
-    for (int i = 0; i < 3 * n; ++i)
-        if (!(pos[i] >= 0.0f && pos[i] < R->cfg.L[i % 3]) || !std::isfinite(vel[i]))
-            return fail(s, TDPD_EINVAL, "particle %d: position outside the box or non-finite velocity", i / 3);
+    const float L0 = R->cfg.L[0], L1 = R->cfg.L[1], L2 = R->cfg.L[2];
+    for (int i = 0; i < n; ++i) {
+        const float *x = pos + 3 * (size_t)i, *v = vel + 3 * (size_t)i;
+        const bool ok = x[0] >= 0.0f && x[0] < L0 && x[1] >= 0.0f && x[1] < L1 && x[2] >= 0.0f && x[2] < L2 &&
+                        std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+        if (!ok) return fail(s, TDPD_EINVAL, "particle %d: position outside the box or non-finite velocity", i);
+    }
+    if (s->reps.size() == 1 && conc) {
+        // one replica: the caller's arrays go to the device as they are (by DMA
+        // when they are pinned) and are packed there; the host copy of the
+        // state is left as it was, every other path refreshes it before use
+        CU(cudaEventSynchronize(s->stage_done));
+        for (int b = 0; b < s->n_rbc; ++b) stage_ref(s)[b] = s->h_ref[b] = membrane_ref(s, b, pos);
+        cudaStream_t st = exec_stream(s);
+        CU(cudaMemcpyAsync(s->d_in, pos, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(s->d_in + 3 * (size_t)n, vel, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(s->d_in + 6 * (size_t)n, conc, sizeof(float) * (size_t)n * ns, cudaMemcpyHostToDevice, st));
+        if ((rc = init_device(s, false))) return rc;
+        CU(cudaEventSynchronize(s->stage_done));     // the caller's arrays are read
+        return TDPD_OK;
+    }
     // other replicas keep their current device state
     for (size_t q = 0; q < s->reps.size(); ++q) {
         if ((int)q == r) continue;
@@ -1120,13 +1218,11 @@ tdpd_status tdpd_read_observables(tdpd_sys *s, int r, tdpd_obs *out)
     int c0 = -1, c1 = -1;
     for (size_t c = 0; c < s->h_chunks.size(); ++c)
         if (s->h_chunks[c].x == r) { if (c0 < 0) c0 = (int)c; c1 = (int)c + 1; }
-    launch_observables(s->buf[s->parity], s->d_reps, s->d_chunks + c0, c1 - c0, s->ns, s->d_obs, st);
-    std::vector<double> part((size_t)(c1 - c0) * OBS_K);
-    CU(cudaMemcpyAsync(part.data(), s->d_obs, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st));
+    launch_observables(s->buf[s->parity], s->d_reps, s->d_chunks + c0, c1 - c0, s->ns, s->d_obs,
+                       s->d_obs_tot, s->d_obs_done, st);
+    CU(cudaMemcpyAsync(s->h_obs, s->d_obs_tot, sizeof(double) * OBS_K, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    double h[OBS_K] = {};
-    for (int c = 0; c < c1 - c0; ++c)
-        for (int k = 0; k < OBS_K; ++k) h[k] += part[(size_t)c * OBS_K + k];
+    const double *h = s->h_obs;
     std::memset(out, 0, sizeof *out);
     out->step = s->step + (s->reps.size() > 1 ? R->step : 0);
     out->n_particles = (int)R->type.size();

@@ -12,8 +12,8 @@
 //   a shuffle sums the lanes. Every vertex force is written once, no atomics.
 //
 // Both kernels read the vertices' predicted positions and v~ from arrays in
-// load order (written by the previous step's pair kernel, or by k_mem_stage
-// for a loaded state) and write the force in load order, so they do not
+// load order (written by the previous step's pair kernel, or by the packing of
+// a loaded state) and write the force in load order, so they do not
 // depend on the cell sort and run beside it.
 //
 // Coordinates are taken relative to a per-membrane reference point with the
@@ -226,25 +226,6 @@ __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
         f.z += __shfl_xor_sync(0xffffffffu, f.z, o);
     }
     if (live && lane8 == 0) A.fext[R.gbase + v] = make_float4(f.x, f.y, f.z, 0.0f);
-}
-
-// Copy the membrane vertices of a binned state (slot order) into the
-// load-order arrays the membrane kernels read.
-__global__ void k_mem_stage(const float4 *__restrict__ pos, const float4 *__restrict__ vt,
-                            const int *__restrict__ inv, float4 *mx, float4 *mv, int g0, int g1)
-{
-    const int g = g0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= g1) return;
-    const int slot = inv[g];
-    mx[g] = pos[slot];
-    mv[g] = vt[slot];
-}
-
-void launch_mem_stage(const Buffers &b, const int *inv, float4 *mx, float4 *mv, int g0, int g1,
-                      cudaStream_t st)
-{
-    if (g1 <= g0) return;
-    k_mem_stage<<<(g1 - g0 + 255) / 256, 256, 0, st>>>(b.pos, b.vt, inv, mx, mv, g0, g1);
 }
 
 void launch_mem_gather(const MemArgs &a, cudaStream_t st, bool pdl)

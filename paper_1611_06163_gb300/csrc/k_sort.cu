@@ -185,3 +185,45 @@ void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams 
 }
 
 }  // namespace tdpd
+
+namespace tdpd {
+
+// Load-order state of a loaded or replaced configuration: raw x, v (3 floats
+// each) and C from the upload area, with each particle's fixed bits (id and
+// type, replica, membrane) from wstat; F and Q start at zero. Membrane
+// vertices also go to mx, mv (load order), where the membrane kernels read them.
+__global__ void k_pack_state(const float *__restrict__ x3, const float *__restrict__ v3,
+                             const float *__restrict__ c, const int4 *__restrict__ wstat, Buffers b,
+                             float4 *mx, float4 *mv, int n, int ns)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int4 w = wstat[g];
+    const float vx = v3[3 * (size_t)g], vy = v3[3 * (size_t)g + 1], vz = v3[3 * (size_t)g + 2];
+    const float4 p = make_float4(x3[3 * (size_t)g], x3[3 * (size_t)g + 1], x3[3 * (size_t)g + 2], __int_as_float(w.x));
+    const float4 vt = make_float4(vx, vy, vz, __int_as_float(w.z));
+    b.pos[g] = p;
+    b.vel[g] = make_float4(vx, vy, vz, __int_as_float(w.y));
+    b.vt[g] = vt;
+    if (w.z >= 0) {
+        mx[g] = p;
+        mv[g] = vt;
+    }
+    b.frc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < ns; ++s) {
+        const size_t k = (size_t)g * ns + s;
+        b.C[k] = c[k];
+        b.Ct[k] = c[k];
+        b.Q[k] = 0.0f;
+    }
+}
+
+void launch_pack_state(const float *in, const int4 *wstat, const Buffers &b, float4 *mx, float4 *mv, int n,
+                       int ns, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_pack_state<<<(n + 255) / 256, 256, 0, st>>>(in, in + 3 * (size_t)n, in + 6 * (size_t)n, wstat, b, mx, mv,
+                                                  n, ns);
+}
+
+}  // namespace tdpd

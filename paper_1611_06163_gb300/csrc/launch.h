@@ -27,7 +27,8 @@ inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream
 }
 
 constexpr int OBS_K = 6 + 2 * MAXS;  // px, py, pz, sum v^2, n_mobile, n_membrane, species totals (all, membrane)
-constexpr int OBS_CHUNK = 8192;   // slots per observables CTA
+constexpr int OBS_CHUNK = 1024;   // slots per observables CTA
+static_assert(OBS_K <= 256, "the last observables CTA sums one quantity per thread");
 
 struct Buffers {
     float4 *pos, *vt, *vel, *frc;
@@ -70,6 +71,10 @@ struct MemArgs {
     int n_rbc, max_nv;
 };
 
+// in: x[3n], v[3n], C[n*ns] in load order; wstat: (id | type << 24, replica,
+// membrane or -1, 0) per particle; membrane vertices also to mx, mv
+void launch_pack_state(const float *in, const int4 *wstat, const Buffers &b, float4 *mx, float4 *mv, int n,
+                       int ns, cudaStream_t st);
 void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum,
                      int2 *cellrank, cudaStream_t st);
 // exclusive scan of count[0, n_tiles * SCAN_TILE) into cell_start; reads the
@@ -84,12 +89,12 @@ void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams 
 void launch_pair(const PairArgs &a, cudaStream_t st);
 // pdl: launched as a programmatic dependent of the previous kernel on st
 void launch_mem_gather(const MemArgs &a, cudaStream_t st, bool pdl);
-void launch_mem_stage(const Buffers &b, const int *inv, float4 *mx, float4 *mv, int g0, int g1,
-                      cudaStream_t st);
 void launch_mem_forces(const MemArgs &a, cudaStream_t st);
-// chunks: (replica, first slot, end slot); out: OBS_K doubles per chunk
+// chunks: (replica, first slot, end slot); part: OBS_K doubles per chunk;
+// total: their sums over the chunks in chunk order (binary64); done: a
+// counter at zero, left at zero
 void launch_observables(const Buffers &b, const RepParams *reps, const int4 *chunks, int n_chunks,
-                        int ns, double *out, cudaStream_t st);
+                        int ns, double *part, double *total, unsigned *done, cudaStream_t st);
 // Per-replica constants from a configuration and compact coefficient tables
 // (pair_coef [T*T*3] = a, gamma, sigma; kappa [T*T*S]) for a given cell grid.
 RepParams build_rep_params(const tdpd_config &c, const float *pair_coef, const float *kappa,
