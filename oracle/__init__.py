@@ -75,6 +75,8 @@ def lib():
         L.orc_mem_create.restype = P
         L.orc_mem_destroy.argtypes = [P]
         L.orc_mem_nedges.argtypes = [P]
+        L.orc_mem_reset_lag.argtypes = [P]
+        L.orc_mem_reset_lag.restype = None
         L.orc_mem_nedges.restype = C.c_int
         L.orc_mem_rest.argtypes = [P, P, P, P, P]
         L.orc_mem_forces.argtypes = [P, P, P, P, C.c_uint64, C.c_uint32, C.c_double, C.c_int, P, P]
@@ -120,7 +122,7 @@ def _f64(x):
     return np.asarray(x, np.float32).astype(np.float64)
 
 
-MEM_KEYS = ('kT', 'p', 'x0', 'm', 'kg', 'kl', 'kv', 'kb', 'theta0', 'gammaT', 'gammaC', 'v_ratio')
+MEM_KEYS = ('kT', 'p', 'x0', 'm', 'kg', 'kl', 'kv', 'kb', 'theta0', 'gammaT', 'gammaC', 'v_ratio', 'lagged_av')
 
 
 class Oracle:
@@ -180,7 +182,7 @@ class Oracle:
             rest = np.concatenate([(rb['rest'] if rb['rest'] is not None else rb['pos'])
                                    for rb in desc['rbcs']]).astype(np.float32).astype(np.float64)
             mp = desc['membrane']
-            self.mparams = np.array([float(_f64(mp[k])) for k in MEM_KEYS])
+            self.mparams = np.array([float(_f64(mp.get(k, 0))) for k in MEM_KEYS])
             Lp = np.array(s.L[:], np.float64)
             per = np.array(s.periodic[:], np.int32)
             self.mem = lib().orc_mem_create(self.nrbc, self.nv, self.ntri, _p(self.tri), _p(self.first),
@@ -254,6 +256,8 @@ class Oracle:
         return F, Q
 
     def init_forces(self):
+        if getattr(self, 'mem', None):
+            lib().orc_mem_reset_lag(self.mem)
         self.F, self.Q = self.forces()
 
     def set_state(self, pos, vel, conc, step=0):

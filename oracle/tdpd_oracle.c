@@ -245,6 +245,11 @@ struct orc_mem {
     double L[3];
     int periodic[3];
     double kT, p, x0, m, kg, kl, kv, kb, theta0, gT, gC, v_ratio;
+    /* Sec. 3.3 concurrent variant: the area and volume constraints of a force
+     * evaluation use the totals of the previous evaluation. lag[2b], lag[2b+1]
+     * hold them; lag[2 nrbc] != 0 once they are set. */
+    int lagged;
+    double *lag;
 };
 
 static void cross3(const double a[3], const double b[3], double c[3])
@@ -304,9 +309,11 @@ static void tri_area_vol(const double *x, const int *t, double *A, double *V, do
 
 orc_mem *orc_mem_create(int nrbc, int nv, int ntri, const int *tri, const int *first,
                         const double *rest, const double L[3], const int periodic[3],
-                        const double P[12])
+                        const double P[13])
 {
     orc_mem *m = (orc_mem *)calloc(1, sizeof(orc_mem));
+    m->lagged = P[12] != 0.0;
+    m->lag = (double *)calloc(2 * (size_t)nrbc + 1, sizeof(double));
     m->nrbc = nrbc;
     m->nv = nv;
     m->ntri = ntri;
@@ -393,11 +400,16 @@ void orc_mem_destroy(orc_mem *m)
 {
     if (!m) return;
     free(m->tri); free(m->edge); free(m->dih); free(m->first);
-    free(m->A0j); free(m->l0); free(m->A0); free(m->V0);
+    free(m->A0j); free(m->l0); free(m->A0); free(m->V0); free(m->lag);
     free(m);
 }
 
 int orc_mem_nedges(const orc_mem *m) { return m->ne; }
+
+void orc_mem_reset_lag(orc_mem *m)
+{
+    if (m) m->lag[2 * (size_t)m->nrbc] = 0.0;
+}
 
 void orc_mem_rest(const orc_mem *m, double *A0j, double *l0, double *A0, double *V0)
 {
@@ -529,6 +541,13 @@ void orc_mem_forces(const orc_mem *m, const double *pos, const double *vel,
                     const uint32_t *id, uint64_t seed, uint32_t step, double dt,
                     int parts, double *F, double *AV)
 {
+    orc_mem_forces_av(m, pos, vel, id, seed, step, dt, parts, F, AV, NULL);
+}
+
+void orc_mem_forces_av(const orc_mem *m, const double *pos, const double *vel,
+                       const uint32_t *id, uint64_t seed, uint32_t step, double dt,
+                       int parts, double *F, double *AV, const double *av_use)
+{
     double *x = (double *)malloc(sizeof(double) * 3 * (size_t)m->nv);
     double *f = (double *)malloc(sizeof(double) * 3 * (size_t)m->nv);
     for (int b = 0; b < m->nrbc; ++b) {
@@ -551,8 +570,9 @@ void orc_mem_forces(const orc_mem *m, const double *pos, const double *vel,
         if (parts & 4) {
             /* Eq. 14-15: -dE/dx_k with dA_j/dx_k = n_hat x (x_{k+2} - x_{k+1}) / 2
              * and dV_j/dx_k = (x_{k+1} x x_{k+2}) / 6, (k, k+1, k+2) cyclic */
-            double cg = m->kg * (A - m->A0[b]) / m->A0[b];
-            double cv = m->kv * (V - m->V0[b]) / m->V0[b];
+            const double Au = av_use ? av_use[2 * b] : A, Vu = av_use ? av_use[2 * b + 1] : V;
+            double cg = m->kg * (Au - m->A0[b]) / m->A0[b];
+            double cv = m->kv * (Vu - m->V0[b]) / m->V0[b];
             for (int t = 0; t < m->ntri; ++t) {
                 const int *tv = m->tri + 3 * t;
                 double At, Vt, n[3];
@@ -642,7 +662,18 @@ int orc_forces(const orc_sys *s, const orc_mem *m, const double *pos, const doub
 {
     int rc = orc_pair_forces(s, pos, vel, conc, step, mode, F, Q);
     if (rc) return rc;
-    if (m) orc_mem_forces(m, pos, vel, s->id, s->seed, step, s->dt, 15, F, NULL);
+    if (m) {
+        /* lagged: the previous evaluation's totals once there is one; either
+         * way this evaluation's totals become the next one's */
+        const int use = m->lagged && m->lag[2 * (size_t)m->nrbc] != 0.0;
+        double *av = (double *)malloc(sizeof(double) * (2 * (size_t)m->nrbc + 1));
+        orc_mem_forces_av(m, pos, vel, s->id, s->seed, step, s->dt, 15, F, av, use ? m->lag : NULL);
+        if (m->lagged) {
+            memcpy(m->lag, av, sizeof(double) * 2 * (size_t)m->nrbc);
+            m->lag[2 * (size_t)m->nrbc] = 1.0;
+        }
+        free(av);
+    }
     return 0;
 }
 

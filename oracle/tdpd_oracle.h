@@ -63,10 +63,13 @@ int orc_pair_forces(const orc_sys *s, const double *pos, const double *vel,
 /* Membrane model. nrbc membranes of one topology (nv vertices, ntri
  * outward triangles); membrane b occupies particles first[b]..first[b]+nv-1.
  * rest [nrbc*nv*3] fixes l0 per bond, A0 per triangle, A0 = sum and
- * V0 = v_ratio * A0^1.5 (v_ratio <= 0: V0 = rest volume). */
+ * V0 = v_ratio * A0^1.5 (v_ratio <= 0: V0 = rest volume). params: kT, p, x0,
+ * m, kg, kl, kv, kb, theta0, gammaT, gammaC, v_ratio, lagged (nonzero: the
+ * area and volume constraints of orc_forces use the totals of the previous
+ * orc_forces call, Sec. 3.3). */
 orc_mem *orc_mem_create(int nrbc, int nv, int ntri, const int *tri, const int *first,
                         const double *rest, const double L[3], const int periodic[3],
-                        const double params[12]);
+                        const double params[13]);
 void orc_mem_destroy(orc_mem *m);
 int orc_mem_nedges(const orc_mem *m);
 /* Rest quantities: A0j [nrbc*ntri], l0 [nrbc*ne], A0/V0 [nrbc]. */
@@ -74,9 +77,16 @@ void orc_mem_rest(const orc_mem *m, double *A0j, double *l0, double *A0, double 
 /* parts bit 1: WLC+POW bonds (Eq. 10-11); 2: bond viscous + random (Eq. 12-13);
  * 4: area + volume (Eq. 14-15); 8: bending (Eq. 16). Adds into F. AV [nrbc*2]
  * receives (A, V) of each membrane (may be NULL). */
+/* Forget the totals a lagged membrane model carries (a new state follows). */
+void orc_mem_reset_lag(orc_mem *m);
 void orc_mem_forces(const orc_mem *m, const double *pos, const double *vel,
                     const uint32_t *id, uint64_t seed, uint32_t step, double dt,
                     int parts, double *F, double *AV);
+/* The same with the area and volume constraints evaluated at the totals
+ * av_use [nrbc*2] (NULL: this configuration's own). */
+void orc_mem_forces_av(const orc_mem *m, const double *pos, const double *vel,
+                       const uint32_t *id, uint64_t seed, uint32_t step, double dt,
+                       int parts, double *F, double *AV, const double *av_use);
 /* Conservative membrane energy of the selected parts (1, 4, 8). */
 double orc_mem_energy(const orc_mem *m, const double *pos, int parts);
 /* Bending angles theta_j of membrane b, per edge [ne]. */

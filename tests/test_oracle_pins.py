@@ -436,3 +436,44 @@ def test_bond_random_force_covariance_satisfies_fdt():
     S = np.cov(samples.T)
     assert np.abs(samples.mean(0)).max() < 5 * math.sqrt(C.max() / len(samples))
     assert np.abs(S - C).max() < 0.05 * C.max()
+
+
+def test_lagged_area_volume_uses_previous_totals():
+    """Sec. 3.3 concurrent variant: an evaluation with lagged area and volume
+    differs from the sequential one only by the constraint coefficients,
+    taken at the previous evaluation's totals (A', V') instead of the current
+    ones (A, V): F_lag - F_seq = -(k_g (A' - A)/A0) grad A - (k_v (V' - V)/V0)
+    grad V, with grad A and grad V by central differences of the totals; an
+    unmoved state gives the sequential forces; the first evaluation after a
+    state is loaded is the sequential one."""
+    d = _perturbed_sphere(seed=3, kT=0.0)
+    seq = oracle.Oracle(d, mode=1)
+    d_lag = _perturbed_sphere(seed=3, kT=0.0, lagged_av=1)
+    lag = oracle.Oracle(d_lag, mode=1)
+    assert np.array_equal(lag.F, seq.F)                      # first evaluation
+    x0 = seq.pos.copy()
+    _, AV0 = seq.membrane_forces(parts=0)
+    # a second evaluation of the unmoved state: previous totals = current
+    F1, _ = lag.forces()
+    assert relerr(F1, seq.F) < 1e-14
+    # move the vertices, evaluate lagged (previous totals: those at x0)
+    rng = np.random.default_rng(4)
+    x1 = x0 + rng.uniform(-0.03, 0.03, x0.shape)
+    lag.forces(pos=x0)                                        # totals at x0 carried
+    F_lag, _ = lag.forces(pos=x1)
+    F_seq, _ = seq.forces(pos=x1)
+    _, AV1 = seq.membrane_forces(pos=x1, parts=0)
+    h = 1e-6
+    gA = np.zeros_like(x1)
+    gV = np.zeros_like(x1)
+    for i in range(seq.n):
+        for c in range(3):
+            p = x1.copy(); p[i, c] += h; _, ap = seq.membrane_forces(pos=p, parts=0)
+            p[i, c] -= 2 * h; _, am = seq.membrane_forces(pos=p, parts=0)
+            gA[i, c] = (ap[0, 0] - am[0, 0]) / (2 * h)
+            gV[i, c] = (ap[0, 1] - am[0, 1]) / (2 * h)
+    _, _, A0, V0 = seq.membrane_rest()
+    mp = d['membrane']
+    expect = -(mp['kg'] * (AV0[0, 0] - AV1[0, 0]) / A0[0]) * gA - (mp['kv'] * (AV0[0, 1] - AV1[0, 1]) / V0[0]) * gV
+    assert np.linalg.norm(F_lag - F_seq) > 1e-3 * np.linalg.norm(F_seq)
+    assert relerr(F_lag - F_seq, expect) < 1e-5
