@@ -209,6 +209,7 @@ def run_native(args):
     descs = WORKLOADS[args.workload][1](rank)
     for d in descs:
         d['cells_per_cutoff'] = args.cells_per_cutoff
+        d['skin'] = args.skin
     n = sum(W.n_mobile(d) for d in descs)
     stream = torch.cuda.Stream()
     if len(descs) == 1:
@@ -218,6 +219,8 @@ def run_native(args):
         parts = [bd.create_from(d) for d in descs]
         h = bd.tdpd_batch_create(parts)
         bd.tdpd_set_stream(h, stream.cuda_stream)
+        if args.skin is not None:
+            bd.tdpd_set_skin(h, args.skin)
     bd.tdpd_commit(h)
     nk = bd.tdpd_launches_per_step(h)
     names = [bd.tdpd_kernel_name(h, k) for k in range(nk)]
@@ -236,6 +239,7 @@ def run_native(args):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kms = []
+    rebuilds0 = sum(bd.tdpd_list_rebuilds(h, r) for r in range(len(descs)))
     barrier()
     with Clocks(local) as clk:
         t_wall = time.perf_counter()
@@ -258,6 +262,9 @@ def run_native(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     bd.tdpd_sync(h)
+    # list rebuilds per replica-step over the timed and the instrumented replays
+    rebuild_rate = (sum(bd.tdpd_list_rebuilds(h, r) for r in range(len(descs))) - rebuilds0) / (
+        2.0 * args.steps * len(descs))
     total_ms, value = combine_ranks(total_ms, n, args.steps, world, 'cuda')
 
     # dominant kernel: the pair force + flux + update
@@ -273,7 +280,9 @@ def run_native(args):
     # Box-Muller, Eq. 3); pair counts are the workload's mean density times
     # the cut-off spheres. Algorithmic bytes: read r, v~ (16 B each), C~ (4 B
     # per species), v, F (16 B each), C, Q (4 B per species); write v, F, C, Q;
-    # plus the next binning's (cell, rank) 8 B = 112 + 16 ns bytes.
+    # plus the next binning's (cell, rank) 8 B = 112 + 16 ns bytes. With
+    # neighbour lists the binning is replaced by the list entries (4 B per
+    # partner within rcut + skin) and the position at the last build (16 B).
     ns = int(descs[0]['n_species'])
     n_all = sum(W.n_particles(d) for d in descs)
     vol = sum(float(np.prod(d['L'])) for d in descs)
@@ -282,7 +291,10 @@ def run_native(args):
     n_flux = rho * 4.0 / 3.0 * math.pi * float(d0['rcc']) ** 3
     n_force = rho * 4.0 / 3.0 * math.pi * float(d0['rc']) ** 3
     ops_pp = n_flux * (20 + 4 * (ns - 1)) + n_force * 110
-    bytes_pp = 112 + 16 * ns
+    skin = 0.3 if args.skin is None else args.skin
+    rcut = max(float(d0['rc']), float(d0['rcc']))
+    n_list = rho * 4.0 / 3.0 * math.pi * (rcut + skin) ** 3 if skin > 0 else 0.0
+    bytes_pp = 112 + 16 * ns if skin == 0 else 104 + 16 * ns + 16 + 4 * n_list
     hbm, src = peaks()
     alu_peak = 152 * 128 * sm_max_mhz() * 1e6 / 1e12
     alu = ops_pp * n_all / (pair_ms * 1e-3) / 1e12
@@ -372,6 +384,7 @@ def run_native(args):
             'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
             'config': {'workload': WORKLOADS[args.workload][0], 'name': args.workload, 'particles': n,
                        'l2': 'flushed between timed steps (256 MB write)',
+                       'neighbour_list': {'skin': skin, 'rebuilds_per_step': rebuild_rate} if skin > 0 else 'off (cell stencil every step)',
                        'parallelism': 'replicas only' if world > 1 else 'single GPU'},
             'roofline': roof,
             'cpu_baseline': cpu,
@@ -401,6 +414,8 @@ def main():
     ap.add_argument('--compare-steps', type=int, default=20)
     ap.add_argument('--cells-per-cutoff', type=int, default=0,
                     help='cell-list stencil width m (cells of edge >= rcut/m); 0 = library default')
+    ap.add_argument('--skin', type=float, default=None,
+                    help='neighbour-list skin; 0 = cell mode (stencil every step); default: the library\'s')
     args = ap.parse_args()
     if args.impl == 'reference':
         return run_reference(args)

@@ -149,6 +149,27 @@ tdpd_status tdpd_set_stream(tdpd_sys *s, void *cuda_stream);
  * the paper (a scheduling choice of this implementation). */
 tdpd_status tdpd_set_lanes(tdpd_sys *s, int lanes);
 
+/* Skin of the Verlet neighbour lists of the pair kernel (length units): each
+ * particle keeps the partners within max(rc, rcc) + skin found at a list
+ * build; a replica rebuilds its lists (and re-sorts its cells) in the step
+ * after one of its particles has moved more than skin/2 from its position at
+ * the last build, which keeps every pair inside the cut-off in the lists
+ * (Sec. 3.1 rebuilds the list every few steps). 0 selects cell mode: no
+ * lists, the cell stencil is walked and the particles re-sorted every step.
+ * Default (not called): 0.3. A replica whose box is too small for the skin
+ * (rcut + 2 skin must not exceed half a periodic edge, and the cells of edge
+ * (rcut + skin)/m must fit 2m+1 times) gets a smaller one. The skin changes
+ * the order in which pair terms are summed, so results agree to rounding,
+ * not bitwise, across skins. Before tdpd_commit; TDPD_EINVAL for a negative
+ * or non-finite value, TDPD_ESTATE after commit. A list that overflows its
+ * capacity (sized at commit to 1.5 x the longest list plus 16) marks its
+ * replica TDPD_EOVERFLOW in tdpd_replica_status. */
+tdpd_status tdpd_set_skin(tdpd_sys *s, float skin);
+
+/* Number of steps since commit in which replica r rebuilt its neighbour lists
+ * (0 in cell mode; the builds at commit and at state loads are not counted). */
+tdpd_status tdpd_list_rebuilds(tdpd_sys *s, int r, int64_t *out);
+
 /* Upload, bin and compute the forces F(0), Q(0) of the loaded state. Called
  * implicitly by the first step or read; afterwards no particles can be added. */
 tdpd_status tdpd_commit(tdpd_sys *s);
@@ -169,7 +190,8 @@ tdpd_status tdpd_step_timed(tdpd_sys *s, float *kernel_ms, int max_kernels, int 
 const char *tdpd_kernel_name(const tdpd_sys *s, int k);
 
 /* Wait for enqueued work; returns TDPD_ENONFINITE if any replica reported a
- * non-finite value since the last call (see tdpd_replica_status). */
+ * non-finite value (TDPD_EOVERFLOW: a neighbour list overflowed) since the
+ * last commit or state load (see tdpd_replica_status). */
 tdpd_status tdpd_sync(tdpd_sys *s);
 
 /* Replace the state of replica r (host arrays in load order) and recompute
@@ -187,7 +209,8 @@ tdpd_status tdpd_read_observables(tdpd_sys *s, int replica, tdpd_obs *out);
 /* Area and volume (FP64, compensated sums) of each membrane of the replica at
  * the current step, as used by the constraint forces (Eq. 14-15). */
 tdpd_status tdpd_read_rbc(tdpd_sys *s, int replica, double *area, double *volume);
-/* Per-replica status words (TDPD_OK or TDPD_ENONFINITE), int32[n_replicas]. */
+/* Per-replica status words (TDPD_OK, TDPD_ENONFINITE, or TDPD_EOVERFLOW for
+ * an overflowed neighbour list), int32[n_replicas]. */
 tdpd_status tdpd_replica_status(tdpd_sys *s, int32_t *status);
 
 int tdpd_num_replicas(const tdpd_sys *s);

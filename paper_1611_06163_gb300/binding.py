@@ -69,6 +69,8 @@ def _load():
         'tdpd_batch_create': ([C.POINTER(P), P, I], I),
         'tdpd_set_stream': ([P, P], I),
         'tdpd_set_lanes': ([P, I], I),
+        'tdpd_set_skin': ([P, C.c_float], I),
+        'tdpd_list_rebuilds': ([P, I, C.POINTER(C.c_int64)], I),
         'tdpd_commit': ([P], I),
         'tdpd_step': ([P, I], I),
         'tdpd_sync': ([P], I),
@@ -182,6 +184,16 @@ def tdpd_set_stream(h, stream_ptr):
 
 def tdpd_set_lanes(h, lanes):
     _chk(h, lib.tdpd_set_lanes(h, int(lanes)))
+
+
+def tdpd_set_skin(h, skin):
+    _chk(h, lib.tdpd_set_skin(h, float(skin)))
+
+
+def tdpd_list_rebuilds(h, replica=0):
+    v = C.c_int64(0)
+    _chk(h, lib.tdpd_list_rebuilds(h, int(replica), C.byref(v)))
+    return v.value
 
 
 def tdpd_commit(h):
@@ -391,6 +403,10 @@ def create_from(desc, stream_ptr=None):
             tdpd_add_particles(h, p['pos'], p['vel'], p['conc'], p['type'])
         for rb in desc['rbcs']:
             tdpd_add_rbc(h, rb['pos'], rb['vel'], rb['conc'], rb['type'], rb['tri'], rb['rest'])
+        if desc.get('skin') is not None:
+            tdpd_set_skin(h, desc['skin'])
+        if desc.get('lanes') is not None:
+            tdpd_set_lanes(h, desc['lanes'])
         if stream_ptr:
             tdpd_set_stream(h, stream_ptr)
     except Exception:

@@ -38,6 +38,9 @@ struct RepParams {
     int ntypes, ns;
     float dt, hdt, hdt2, ldt, inv_sqrt_dt;
     float rc2, inv_rc, rcc2, inv_rcc, rcut2;
+    float rlist2;            // neighbour-list radius (rcut + skin) squared
+    float half_skin2;        // (skin / 2)^2: a larger displacement forces a rebuild
+    float inv_L[3];          // 1/L on periodic axes, 0 on walled ones (minimum image)
     float sR;                // exponent of w_R: s_f / 2
     float s_c;
     int sR_is1, sc_is2;      // integer fast paths
@@ -165,6 +168,61 @@ __device__ __forceinline__ void add_tile_count(int *tile_sum, int c)
     const int tile = c >= 0 ? (c >> SCAN_TILE_LOG2) : -1 - (int)(threadIdx.x & 31);
     const unsigned same = __match_any_sync(0xffffffffu, tile);
     if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(tile_sum + tile, __popc(same));
+}
+
+// One row (dy, dz) of the cell stencil of particle i, whose cell is
+// (cx, cy, cz) and whose offsets inside it along y and z are oy, oz: the
+// cells cx-m..cx+m of that row that come within sqrt(rtrim2) of the particle
+// (less a margin eps for the rounding of cell assignment), as at most two
+// contiguous slot ranges [jb, je) -- two where the row wraps around x -- and
+// the periodic image shifts to add to x_i. g must come in zeroed; false (g
+// untouched apart from the shifts) when the row has no such cell.
+struct RowSeg {
+    int jb[2], je[2];
+    float sx1, sy, sz;       // x shift of the second range; y and z shifts
+};
+
+__device__ __forceinline__ bool stencil_row(const RepParams &P, const int *__restrict__ cs, float4 pi, int cx,
+                                            int cy, int cz, int row, float oy, float oz, float eps,
+                                            float rtrim2, RowSeg &g)
+{
+    const int m = P.m_stencil, width = 2 * m + 1;
+    const float hy = P.h[1], hz = P.h[2];
+    const int dy = row % width - m, dz = row / width - m;
+    // distance from particle i to the slab of the row's cells
+    const float ay = dy == 0 ? 0.f : (dy > 0 ? (float)dy * hy - oy : oy - (float)(dy + 1) * hy);
+    const float az = dz == 0 ? 0.f : (dz > 0 ? (float)dz * hz - oz : oz - (float)(dz + 1) * hz);
+    const float by = fmaxf(ay - eps, 0.f), bz = fmaxf(az - eps, 0.f);
+    const float rem = rtrim2 - by * by - bz * bz;
+    int y = cy + dy, z = cz + dz;
+    bool ok = rem > 0.f;
+    if (y < 0) { y += P.nc[1]; g.sy = P.L[1]; }
+    else if (y >= P.nc[1]) { y -= P.nc[1]; g.sy = -P.L[1]; }
+    if (z < 0) { if (P.periodic[2]) { z += P.nc[2]; g.sz = P.L[2]; } else ok = false; }
+    else if (z >= P.nc[2]) { if (P.periodic[2]) { z -= P.nc[2]; g.sz = -P.L[2]; } else ok = false; }
+    if (!ok) return false;
+    const float rx = sqrtf(rem) + eps;
+    const int x0 = max(cx - m, __float2int_rd((pi.x - rx) * P.cell_scale[0]));
+    const int x1 = min(cx + m, __float2int_rd((pi.x + rx) * P.cell_scale[0]));
+    const int base = P.cell_base + (z * P.nc[1] + y) * P.nc[0];
+    const int nx = P.nc[0];
+    if (x0 >= 0 && x1 < nx) {
+        g.jb[0] = cs[base + x0];
+        g.je[0] = cs[base + x1 + 1];
+    } else if (x0 < 0) {
+        g.jb[0] = cs[base];
+        g.je[0] = cs[base + x1 + 1];
+        g.jb[1] = cs[base + nx + x0];
+        g.je[1] = cs[base + nx];
+        g.sx1 = P.L[0];
+    } else {
+        g.jb[0] = cs[base + x0];
+        g.je[0] = cs[base + nx];
+        g.jb[1] = cs[base];
+        g.je[1] = cs[base + x1 - nx + 1];
+        g.sx1 = -P.L[0];
+    }
+    return true;
 }
 
 // Fold a coordinate back into [0, L) after a move of less than one box.

@@ -42,6 +42,7 @@ struct HostRep {
     int64_t step = 0;
     int nc[3] = {0, 0, 0};
     int m = 2;
+    float skin = 0.0f;     // neighbour-list skin of this replica (0: cell mode)
 };
 
 struct Topo {
@@ -65,6 +66,14 @@ struct tdpd_sys {
     int N = 0, NC = 0, ns = 0, n_rbc = 0, max_nv = 0;
     int lpp = 1;
     int lanes_fixed = 0;   // 0: timed at commit
+    float skin = -1.0f;    // neighbour-list skin; 0: cell mode; < 0: default
+    bool use_list = false;
+    int *nl = nullptr, *nlc = nullptr;   // neighbour lists (own allocation: resized by the lane count)
+    int nl_cap = 0;
+    size_t nl_ints = 0;
+    float4 *xb = nullptr;
+    uint32_t *disp[2] = {nullptr, nullptr}, *rb = nullptr, *rb_all = nullptr;
+    uint32_t *builds = nullptr;          // list rebuild steps per replica (since commit)
     int parity = 0;
     int64_t step = 0;
     Buffers buf[2] = {};
@@ -102,7 +111,7 @@ struct tdpd_sys {
     std::vector<Topo> topos;
     std::vector<float4> h_ref;
     cudaGraphExec_t g1[2] = {nullptr, nullptr}, glong[2] = {nullptr, nullptr}, gtimed[2] = {nullptr, nullptr};
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[12] = {};
     int n_ev = 0;
 };
 
@@ -280,6 +289,9 @@ RepParams make_params(const HostRep &R, int cell_base, int pbase, int n)
     P.inv_rcc = c.rcc > 0 ? (float)(1.0 / c.rcc) : 0.f;
     const float rcut = std::max(c.rc, c.rcc);
     P.rcut2 = rcut * rcut;
+    P.rlist2 = (rcut + R.skin) * (rcut + R.skin);
+    P.half_skin2 = 0.25f * R.skin * R.skin;
+    for (int k = 0; k < 3; ++k) P.inv_L[k] = c.periodic[k] ? (float)(1.0 / (double)c.L[k]) : 0.0f;
     P.sR = 0.5f * c.s_f;
     P.s_c = c.s_c;
     P.sR_is1 = (P.sR == 1.0f);
@@ -360,6 +372,10 @@ tdpd_status free_device(tdpd_sys *s)
     s->side = nullptr;
     for (void *p : s->allocs) cudaFree(p);
     s->allocs.clear();
+    if (s->nl) cudaFree(s->nl);
+    s->nl = nullptr;
+    s->nl_ints = 0;
+    s->nl_cap = 0;
     if (s->stage_done) cudaEventSynchronize(s->stage_done), cudaEventDestroy(s->stage_done);
     if (s->h_stage) cudaFreeHost(s->h_stage);
     s->stage_done = nullptr;
@@ -369,7 +385,8 @@ tdpd_status free_device(tdpd_sys *s)
     return TDPD_OK;
 }
 
-const char *const KERNEL_NAMES[] = {"scan", "scatter_keys", "rank_gather", "mem_gather", "mem_forces", "pair"};
+const char *const KERNEL_NAMES[] = {"scan",       "scatter_keys", "rank_gather", "mem_gather", "mem_forces",
+                                    "pair",       "decide",       "bin",         "list_build"};
 
 MemArgs mem_args(tdpd_sys *s, int ref_in, int inc)
 {
@@ -382,7 +399,8 @@ MemArgs mem_args(tdpd_sys *s, int ref_in, int inc)
     return m;
 }
 
-PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum)
+// disp_next: where list mode records the displacements of the next positions
+PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum, uint32_t *disp_next = nullptr)
 {
     PairArgs a{};
     a.tile_sum = tile_sum;
@@ -390,13 +408,27 @@ PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum)
     a.cellrank = s->cellrank; a.err = s->errw; a.step_ctr = s->step_ctr; a.n = s->N; a.ns = s->ns;
     a.integrate = integrate;
     a.lpp = s->lpp;
+    if (s->use_list) {
+        a.nl = s->nl; a.nlc = s->nlc; a.cap = s->nl_cap; a.xb = s->xb; a.disp_next = disp_next;
+    }
     return a;
+}
+
+// List build over the sorted buffer b for the replicas flagged in rb.
+ListArgs list_args(tdpd_sys *s, const Buffers &b, const uint32_t *rb, int cap)
+{
+    ListArgs l{};
+    l.pos = b.pos; l.vel = b.vel; l.reps = s->d_reps; l.cell_start = s->cell_start; l.rb = rb;
+    l.nl = s->nl; l.nlc = s->nlc; l.xb = s->xb; l.err = s->errw; l.n = s->N; l.lpp = s->lpp; l.cap = cap;
+    return l;
 }
 
 // Kernel kinds one step launches, in order (indices into KERNEL_NAMES).
 std::vector<int> step_kernels(const tdpd_sys *s)
 {
-    std::vector<int> k{0, 1, 2};
+    std::vector<int> k;
+    if (s->use_list) k = {6, 7, 0, 1, 2, 8};
+    else k = {0, 1, 2};
     if (s->n_rbc) { k.push_back(3); k.push_back(4); }
     k.push_back(5);
     return k;
@@ -424,12 +456,32 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         cudaEventRecord(s->join, s->side);
     }
     mark();
-    launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[p], s->tile_sum[1 - p], s->step_ctr, 1, st);
-    mark();
-    launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st);
-    mark();
-    launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st);
-    mark();
+    const int nrep = (int)s->reps.size();
+    if (s->use_list) {
+        // rebuild the lists of the replicas whose particles moved more than
+        // half their skin; the others keep their lists and their slots
+        const uint32_t *any = s->rb + nrep;
+        launch_rebuild_decide(s->disp[p], s->disp[1 - p], s->rb, s->d_reps, nrep, 0, s->step_ctr, s->builds, st);
+        mark();
+        launch_bin_next(cur, s->d_reps, s->N, s->count, s->tile_sum[0], s->cellrank, any, st);
+        mark();
+        launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[0], s->tile_sum[1], s->step_ctr, 0, st, any);
+        mark();
+        launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st, any);
+        mark();
+        launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st,
+                           s->rb, nrep, s->tile_sum[0], s->n_tiles);
+        mark();
+        launch_list_build(list_args(s, nxt, s->rb, s->nl_cap), st);
+        mark();
+    } else {
+        launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[p], s->tile_sum[1 - p], s->step_ctr, 1, st);
+        mark();
+        launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st);
+        mark();
+        launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st);
+        mark();
+    }
     if (s->n_rbc && ev) {
         const MemArgs m = mem_args(s, 1 - p, 1);
         launch_mem_gather(m, st, true);
@@ -438,11 +490,12 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         mark();
     }
     if (branch) cudaStreamWaitEvent(st, s->join, 0);
-    launch_pair(pair_args(s, nxt, 1, s->tile_sum[1 - p]), st);
+    launch_pair(pair_args(s, nxt, 1, s->tile_sum[1 - p], s->disp[1 - p]), st);
     mark();
 }
 
 constexpr size_t OBS_STAGE = (sizeof(double) * OBS_K + 15) / 16 * 16;
+constexpr float DEFAULT_SKIN = 0.3f;   // neighbour-list skin (length units)
 
 // Pinned staging area: observables, the step counters, the membranes'
 // reference points, then x[3N], v[3N], C[N*ns] in load order.
@@ -500,14 +553,22 @@ void enqueue_init(tdpd_sys *s, cudaStream_t st, bool branch)
     launch_bin_init(s->buf[0], s->d_reps, N, s->count, s->tile_sum[0], s->cellrank, st);
     launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[0], s->tile_sum[1], s->step_ctr, 0, st);
     launch_scatter_keys(s->buf[0], s->cellrank, s->cell_start, s->keys, N, st);
-    launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0, st);
+    if (s->use_list) {
+        launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0,
+                           st, nullptr, 0, s->tile_sum[0], s->n_tiles);
+        cudaMemsetAsync(s->disp[1], 0, sizeof(uint32_t) * s->reps.size(), st);
+        launch_list_build(list_args(s, s->buf[1], s->rb_all, s->nl_cap), st);
+    } else {
+        launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0,
+                           st);
+    }
     if (s->n_rbc && !branch) {
         const MemArgs m = mem_args(s, 1, 0);
         launch_mem_gather(m, st, true);
         launch_mem_forces(m, st);
     }
     if (branch) cudaStreamWaitEvent(st, s->join, 0);
-    launch_pair(pair_args(s, s->buf[1], 0, s->tile_sum[1]), st);
+    launch_pair(pair_args(s, s->buf[1], 0, s->tile_sum[1], s->disp[1]), st);
 }
 
 // Device part of loading a state whose reference points are staged and whose
@@ -554,6 +615,35 @@ tdpd_status init_state(tdpd_sys *s)
 // Pick the lanes per particle of the pair kernel by timing its forces-only
 // mode (idempotent apart from the next binning's counters) for each choice,
 // then rebuild the state with the winner.
+// Size the neighbour lists of the current lane count from a counting pass
+// over the sorted state in buffer 1 (capacity: 1.5 x the longest lane list,
+// plus 16), allocate them and build them.
+tdpd_status prepare_list(tdpd_sys *s)
+{
+    cudaStream_t st = exec_stream(s);
+    const size_t lanes = (size_t)s->N * s->lpp;
+    launch_list_build(list_args(s, s->buf[1], s->rb_all, 0), st);
+    std::vector<int> cnt(lanes);
+    CU(cudaMemcpyAsync(cnt.data(), s->nlc, sizeof(int) * lanes, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    int mx = 0;
+    for (int c : cnt) mx = std::max(mx, c);
+    const int cap = (mx * 3 / 2 + 16 + 7) / 8 * 8;
+    const size_t need = (lanes + 31) / 32 * 32 * (size_t)cap;
+    if (need > s->nl_ints) {
+        if (s->nl) CU(cudaFree(s->nl));
+        s->nl = nullptr;
+        s->nl_ints = 0;
+        cudaError_t e = cudaMalloc(&s->nl, need * sizeof(int));
+        if (e != cudaSuccess) return fail(s, TDPD_ENOMEM, "neighbour lists (%zu bytes): %s", need * sizeof(int), cudaGetErrorString(e));
+        s->nl_ints = need;
+    }
+    s->nl_cap = cap;
+    launch_list_build(list_args(s, s->buf[1], s->rb_all, cap), st);
+    CU(cudaGetLastError());
+    return TDPD_OK;
+}
+
 tdpd_status autotune(tdpd_sys *s)
 {
     cudaStream_t st = exec_stream(s);
@@ -565,7 +655,9 @@ tdpd_status autotune(tdpd_sys *s)
     for (int lpp = 1; lpp <= 32; lpp *= 2) {
         if (lpp > 1 && (long)s->N * lpp > 4000000L) break;
         s->lpp = lpp;
-        const PairArgs a = pair_args(s, s->buf[1], 0, s->tile_sum[1]);
+        tdpd_status rc;
+        if (s->use_list && (rc = prepare_list(s))) return rc;
+        const PairArgs a = pair_args(s, s->buf[1], 0, s->tile_sum[1], s->disp[1]);
         launch_pair(a, st);                       // warm-up
         float tot = 0.f;
         for (int k = 0; k < 3; ++k) {
@@ -587,6 +679,8 @@ tdpd_status autotune(tdpd_sys *s)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     s->lpp = best_lpp;
+    tdpd_status rc;
+    if (s->use_list && (rc = prepare_list(s))) return rc;
     return init_state(s);
 }
 
@@ -609,6 +703,8 @@ tdpd_status commit(tdpd_sys *s)
     if (s->reps.empty()) return fail(s, TDPD_ESTATE, "no replicas");
     s->ns = s->reps[0].cfg.n_species;
     int N = 0, NC = 0;
+    const float skin = s->skin < 0.0f ? DEFAULT_SKIN : s->skin;
+    s->use_list = skin > 0.0f;
     s->rep_pbase.clear();
     s->rep_rbc0.clear();
     s->h_rbcs.clear();
@@ -626,10 +722,19 @@ tdpd_status commit(tdpd_sys *s)
         for (int c = 0; c < 3; ++c)
             if ((double)R.cfg.L[c] < 3.0 * rcut * 1.0001)
                 return fail(s, TDPD_EINVAL, "replica %zu: box edge %g is shorter than 3 cut-offs (%g)", r, R.cfg.L[c], rcut);
-        // cells of edge >= rcut/m; a periodic axis needs 2m+1 distinct cells
+        // cells of edge >= (rcut + skin)/m; a periodic axis needs 2m+1
+        // distinct cells, and a list partner must stay the nearest image
+        // (rcut + 2 skin <= L/2), so small boxes get a smaller skin
         R.m = R.cfg.cells_per_cutoff > 0 ? R.cfg.cells_per_cutoff : 2;
+        float sk = s->use_list ? skin : 0.0f;
         for (int c = 0; c < 3; ++c) {
-            R.nc[c] = (int)std::floor((double)R.cfg.L[c] * R.m / ((double)rcut * 1.0001));
+            const double L = R.cfg.L[c];
+            if (R.cfg.periodic[c]) sk = std::min(sk, (float)(0.999 * (0.5 * L - rcut) / 2));
+            sk = std::min(sk, (float)(0.999 * (L * R.m / ((2 * R.m + 1) * 1.0001) - rcut)));
+        }
+        R.skin = std::max(sk, 0.0f);
+        for (int c = 0; c < 3; ++c) {
+            R.nc[c] = (int)std::floor((double)R.cfg.L[c] * R.m / ((double)(rcut + R.skin) * 1.0001));
             if (R.nc[c] < 2 * R.m + 1) return fail(s, TDPD_EINVAL, "replica %zu: too few cells", r);
         }
         const long ncells = (long)R.nc[0] * R.nc[1] * R.nc[2];
@@ -793,10 +898,29 @@ tdpd_status commit(tdpd_sys *s)
         if ((rc = upload(s, s->d_wstat, ws.data(), N))) return rc;
         CU(cudaMemsetAsync(s->d_obs_done, 0, sizeof(unsigned), exec_stream(s)));
     }
+    if (s->use_list) {
+        const int nrep = (int)s->reps.size();
+        if ((rc = dalloc(s, &s->xb, N)) || (rc = dalloc(s, &s->disp[0], nrep)) || (rc = dalloc(s, &s->disp[1], nrep)) ||
+            (rc = dalloc(s, &s->rb, nrep + 1)) || (rc = dalloc(s, &s->rb_all, nrep + 1)) ||
+            (rc = dalloc(s, &s->nlc, (size_t)N * 32)) || (rc = dalloc(s, &s->builds, nrep)))
+            return rc;
+        CU(cudaMemsetAsync(s->builds, 0, sizeof(uint32_t) * nrep, exec_stream(s)));
+        std::vector<uint32_t> ones(nrep + 1, 1u);
+        if ((rc = upload(s, s->rb_all, ones.data(), ones.size()))) return rc;
+        CU(cudaMemsetAsync(s->disp[0], 0, sizeof(uint32_t) * nrep, exec_stream(s)));
+        CU(cudaMemsetAsync(s->disp[1], 0, sizeof(uint32_t) * nrep, exec_stream(s)));
+    }
     s->step = 0;
-    if ((rc = init_state(s))) return rc;
     if (s->lanes_fixed > 0) s->lpp = s->lanes_fixed;
-    else if ((rc = autotune(s))) return rc;
+    if (s->use_list) {
+        // a sorted state for the counting pass that sizes the lists
+        s->use_list = false;
+        rc = init_state(s);
+        s->use_list = true;
+        if (rc || (rc = prepare_list(s))) return rc;
+    }
+    if ((rc = init_state(s))) return rc;
+    if (s->lanes_fixed == 0 && (rc = autotune(s))) return rc;
     const int nk = (int)step_kernels(s).size();
     for (int k = 0; k <= nk; ++k) CU(cudaEventCreate(&s->ev[k]));
     s->n_ev = nk + 1;
@@ -1085,7 +1209,30 @@ tdpd_status tdpd_set_lanes(tdpd_sys *s, int lanes)
     return TDPD_OK;
 }
 
+tdpd_status tdpd_set_skin(tdpd_sys *s, float skin)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed) return fail(s, TDPD_ESTATE, "the skin is fixed after commit");
+    if (!(skin >= 0.0f && skin < 1e3f)) return fail(s, TDPD_EINVAL, "skin must be finite and >= 0");
+    s->skin = skin;
+    return TDPD_OK;
+}
+
 tdpd_status tdpd_commit(tdpd_sys *s) { return ensure(s); }
+
+tdpd_status tdpd_list_rebuilds(tdpd_sys *s, int r, int64_t *out)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    if (r < 0 || r >= (int)s->reps.size() || !out) return fail(s, TDPD_EINVAL, "bad replica or output");
+    uint32_t v = 0;
+    if (s->use_list) {
+        CU(cudaMemcpyAsync(&v, s->builds + r, sizeof v, cudaMemcpyDeviceToHost, exec_stream(s)));
+        CU(cudaStreamSynchronize(exec_stream(s)));
+    }
+    *out = v;
+    return TDPD_OK;
+}
 
 tdpd_status tdpd_step(tdpd_sys *s, int n)
 {
@@ -1136,7 +1283,8 @@ tdpd_status tdpd_replica_status(tdpd_sys *s, int32_t *status)
     std::vector<uint32_t> w(s->reps.size());
     CU(cudaMemcpyAsync(w.data(), s->errw, sizeof(uint32_t) * w.size(), cudaMemcpyDeviceToHost, exec_stream(s)));
     CU(cudaStreamSynchronize(exec_stream(s)));
-    for (size_t r = 0; r < w.size(); ++r) status[r] = w[r] ? TDPD_ENONFINITE : TDPD_OK;
+    for (size_t r = 0; r < w.size(); ++r)
+        status[r] = (w[r] & 1u) ? TDPD_ENONFINITE : (w[r] & 2u) ? TDPD_EOVERFLOW : TDPD_OK;
     return TDPD_OK;
 }
 
@@ -1147,7 +1295,8 @@ tdpd_status tdpd_sync(tdpd_sys *s)
     std::vector<int32_t> st(s->reps.size());
     if ((rc = tdpd_replica_status(s, st.data()))) return rc;
     for (size_t r = 0; r < st.size(); ++r)
-        if (st[r]) return fail(s, TDPD_ENONFINITE, "replica %zu produced a non-finite force", r);
+        if (st[r] == TDPD_ENONFINITE) return fail(s, TDPD_ENONFINITE, "replica %zu produced a non-finite force", r);
+        else if (st[r]) return fail(s, (tdpd_status)st[r], "replica %zu: a neighbour list overflowed", r);
     return TDPD_OK;
 }
 

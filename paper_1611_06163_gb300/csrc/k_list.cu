@@ -1,0 +1,144 @@
+// Verlet neighbour lists for the pair kernel (the list of Sec. 3.1 that is
+// rebuilt every few steps rather than every step).
+//
+// A list holds, per lane of the pair kernel, the slots of the partners within
+// rlist = rcut + skin of the particle at build time, found over the same cell
+// stencil rows that lane would walk (rows s, s+LPP, ... of its particle). As
+// long as no particle of the replica has moved more than skin/2 since the
+// build, every pair closer than rcut is in the list. The pair kernel's
+// epilogue records the largest displacement of each replica's next positions;
+// the next step rebuilds exactly the replicas that crossed skin/2, so a
+// replica's rebuild steps -- and its summation order -- do not depend on the
+// other replicas of a batch.
+//
+// Layout: entry k of lane l of warp w at nl[(w * cap + k) * 32 + l], so the
+// 32 lanes of a warp read one 128-byte line per entry.
+#include "launch.h"
+
+namespace tdpd {
+
+__global__ void k_rebuild_decide(const uint32_t *__restrict__ disp, uint32_t *disp_clear, uint32_t *rb,
+                                 const RepParams *__restrict__ reps, int n_rep, int force, uint32_t *step_ctr,
+                                 uint32_t *builds)
+{
+    pdl_enter();
+    int any = 0;
+    for (int r = threadIdx.x; r < n_rep; r += blockDim.x) {
+        const bool b = force || __uint_as_float(disp[r]) > reps[r].half_skin2;
+        rb[r] = b ? 1u : 0u;
+        disp_clear[r] = 0u;
+        if (b) builds[r] += 1u;
+        any |= b;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        rb[n_rep] = any ? 1u : 0u;
+        *step_ctr += 1u;
+    }
+}
+
+// Cell and rank of the position each particle will have at the next force
+// evaluation (the predictor of the gather), for the sort of a rebuild step.
+__global__ void k_bin_next(Buffers b, const RepParams *__restrict__ reps, int n, int *count, int *tile_sum,
+                           int2 *cellrank, const uint32_t *any)
+{
+    pdl_enter();
+    if (!*any) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = -1;
+    if (k < n) {
+        const float4 p = b.pos[k];
+        const float4 v = b.vel[k];
+        const RepParams &P = reps[wbits(v.w)];
+        const int type = (int)((uint32_t)wbits(p.w) >> 24);
+        float3 rn = make_float3(p.x, p.y, p.z);
+        if (!((P.frozen_mask >> type) & 1u)) {
+            bool flip;
+            rn = predict_pos(P, p, v, b.frc[k], flip);
+        }
+        c = cell_of(P, rn.x, rn.y, rn.z);
+        const int rank = atomicAdd(count + c, 1);
+        cellrank[k] = make_int2(c, rank);
+    }
+    add_tile_count(tile_sum, c);
+}
+
+template <int LPP>
+__global__ void __launch_bounds__(128) k_list_build(ListArgs A)
+{
+    pdl_enter();
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / LPP, sub = gt % LPP;
+    if (i >= A.n) return;
+    const float4 pi = A.pos[i];
+    const int rep = wbits(A.vel[i].w);
+    if (!A.rb[rep]) return;
+    const RepParams &P = A.reps[rep];
+    const int m = P.m_stencil, width = 2 * m + 1, nrow = width * width;
+    const int cx = cell_coord(pi.x, P.cell_scale[0], P.nc[0]);
+    const int cy = cell_coord(pi.y, P.cell_scale[1], P.nc[1]);
+    const int cz = cell_coord(pi.z, P.cell_scale[2], P.nc[2]);
+    const float oy = pi.y - (float)cy * P.h[1], oz = pi.z - (float)cz * P.h[2];
+    const float eps = 1e-4f * fmaxf(P.h[0], fmaxf(P.h[1], P.h[2]));
+    const float rl2 = P.rlist2;
+    int *out = A.nl + (size_t)(gt >> 5) * A.cap * 32 + (gt & 31);
+    int c = 0;
+    for (int row = sub; row < nrow; row += LPP) {
+        RowSeg g = {{0, 0}, {0, 0}, 0.f, 0.f, 0.f};
+        if (!stencil_row(P, A.cell_start, pi, cx, cy, cz, row, oy, oz, eps, rl2 * 1.0002f, g)) continue;
+        const float py = pi.y + g.sy, pz = pi.z + g.sz;
+#pragma unroll
+        for (int sg = 0; sg < 2; ++sg) {
+            const float px = pi.x + (sg ? g.sx1 : 0.f);
+            const int je = g.je[sg];
+            // four candidates per trip, their loads in flight together;
+            // appended in slot order
+            for (int j0 = g.jb[sg]; j0 < je; j0 += 4) {
+                float4 pj[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) pj[u] = j0 + u < je ? A.pos[j0 + u] : make_float4(1e30f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u;
+                    const float dx = px - pj[u].x, dy = py - pj[u].y, dz = pz - pj[u].z;
+                    if (j < je && j != i && dx * dx + dy * dy + dz * dz < rl2) {
+                        if (c < A.cap) out[(size_t)c * 32] = j;
+                        ++c;
+                    }
+                }
+            }
+        }
+    }
+    A.nlc[gt] = A.cap > 0 ? min(c, A.cap) : c;
+    if (A.cap > 0 && c > A.cap) atomicOr(A.err + rep, 2u);
+    if (sub == 0) A.xb[i] = pi;
+}
+
+void launch_rebuild_decide(const uint32_t *disp, uint32_t *disp_clear, uint32_t *rb, const RepParams *reps,
+                           int n_rep, int force, uint32_t *step_ctr, uint32_t *builds, cudaStream_t st)
+{
+    launch_pdl(k_rebuild_decide, 1, 256, st, disp, disp_clear, rb, reps, n_rep, force, step_ctr, builds);
+}
+
+void launch_bin_next(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum, int2 *cellrank,
+                     const uint32_t *any, cudaStream_t st)
+{
+    if (n <= 0) return;
+    launch_pdl(k_bin_next, (n + 255) / 256, 256, st, b, reps, n, count, tile_sum, cellrank, any);
+}
+
+void launch_list_build(const ListArgs &a, cudaStream_t st)
+{
+    if (a.n <= 0) return;
+    const int g = (int)(((long)a.n * a.lpp + 127) / 128);
+    switch (a.lpp) {
+    case 1: launch_pdl(k_list_build<1>, g, 128, st, a); break;
+    case 2: launch_pdl(k_list_build<2>, g, 128, st, a); break;
+    case 4: launch_pdl(k_list_build<4>, g, 128, st, a); break;
+    case 8: launch_pdl(k_list_build<8>, g, 128, st, a); break;
+    case 16: launch_pdl(k_list_build<16>, g, 128, st, a); break;
+    default: launch_pdl(k_list_build<32>, g, 128, st, a); break;
+    }
+}
+
+}  // namespace tdpd

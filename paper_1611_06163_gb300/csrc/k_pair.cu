@@ -1,13 +1,19 @@
-// Pairwise tDPD force (Eq. 3) and Fickian flux (Eq. 6) over the cell list,
-// fused with the velocity-Verlet corrector and the binning of the next step.
+// Pairwise tDPD force (Eq. 3) and Fickian flux (Eq. 6), fused with the
+// velocity-Verlet corrector. Two ways to find the partners:
+//   - cell mode: over the cell stencil, every step; the epilogue also bins
+//     the next predicted position for the next step's sort;
+//   - list mode: over the lane's Verlet list (k_list.cu), separations by
+//     minimum image; the epilogue records how far the next position has moved
+//     from the list build instead of binning.
 //
-// Layout of the work:
+// Layout of the work in cell mode:
 //   - cells have edge >= rcut/m, so the partners of particle i lie in the
 //     (2m+1)^2 rows (dy, dz) of 2m+1 cells along x around its cell; a row is
 //     one contiguous range of the cell-sorted arrays (two at a periodic wrap);
 //   - LPP lanes share particle i and split its rows (lane s takes rows
 //     s, s+LPP, ...); a butterfly of shuffles sums their partial results in a
 //     fixed order, so small systems still fill the GPU;
+//   - (list mode: lane s holds the partners found in those rows at build)
 //   - the flux (about a quarter of the candidates) is summed inline by the
 //     lane that found it; the force pairs (a few per cent of the candidates,
 //     each needing a TEA draw) are pushed to a per-warp queue and evaluated
@@ -98,7 +104,7 @@ __device__ __forceinline__ void drain(WarpSmem &W, int head, int n, const RepPar
 
 }  // namespace
 
-template <int NS, int LPP>
+template <int NS, int LPP, bool LIST>
 __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
 {
     pdl_enter();
@@ -160,120 +166,118 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
 
     __syncwarp();
     int qhead = 0, qcount = 0;
-    // rows are split round-robin over the LPP lanes of the particle; the loop
-    // trip counts are warp-uniform (maxima over the warp)
-    const int kmax = (nrow + LPP - 1) / LPP;
-    const int kw = __reduce_max_sync(0xffffffffu, valid ? kmax : 0);
-    for (int k = 0; k < kw; ++k) {
-        const int row = sub + k * LPP;
-        int jb[2] = {0, 0}, je[2] = {0, 0};
-        float sx[2] = {0.f, 0.f};
-        float sy = 0.f, sz = 0.f;
-        bool rok = valid && row < nrow;
-        if (rok) {
-            const int dy = row % width - m, dz = row / width - m;
-            // distance from particle i to the slab of the row's cells, minus a
-            // margin for the rounding of the cell assignment
-            const float ay = dy == 0 ? 0.f : (dy > 0 ? (float)dy * hy - oy : oy - (float)(dy + 1) * hy);
-            const float az = dz == 0 ? 0.f : (dz > 0 ? (float)dz * hz - oz : oz - (float)(dz + 1) * hz);
-            const float by = fmaxf(ay - eps, 0.f), bz = fmaxf(az - eps, 0.f);
-            const float rem = rtrim2 - by * by - bz * bz;
-            int y = cy + dy, z = cz + dz;
-            if (rem <= 0.f) rok = false;
-            if (y < 0) { y += P.nc[1]; sy = P.L[1]; }
-            else if (y >= P.nc[1]) { y -= P.nc[1]; sy = -P.L[1]; }
-            if (z < 0) { if (P.periodic[2]) { z += P.nc[2]; sz = P.L[2]; } else rok = false; }
-            else if (z >= P.nc[2]) { if (P.periodic[2]) { z -= P.nc[2]; sz = -P.L[2]; } else rok = false; }
-            if (rok) {
-                const float rx = sqrtf(rem) + eps;
-                const int x0 = max(cx - m, __float2int_rd((pi.x - rx) * P.cell_scale[0]));
-                const int x1 = min(cx + m, __float2int_rd((pi.x + rx) * P.cell_scale[0]));
-                const int base = P.cell_base + (z * P.nc[1] + y) * P.nc[0];
-                const int nx = P.nc[0];
-                if (x0 >= 0 && x1 < nx) {
-                    jb[0] = cs[base + x0];
-                    je[0] = cs[base + x1 + 1];
-                } else if (x0 < 0) {
-                    jb[0] = cs[base];
-                    je[0] = cs[base + x1 + 1];
-                    jb[1] = cs[base + nx + x0];
-                    je[1] = cs[base + nx];
-                    sx[1] = P.L[0];
-                } else {
-                    jb[0] = cs[base + x0];
-                    je[0] = cs[base + nx];
-                    jb[1] = cs[base];
-                    je[1] = cs[base + x1 - nx + 1];
-                    sx[1] = -P.L[0];
+    // one candidate j at separation (dx, dy, dz) from i, with its id/type
+    // bits wj and first concentration cj0 loaded
+    auto consider = [&](bool live, int j, float dx, float dy, float dz, uint32_t wj, float cj0) {
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const bool near = live && r2 > 0.0f;
+        // flux without a branch: the terms of candidates outside r_cc (or of
+        // dead lanes) are computed and dropped by the select
+        const bool inc = near && r2 < rcc2;
+        const float r = r2 * rsqrtf(r2);
+        const float w = 1.0f - r * inv_rcc;
+        const float wdc = sc2 ? w * w : __powf(w, s_c);
+        const int tj = (int)(wj >> 24);
+        if (NS == 1) {
+            float kap = kr[0];
+            kap = tj == 1 ? kr[1] : kap;
+            kap = tj == 2 ? kr[2] : kap;
+            kap = tj == 3 ? kr[3] : kap;
+            const float qn = q[0] - kap * wdc * (ci[0] - cj0);
+            q[0] = inc ? qn : q[0];
+        } else if (inc) {
+            const float *kap = kap_row + tj * ns;
+            q[0] -= kap[0] * wdc * (ci[0] - cj0);
+            for (int s = 1; s < ns; ++s)
+                q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
+        }
+        const bool push = near && r2 < rc2;
+        const unsigned bal = __ballot_sync(0xffffffffu, push);
+        if (push) {
+            const int slot = (qhead + qcount + __popc(bal & ((1u << lane) - 1u))) & (QCAP - 1);
+            int4 *e = reinterpret_cast<int4 *>(&W.q[slot]);
+            e[0] = make_int4(j, (int)wj, lane, 0);
+            e[1] = make_int4(__float_as_int(dx), __float_as_int(dy), __float_as_int(dz), __float_as_int(r2));
+        }
+        qcount += __popc(bal);
+        if (qcount >= 32) {
+            __syncwarp();
+            drain(W, qhead, 32, A.reps, vt, step_ctr, lane);
+            qhead = (qhead + 32) & (QCAP - 1);
+            qcount -= 32;
+        }
+    };
+    if constexpr (LIST) {
+        // the lane's list, UNR entries per trip (index loads, then partner
+        // loads, then the visits in list order); separations by minimum image
+        const int *__restrict__ nl = A.nl + (size_t)(gt >> 5) * A.cap * 32 + (gt & 31);
+        const int cnt = valid ? A.nlc[gt] : 0;
+        const int nit = __reduce_max_sync(0xffffffffu, cnt);
+        const float Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];
+        const float iLx = P.inv_L[0], iLy = P.inv_L[1], iLz = P.inv_L[2];
+        for (int t = 0; t < nit; t += UNR) {
+            int jj[UNR];
+            float4 pp[UNR];
+            float cc[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) jj[u] = t + u < cnt ? nl[(size_t)(t + u) * 32] : 0;
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                pp[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                cc[u] = 0.f;
+                if (t + u < cnt) {
+                    pp[u] = pos[jj[u]];
+                    cc[u] = Ct[(size_t)jj[u] * ns];
                 }
             }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u)
+                if (u == 0 || t + u < nit) {
+                    float dx = pi.x - pp[u].x, dy = pi.y - pp[u].y, dz = pi.z - pp[u].z;
+                    dx = __fmaf_rn(-Lx, rintf(dx * iLx), dx);
+                    dy = __fmaf_rn(-Ly, rintf(dy * iLy), dy);
+                    dz = __fmaf_rn(-Lz, rintf(dz * iLz), dz);
+                    consider(t + u < cnt, jj[u], dx, dy, dz, (uint32_t)wbits(pp[u].w), cc[u]);
+                }
         }
+    } else {
+        // rows are split round-robin over the LPP lanes of the particle; the
+        // loop trip counts are warp-uniform (maxima over the warp)
+        const int kmax = (nrow + LPP - 1) / LPP;
+        const int kw = __reduce_max_sync(0xffffffffu, valid ? kmax : 0);
+        for (int k = 0; k < kw; ++k) {
+            const int row = sub + k * LPP;
+            RowSeg g = {{0, 0}, {0, 0}, 0.f, 0.f, 0.f};
+            if (valid && row < nrow) stencil_row(P, cs, pi, cx, cy, cz, row, oy, oz, eps, rtrim2, g);
+            const float py = pi.y + g.sy, pz = pi.z + g.sz;
 #pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-            const float px = pi.x + sx[sg], py = pi.y + sy, pz = pi.z + sz;
-            const int j0 = jb[sg];
-            const int len = je[sg] - j0;
-            const int nit = __reduce_max_sync(0xffffffffu, len);
-            // one candidate j whose position and first concentration are loaded
-            auto visit = [&](bool live, int j, const float4 &pj, float cj0) {
-                const float dx = px - pj.x, dy = py - pj.y, dz = pz - pj.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                const uint32_t wj = (uint32_t)wbits(pj.w);
-                const bool near = live && r2 > 0.0f;
-                // flux without a branch: the terms of candidates outside r_cc
-                // (or of dead lanes) are computed and dropped by the select
-                const bool inc = near && r2 < rcc2;
-                const float r = r2 * rsqrtf(r2);
-                const float w = 1.0f - r * inv_rcc;
-                const float wdc = sc2 ? w * w : __powf(w, s_c);
-                const int tj = (int)(wj >> 24);
-                if (NS == 1) {
-                    float kap = kr[0];
-                    kap = tj == 1 ? kr[1] : kap;
-                    kap = tj == 2 ? kr[2] : kap;
-                    kap = tj == 3 ? kr[3] : kap;
-                    const float qn = q[0] - kap * wdc * (ci[0] - cj0);
-                    q[0] = inc ? qn : q[0];
-                } else if (inc) {
-                    const float *kap = kap_row + tj * ns;
-                    q[0] -= kap[0] * wdc * (ci[0] - cj0);
-                    for (int s = 1; s < ns; ++s)
-                        q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
-                }
-                const bool push = near && r2 < rc2;
-                const unsigned bal = __ballot_sync(0xffffffffu, push);
-                if (push) {
-                    const int slot = (qhead + qcount + __popc(bal & ((1u << lane) - 1u))) & (QCAP - 1);
-                    int4 *e = reinterpret_cast<int4 *>(&W.q[slot]);
-                    e[0] = make_int4(j, (int)wj, lane, 0);
-                    e[1] = make_int4(__float_as_int(dx), __float_as_int(dy), __float_as_int(dz), __float_as_int(r2));
-                }
-                qcount += __popc(bal);
-                if (qcount >= 32) {
-                    __syncwarp();
-                    drain(W, qhead, 32, A.reps, vt, step_ctr, lane);
-                    qhead = (qhead + 32) & (QCAP - 1);
-                    qcount -= 32;
-                }
-            };
-            // UNR candidates per trip: their loads are all in flight before
-            // the first is used; the visits keep the order of t, so each
-            // lane's queue entries come in the same order as one per trip
-            for (int t = 0; t < nit; t += UNR) {
-                float4 pp[UNR];
-                float cc[UNR];
+            for (int sg = 0; sg < 2; ++sg) {
+                const float px = pi.x + (sg ? g.sx1 : 0.f);
+                const int j0 = g.jb[sg];
+                const int len = g.je[sg] - j0;
+                const int nit = __reduce_max_sync(0xffffffffu, len);
+                // UNR candidates per trip: their loads are all in flight
+                // before the first is used; the visits keep the order of t,
+                // so each lane's queue entries come in the same order as one
+                // per trip
+                for (int t = 0; t < nit; t += UNR) {
+                    float4 pp[UNR];
+                    float cc[UNR];
 #pragma unroll
-                for (int u = 0; u < UNR; ++u) {
-                    pp[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    cc[u] = 0.f;
-                    if (t + u < len) {
-                        pp[u] = pos[j0 + t + u];
-                        cc[u] = Ct[(size_t)(j0 + t + u) * ns];
+                    for (int u = 0; u < UNR; ++u) {
+                        pp[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        cc[u] = 0.f;
+                        if (t + u < len) {
+                            pp[u] = pos[j0 + t + u];
+                            cc[u] = Ct[(size_t)(j0 + t + u) * ns];
+                        }
                     }
-                }
 #pragma unroll
-                for (int u = 0; u < UNR; ++u)
-                    if (u == 0 || t + u < nit) visit(t + u < len, j0 + t + u, pp[u], cc[u]);
+                    for (int u = 0; u < UNR; ++u)
+                        if (u == 0 || t + u < nit)
+                            consider(t + u < len, j0 + t + u, px - pp[u].x, py - pp[u].y, pz - pp[u].z,
+                                     (uint32_t)wbits(pp[u].w), cc[u]);
+                }
             }
         }
     }
@@ -293,6 +297,7 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
         for (int s = 0; s < ns; ++s) q[s] += __shfl_xor_sync(0xffffffffu, q[s], o);
     }
     int cell = -1;
+    float disp2 = 0.0f;
     if (valid && sub == 0) {
         // ---- epilogue: membrane force, sources, corrector, next binning
         const int bi = wbits(vi.w);
@@ -345,36 +350,67 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
             A.mx[gi] = make_float4(rn.x, rn.y, rn.z, 0.0f);
             A.mv[gi] = vtn;
         }
-        cell = cell_of(P, rn.x, rn.y, rn.z);
-        const int rank = atomicAdd(A.count + cell, 1);
-        A.cellrank[i] = make_int2(cell, rank);
+        if constexpr (LIST) {
+            // displacement of the next position from the list build
+            const float4 xb = A.xb[i];
+            float ex = rn.x - xb.x, ey = rn.y - xb.y, ez = rn.z - xb.z;
+            ex = __fmaf_rn(-P.L[0], rintf(ex * P.inv_L[0]), ex);
+            ey = __fmaf_rn(-P.L[1], rintf(ey * P.inv_L[1]), ey);
+            ez = __fmaf_rn(-P.L[2], rintf(ez * P.inv_L[2]), ez);
+            disp2 = ex * ex + ey * ey + ez * ez;
+        } else {
+            cell = cell_of(P, rn.x, rn.y, rn.z);
+            const int rank = atomicAdd(A.count + cell, 1);
+            A.cellrank[i] = make_int2(cell, rank);
+        }
     }
-    add_tile_count(A.tile_sum, cell);
+    if constexpr (LIST) {
+        // largest squared displacement per replica (non-negative floats order
+        // like their bit patterns); one atomic per warp when it has one replica
+        const uint32_t bits = __float_as_uint(disp2);
+        const int rep0 = __shfl_sync(0xffffffffu, rep, 0);
+        if (__all_sync(0xffffffffu, rep == rep0)) {
+            const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
+            if (lane == 0) atomicMax(A.disp_next + rep0, mx);
+        } else if (valid && sub == 0) {
+            atomicMax(A.disp_next + rep, bits);
+        }
+    } else {
+        add_tile_count(A.tile_sum, cell);
+    }
 }
 
-template <int NS>
+template <int NS, bool LIST>
 static void launch_ns(const PairArgs &a, cudaStream_t st)
 {
     const int t = 128;
     const long threads = (long)a.n * a.lpp;
     const int g = (int)((threads + t - 1) / t);
     switch (a.lpp) {
-    case 1: launch_pdl(k_pair<NS, 1>, g, t, st, a); break;
-    case 2: launch_pdl(k_pair<NS, 2>, g, t, st, a); break;
-    case 4: launch_pdl(k_pair<NS, 4>, g, t, st, a); break;
-    case 8: launch_pdl(k_pair<NS, 8>, g, t, st, a); break;
-    case 16: launch_pdl(k_pair<NS, 16>, g, t, st, a); break;
-    default: launch_pdl(k_pair<NS, 32>, g, t, st, a); break;
+    case 1: launch_pdl(k_pair<NS, 1, LIST>, g, t, st, a); break;
+    case 2: launch_pdl(k_pair<NS, 2, LIST>, g, t, st, a); break;
+    case 4: launch_pdl(k_pair<NS, 4, LIST>, g, t, st, a); break;
+    case 8: launch_pdl(k_pair<NS, 8, LIST>, g, t, st, a); break;
+    case 16: launch_pdl(k_pair<NS, 16, LIST>, g, t, st, a); break;
+    default: launch_pdl(k_pair<NS, 32, LIST>, g, t, st, a); break;
     }
 }
 
 void launch_pair(const PairArgs &a, cudaStream_t st)
 {
     if (a.n <= 0) return;
-    switch (a.ns) {
-    case 1: launch_ns<1>(a, st); break;
-    case 2: launch_ns<2>(a, st); break;
-    default: launch_ns<0>(a, st); break;
+    if (a.nl) {
+        switch (a.ns) {
+        case 1: launch_ns<1, true>(a, st); break;
+        case 2: launch_ns<2, true>(a, st); break;
+        default: launch_ns<0, true>(a, st); break;
+        }
+    } else {
+        switch (a.ns) {
+        case 1: launch_ns<1, false>(a, st); break;
+        case 2: launch_ns<2, false>(a, st); break;
+        default: launch_ns<0, false>(a, st); break;
+        }
     }
 }
 

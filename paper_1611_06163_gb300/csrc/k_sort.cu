@@ -1,5 +1,7 @@
-// Cell-list binning and deterministic counting sort (the reorder of Sec. 3.1,
-// rebuilt every step instead of a Verlet list every few steps).
+// Cell-list binning and deterministic counting sort (the reorder of Sec. 3.1).
+// In cell mode the sort runs every step; in neighbour-list mode only in the
+// steps that rebuild the list, and the gather then keeps every slot's
+// particle in the other steps (it still applies the predictor).
 //
 // Order within a cell is by particle id, so the sorted layout -- and with it
 // every floating-point summation order -- depends only on the state, not on
@@ -30,9 +32,12 @@ __global__ void k_bin_init(Buffers b, const RepParams *__restrict__ reps, int n,
 // totals were accumulated by the binning, so each CTA finds its offset by
 // summing the totals of the tiles before it -- no inter-CTA waiting.
 __global__ void __launch_bounds__(1024) k_scan(int *count, int *cell_start, const int *tile_read,
-                                               int *tile_clear, uint32_t *step_ctr, int inc)
+                                               int *tile_clear, uint32_t *step_ctr, int inc,
+                                               const uint32_t *any)
 {
     pdl_enter();
+    if (blockIdx.x == 0 && threadIdx.x == 0 && inc) *step_ctr += 1u;
+    if (any && !*any) return;
     __shared__ int wsum[32];
     __shared__ int base_sh;
     const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -81,15 +86,14 @@ __global__ void __launch_bounds__(1024) k_scan(int *count, int *cell_start, cons
     reinterpret_cast<int4 *>(cell_start + (size_t)t * SCAN_TILE)[tid] = out;
     *c4 = make_int4(0, 0, 0, 0);
     if (tid == 0) tile_clear[t] = 0;
-    if (t == 0 && tid == 0 && inc) *step_ctr += 1u;
 }
 
 __global__ void k_scatter_keys(const float4 *__restrict__ pos, const int2 *__restrict__ cellrank,
-                               const int *__restrict__ cell_start, int2 *keys, int n)
+                               const int *__restrict__ cell_start, int2 *keys, int n, const uint32_t *any)
 {
     pdl_enter();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+    if (k >= n || (any && !*any)) return;
     int2 cr = cellrank[k];
     int id = wbits(pos[k].w) & ID_MASK;
     keys[cell_start[cr.x] + cr.y] = make_int2(id, k);
@@ -102,19 +106,33 @@ template <int NS>
 __global__ void k_rank_gather(Buffers cur, Buffers nxt, const RepParams *__restrict__ reps,
                               const int2 *__restrict__ keys, const int2 *__restrict__ cellrank,
                               const int *__restrict__ cell_start, int *inv, int n, int ns_rt,
-                              int predict)
+                              int predict, const uint32_t *__restrict__ rb, int n_rep, int *tile_zero,
+                              int n_tiles)
 {
     pdl_enter();
     const int ns = NS > 0 ? NS : ns_rt;
-    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool any = !rb || rb[n_rep] != 0u;
+    if (tile_zero && any)
+        for (int t = d; t < n_tiles; t += gridDim.x * blockDim.x) tile_zero[t] = 0;
     if (d >= n) return;
-    int2 key = keys[d];
-    const int id = key.x, src = key.y;
-    const int c = cellrank[src].x;
-    const int lo = cell_start[c], hi = cell_start[c + 1];
-    int rank = 0;
-    for (int e = lo; e < hi; ++e) rank += (keys[e].x < id);
-    const int dst = lo + rank;
+    int id, src, dst;
+    if (any) {
+        const int2 key = keys[d];
+        id = key.x;
+        src = key.y;
+        const int c = cellrank[src].x;
+        const int lo = cell_start[c], hi = cell_start[c + 1];
+        int rank = 0;
+        for (int e = lo; e < hi; ++e) rank += (keys[e].x < id);
+        dst = lo + rank;
+        // a replica that keeps its list keeps its slots (its cells map onto
+        // its own slot range, so this is a permutation of that range)
+        if (rb && rb[wbits(cur.vel[src].w)] == 0u) dst = src;
+    } else {
+        src = dst = d;
+        id = wbits(cur.pos[d].w) & ID_MASK;
+    }
 
     float4 p = cur.pos[src];
     float4 v = cur.vel[src];
@@ -158,29 +176,30 @@ void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count,
 }
 
 void launch_scan(int *count, int *cell_start, int n_tiles, const int *tile_read, int *tile_clear,
-                 uint32_t *step_ctr, int inc, cudaStream_t st)
+                 uint32_t *step_ctr, int inc, cudaStream_t st, const uint32_t *any)
 {
     static_assert(SCAN_TILE == 4 * 1024, "one CTA of 1024 threads scans four cells per thread");
-    launch_pdl(k_scan, n_tiles, 1024, st, count, cell_start, tile_read, tile_clear, step_ctr, inc);
+    launch_pdl(k_scan, n_tiles, 1024, st, count, cell_start, tile_read, tile_clear, step_ctr, inc, any);
 }
 
 void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *cell_start,
-                         int2 *keys, int n, cudaStream_t st)
+                         int2 *keys, int n, cudaStream_t st, const uint32_t *any)
 {
     if (n <= 0) return;
-    launch_pdl(k_scatter_keys, nblk(n, 256), 256, st, cur.pos, cellrank, cell_start, keys, n);
+    launch_pdl(k_scatter_keys, nblk(n, 256), 256, st, cur.pos, cellrank, cell_start, keys, n, any);
 }
 
 void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams *reps,
                         const int2 *keys, const int2 *cellrank, const int *cell_start, int *inv,
-                        int n, int ns, int predict, cudaStream_t st)
+                        int n, int ns, int predict, cudaStream_t st, const uint32_t *rb, int n_rep,
+                        int *tile_zero, int n_tiles)
 {
     if (n <= 0) return;
     const int g = nblk(n, 256);
     switch (ns) {
-    case 1: launch_pdl(k_rank_gather<1>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict); break;
-    case 2: launch_pdl(k_rank_gather<2>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict); break;
-    default: launch_pdl(k_rank_gather<0>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict); break;
+    case 1: launch_pdl(k_rank_gather<1>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles); break;
+    case 2: launch_pdl(k_rank_gather<2>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles); break;
+    default: launch_pdl(k_rank_gather<0>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles); break;
     }
 }
 

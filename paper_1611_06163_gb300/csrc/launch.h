@@ -49,7 +49,26 @@ struct PairArgs {
     int n;                       // particles (slots)
     int ns;                      // species (runtime value for the generic path)
     int integrate;               // 0: forces only (commit / set_state); 1: full step
-    int lpp;                     // lanes per particle: 1, 2, 4 or 8
+    int lpp;                     // lanes per particle: 1, 2, 4, 8, 16 or 32
+    // neighbour-list mode (nl != nullptr): partners from the list instead of
+    // the cell stencil, no binning in the epilogue
+    const int *nl;               // [warps][cap][32] partner slots per lane
+    const int *nlc;              // [n*lpp] entries per lane
+    int cap;                     // entries per lane
+    const float4 *xb;            // [n] positions at the last list build
+    uint32_t *disp_next;         // [n_rep] max squared displacement (float bits) of the next positions
+};
+
+// Neighbour-list build over the cell stencil of radius sqrt(rlist2).
+struct ListArgs {
+    const float4 *pos, *vel;     // sorted state (vel.w: replica)
+    const RepParams *reps;
+    const int *cell_start;
+    const uint32_t *rb;          // [n_rep + 1] rebuild flags, rb[n_rep]: any
+    int *nl, *nlc;
+    float4 *xb;
+    uint32_t *err;
+    int n, lpp, cap;             // cap == 0: count only
 };
 
 struct MemArgs {
@@ -79,14 +98,29 @@ void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count,
                      int2 *cellrank, cudaStream_t st);
 // exclusive scan of count[0, n_tiles * SCAN_TILE) into cell_start; reads the
 // tile totals tile_read, clears tile_clear and count for the next binning
+// any (optional): skip all but the step counter when *any == 0
 void launch_scan(int *count, int *cell_start, int n_tiles, const int *tile_read, int *tile_clear,
-                 uint32_t *step_ctr, int inc, cudaStream_t st);
+                 uint32_t *step_ctr, int inc, cudaStream_t st, const uint32_t *any = nullptr);
 void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *cell_start,
-                         int2 *keys, int n, cudaStream_t st);
+                         int2 *keys, int n, cudaStream_t st, const uint32_t *any = nullptr);
 void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams *reps,
                         const int2 *keys, const int2 *cellrank, const int *cell_start, int *inv,
-                        int n, int ns, int predict, cudaStream_t st);
+                        int n, int ns, int predict, cudaStream_t st,
+                        const uint32_t *rb = nullptr, int n_rep = 0, int *tile_zero = nullptr, int n_tiles = 0);
+// list mode: rb[n_rep + 1] rebuild flags; without any rebuild every slot keeps
+// its particle, a replica that does not rebuild keeps its slots; tile_zero
+// (n_tiles ints) is cleared after a rebuild
 void launch_pair(const PairArgs &a, cudaStream_t st);
+// rb[r] = the displacement of replica r exceeds half its skin (or force);
+// rb[n_rep] = any; disp_clear zeroed for the next evaluation; advances the
+// step counter and counts each replica's rebuilds in builds
+void launch_rebuild_decide(const uint32_t *disp, uint32_t *disp_clear, uint32_t *rb, const RepParams *reps,
+                           int n_rep, int force, uint32_t *step_ctr, uint32_t *builds, cudaStream_t st);
+// cell and rank of each particle's next predicted position (list mode, when
+// any replica rebuilds)
+void launch_bin_next(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum, int2 *cellrank,
+                     const uint32_t *any, cudaStream_t st);
+void launch_list_build(const ListArgs &a, cudaStream_t st);
 // pdl: launched as a programmatic dependent of the previous kernel on st
 void launch_mem_gather(const MemArgs &a, cudaStream_t st, bool pdl);
 void launch_mem_forces(const MemArgs &a, cudaStream_t st);
