@@ -210,6 +210,8 @@ def run_native(args):
     for d in descs:
         d['cells_per_cutoff'] = args.cells_per_cutoff
         d['skin'] = args.skin
+        if args.lagged_av and d.get('membrane'):
+            d['membrane']['lagged_av'] = 1
     n = sum(W.n_mobile(d) for d in descs)
     stream = torch.cuda.Stream()
     if len(descs) == 1:
@@ -384,6 +386,7 @@ def run_native(args):
             'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
             'config': {'workload': WORKLOADS[args.workload][0], 'name': args.workload, 'particles': n,
                        'l2': 'flushed between timed steps (256 MB write)',
+                       'area_volume': 'previous step (lagged)' if args.lagged_av else 'current step',
                        'neighbour_list': {'skin': skin, 'rebuilds_per_step': rebuild_rate} if skin > 0 else 'off (cell stencil every step)',
                        'parallelism': 'replicas only' if world > 1 else 'single GPU'},
             'roofline': roof,
@@ -414,6 +417,8 @@ def main():
     ap.add_argument('--compare-steps', type=int, default=20)
     ap.add_argument('--cells-per-cutoff', type=int, default=0,
                     help='cell-list stencil width m (cells of edge >= rcut/m); 0 = library default')
+    ap.add_argument('--lagged-av', action='store_true',
+                    help='area/volume constraints from the previous step (the concurrent variant of Sec. 3.3)')
     ap.add_argument('--skin', type=float, default=None,
                     help='neighbour-list skin; 0 = cell mode (stencil every step); default: the library\'s')
     args = ap.parse_args()

@@ -83,6 +83,11 @@ typedef struct {
     float kb, theta0;           /* Eq. 16 */
     float gammaT, gammaC;       /* Eq. 12-13; needs 3*gammaC >= gammaT */
     float v_ratio;
+    int32_t lagged_av;          /* nonzero: the area and volume constraints of a
+                                 * step use the totals of the previous step's
+                                 * positions (the concurrent K-Gather / K-Apply
+                                 * of Sec. 3.3); the first evaluation after a
+                                 * commit or state load uses its own */
 } tdpd_membrane;
 
 /* FP64 observables of one replica at its current step. */

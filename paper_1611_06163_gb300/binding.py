@@ -41,7 +41,7 @@ class tdpd_config(C.Structure):
 
 class tdpd_membrane(C.Structure):
     _fields_ = [(k, C.c_float) for k in ('kT', 'p', 'x0', 'm', 'kg', 'kl', 'kv', 'kb', 'theta0',
-                                          'gammaT', 'gammaC', 'v_ratio')]
+                                          'gammaT', 'gammaC', 'v_ratio')] + [('lagged_av', C.c_int32)]
 
 
 class tdpd_obs(C.Structure):
@@ -396,7 +396,7 @@ def create_from(desc, stream_ptr=None):
         if r:
             tdpd_set_reaction(h, r['k'], r['src'], r['dst'], r['types'])
         if desc.get('membrane'):
-            m = tdpd_membrane(**{k: float(v) for k, v in desc['membrane'].items()})
+            m = tdpd_membrane(**{k: (int(v) if k == 'lagged_av' else float(v)) for k, v in desc['membrane'].items()})
             tdpd_set_membrane(h, m)
         p = desc['particles']
         if p['pos'].shape[0]:

@@ -55,6 +55,7 @@ struct RepParams {
     float m_kT, m_p, m_x0, m_m, m_kg, m_kl, m_kv, m_kb, m_cos0, m_sin0, m_gT, m_gC;
     float m_wlc0;            // kT/p
     float m_rand_T, m_rand_C;  // sqrt(2kT/dt) sqrt(2 gT), sqrt(2kT/dt) sqrt(3gC-gT)/3
+    int m_lagged;            // area/volume constraints from the previous step's totals
 };
 
 // One membrane.

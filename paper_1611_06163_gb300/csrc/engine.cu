@@ -94,7 +94,10 @@ struct tdpd_sys {
     float *d_a0j = nullptr;
     float2 *d_bond = nullptr;
     float4 *d_ref[2] = {nullptr, nullptr};
-    double2 *d_av = nullptr;
+    double2 *d_av[2] = {nullptr, nullptr};   // (A, V) per membrane, written by step parity
+    float2 *d_cgv[2] = {nullptr, nullptr};   // their constraint coefficients
+    bool all_lagged = false;                 // every membrane's K-Apply uses the previous totals
+    cudaEvent_t gathered = nullptr;          // lagged: K-Gather done on the side stream
     double *d_obs = nullptr, *d_obs_tot = nullptr;
     unsigned *d_obs_done = nullptr;
     float *d_in = nullptr;              // uploaded x, v, C of a loaded state (load order)
@@ -326,6 +329,7 @@ RepParams make_params(const HostRep &R, int cell_base, int pbase, int n)
     const double s0 = std::sqrt(2.0 * (double)m.kT / c.dt);
     P.m_rand_T = (float)(s0 * std::sqrt(2.0 * (double)m.gammaT));
     P.m_rand_C = (float)(s0 * std::sqrt(std::max(0.0, 3.0 * (double)m.gammaC - m.gammaT)) / 3.0);
+    P.m_lagged = m.lagged_av != 0;
     return P;
 }
 
@@ -367,6 +371,8 @@ tdpd_status free_device(tdpd_sys *s)
     s->n_ev = 0;
     if (s->fork) cudaEventDestroy(s->fork);
     if (s->join) cudaEventDestroy(s->join);
+    if (s->gathered) cudaEventDestroy(s->gathered);
+    s->gathered = nullptr;
     if (s->side) cudaStreamDestroy(s->side);
     s->fork = s->join = nullptr;
     s->side = nullptr;
@@ -388,14 +394,21 @@ tdpd_status free_device(tdpd_sys *s)
 const char *const KERNEL_NAMES[] = {"scan",       "scatter_keys", "rank_gather", "mem_gather", "mem_forces",
                                     "pair",       "decide",       "bin",         "list_build"};
 
+// ref_in: which reference point buffer this evaluation reads; its K-Gather
+// writes the other one and the (A, V) buffer of the same index. inc: a step
+// (advance the membrane step counter); the forces of a loaded state (inc 0)
+// use their own totals even where the constraints are lagged.
 MemArgs mem_args(tdpd_sys *s, int ref_in, int inc)
 {
+    const int q = 1 - ref_in;
     MemArgs m{};
     m.mx = s->mx; m.mv = s->mv; m.reps = s->d_reps; m.rbcs = s->d_rbcs;
     m.topos = s->d_topos; m.tri = s->d_tri; m.ring_off = s->d_ring_off; m.ring = s->d_ring;
     m.a0j = s->d_a0j; m.bond = s->d_bond; m.ref_in = s->d_ref[ref_in]; m.ref_out = s->d_ref[1 - ref_in];
-    m.av = s->d_av; m.fext = s->fext; m.n_rbc = s->n_rbc; m.max_nv = s->max_nv;
-    m.mem_ctr = s->step_ctr + 1; m.inc = inc;
+    m.av_out = s->d_av[q]; m.cgv_out = s->d_cgv[q]; m.cgv_seq = s->d_cgv[q];
+    m.cgv_lag = inc ? s->d_cgv[1 - q] : s->d_cgv[q];
+    m.fext = s->fext; m.n_rbc = s->n_rbc; m.max_nv = s->max_nv;
+    m.mem_ctr = s->step_ctr + 1; m.q = q;
     return m;
 }
 
@@ -444,16 +457,25 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
     // The membrane kernels read the predicted vertices the last pair kernel
     // wrote in load order, so they need not wait for the sort: in a plain
     // step they run on a side stream beside scan, scatter and gather, and the
-    // pair kernel joins both. The timed step keeps one stream, so that the
-    // events bracket one kernel each.
+    // pair kernel joins both. When every membrane's constraints are lagged,
+    // K-Apply goes first and the pair kernel waits for it alone; K-Gather
+    // (for the next step) overlaps the pair kernel. The timed step keeps one
+    // stream, so that the events bracket one kernel each.
     const bool branch = s->n_rbc && !ev;
     if (branch) {
         cudaEventRecord(s->fork, st);
         cudaStreamWaitEvent(s->side, s->fork, 0);
         const MemArgs m = mem_args(s, 1 - p, 1);
-        launch_mem_gather(m, s->side, false);
-        launch_mem_forces(m, s->side);
-        cudaEventRecord(s->join, s->side);
+        if (s->all_lagged) {
+            launch_mem_forces(m, s->side);
+            cudaEventRecord(s->join, s->side);
+            launch_mem_gather(m, s->side, true);
+            cudaEventRecord(s->gathered, s->side);
+        } else {
+            launch_mem_gather(m, s->side, false);
+            launch_mem_forces(m, s->side);
+            cudaEventRecord(s->join, s->side);
+        }
     }
     mark();
     const int nrep = (int)s->reps.size();
@@ -492,6 +514,7 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
     if (branch) cudaStreamWaitEvent(st, s->join, 0);
     launch_pair(pair_args(s, nxt, 1, s->tile_sum[1 - p], s->disp[1 - p]), st);
     mark();
+    if (branch && s->all_lagged) cudaStreamWaitEvent(st, s->gathered, 0);
 }
 
 constexpr size_t OBS_STAGE = (sizeof(double) * OBS_K + 15) / 16 * 16;
@@ -580,8 +603,8 @@ tdpd_status init_device(tdpd_sys *s, bool upload_in)
     if (upload_in && (rc = upload(s, s->d_in, stage_in(s), (size_t)s->N * (6 + s->ns)))) return rc;
     if (s->n_rbc && (rc = upload(s, s->d_ref[1], stage_ref(s), s->n_rbc))) return rc;
     uint32_t *ctr = stage_ctr(s);
-    ctr[0] = ctr[1] = (uint32_t)s->step;                 // sort, membrane
-    if ((rc = upload(s, s->step_ctr, ctr, 2))) return rc;
+    ctr[0] = ctr[1] = ctr[2] = (uint32_t)s->step;        // sort / pair, membrane (by parity)
+    if ((rc = upload(s, s->step_ctr, ctr, 3))) return rc;
     CU(cudaEventRecord(s->stage_done, st));
     if (s->ginit) CU(cudaGraphLaunch(s->ginit, st));
     else enqueue_init(s, st, false);
@@ -817,6 +840,9 @@ tdpd_status commit(tdpd_sys *s)
     s->lpp = 1;
     while (s->lpp < 8 && (long)N * s->lpp < 300000) s->lpp *= 2;
     s->n_rbc = (int)s->h_rbcs.size();
+    s->all_lagged = s->n_rbc > 0;
+    for (const HostRep &R : s->reps)
+        if (!R.rbcs.empty() && !R.mem.lagged_av) s->all_lagged = false;
     s->max_nv = max_nv;
     if (N == 0) return fail(s, TDPD_ESTATE, "no particles loaded");
 
@@ -836,7 +862,7 @@ tdpd_status commit(tdpd_sys *s)
         (rc = dalloc(s, &s->cell_start, (size_t)s->n_tiles * SCAN_TILE + 1)) ||
         (rc = dalloc(s, &s->tile_sum[0], s->n_tiles)) || (rc = dalloc(s, &s->tile_sum[1], s->n_tiles)) ||
         (rc = dalloc(s, &s->d_chunks, s->h_chunks.size())) ||
-        (rc = dalloc(s, &s->errw, s->reps.size())) || (rc = dalloc(s, &s->step_ctr, 2)) ||
+        (rc = dalloc(s, &s->errw, s->reps.size())) || (rc = dalloc(s, &s->step_ctr, 3)) ||
         (rc = dalloc(s, &s->d_reps, P.size())) || (rc = dalloc(s, &s->d_obs, OBS_K * s->h_chunks.size())))
         return rc;
     if ((rc = upload(s, s->d_reps, P.data(), P.size()))) return rc;
@@ -868,7 +894,9 @@ tdpd_status commit(tdpd_sys *s)
             (rc = dalloc(s, &s->d_tri, tri.size())) || (rc = dalloc(s, &s->d_ring_off, roff.size())) ||
             (rc = dalloc(s, &s->d_ring, ring.size())) || (rc = dalloc(s, &s->d_a0j, a0j.size())) ||
             (rc = dalloc(s, &s->d_bond, bond.size())) || (rc = dalloc(s, &s->d_ref[0], s->n_rbc)) ||
-            (rc = dalloc(s, &s->d_ref[1], s->n_rbc)) || (rc = dalloc(s, &s->d_av, s->n_rbc)))
+            (rc = dalloc(s, &s->d_ref[1], s->n_rbc)) || (rc = dalloc(s, &s->d_av[0], s->n_rbc)) ||
+            (rc = dalloc(s, &s->d_av[1], s->n_rbc)) || (rc = dalloc(s, &s->d_cgv[0], s->n_rbc)) ||
+            (rc = dalloc(s, &s->d_cgv[1], s->n_rbc)))
             return rc;
         if ((rc = upload(s, s->d_rbcs, s->h_rbcs.data(), s->n_rbc)) || (rc = upload(s, s->d_topos, td.data(), td.size())) ||
             (rc = upload(s, s->d_tri, tri.data(), tri.size())) || (rc = upload(s, s->d_ring_off, roff.data(), roff.size())) ||
@@ -927,6 +955,7 @@ tdpd_status commit(tdpd_sys *s)
     CU(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&s->gathered, cudaEventDisableTiming));
     {
         cudaGraph_t g;
         CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
@@ -1399,7 +1428,9 @@ tdpd_status tdpd_read_rbc(tdpd_sys *s, int r, double *area, double *volume)
     const int nb = (int)R->rbcs.size();
     if (nb == 0) return TDPD_OK;
     std::vector<double2> av(nb);
-    CU(cudaMemcpyAsync(av.data(), s->d_av + s->rep_rbc0[r], sizeof(double2) * nb, cudaMemcpyDeviceToHost, exec_stream(s)));
+    // the last K-Gather wrote the buffer of the last step's parity
+    CU(cudaMemcpyAsync(av.data(), s->d_av[1 - s->parity] + s->rep_rbc0[r], sizeof(double2) * nb,
+                       cudaMemcpyDeviceToHost, exec_stream(s)));
     CU(cudaStreamSynchronize(exec_stream(s)));
     for (int b = 0; b < nb; ++b) {
         if (area) area[b] = av[b].x;

@@ -2,7 +2,9 @@
 //
 // k_mem_gather (K-Gather of Sec. 3.3): one CTA per membrane sums the
 //   triangle areas and signed tetrahedron volumes in FP64 with compensation,
-//   and the vertex centroid that becomes the next step's reference point.
+//   the constraint coefficients they give, and the vertex centroid that
+//   becomes the next step's reference point. A lagged membrane's K-Apply
+//   uses the previous step's coefficients, so it need not wait for this.
 // k_mem_forces (K-Apply, bonds and bending): eight lanes per vertex; lane l
 //   takes the l-th entry of the vertex's one-ring fan and adds
 //     - the bond (v, nb[l]): WLC + POW, viscous and random parts,
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(1024) k_mem_gather(MemArgs A)
 {
     pdl_enter();
     const int b = blockIdx.x;
-    if (A.inc && b == 0 && threadIdx.x == 0) *A.mem_ctr += 1u;   // read by k_mem_forces only
+    if (b == 0 && threadIdx.x == 0) A.mem_ctr[1 - A.q] = A.mem_ctr[A.q] + 1u;   // the next evaluation's
     const RbcDev R = A.rbcs[b];
     const TopoDev T = A.topos[R.topo];
     const RepParams &P = A.reps[R.rep];
@@ -87,7 +89,10 @@ __global__ void __launch_bounds__(1024) k_mem_gather(MemArgs A)
 #pragma unroll
         for (int k = 0; k < 5; ++k) v[k] = ff_add(v[k], ff_shfl_down(v[k], o));
     if (lane == 0) {
-        A.av[b] = make_double2(ff_value(v[0]), ff_value(v[1]));
+        const double Ab = ff_value(v[0]), Vb = ff_value(v[1]);
+        A.av_out[b] = make_double2(Ab, Vb);
+        // constraint coefficients of Eq. 14-15, once per membrane in binary64
+        A.cgv_out[b] = make_float2((float)(P.m_kg * (Ab - R.A0) / R.A0), (float)(P.m_kv * (Vb - R.V0) / R.V0));
         const double inv = 1.0 / T.nv;
         float c3[3] = {(float)(ref.x + ff_value(v[2]) * inv), (float)(ref.y + ff_value(v[3]) * inv),
                        (float)(ref.z + ff_value(v[4]) * inv)};
@@ -132,6 +137,7 @@ __device__ __forceinline__ Dihedral dihedral(float3 xa, float3 xb, float3 xc, fl
 __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
 {
     pdl_enter();
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) A.mem_ctr[1 - A.q] = A.mem_ctr[A.q] + 1u;
     const int b = blockIdx.y;
     const RbcDev R = A.rbcs[b];
     const TopoDev T = A.topos[R.topo];
@@ -142,15 +148,14 @@ __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
     float3 f = make_float3(0.f, 0.f, 0.f);
     if (live) {
         const float4 ref = A.ref_in[b];
-        const double2 av = A.av[b];
-        const float cg = (float)(P.m_kg * (av.x - R.A0) / R.A0);
-        const float cv = (float)(P.m_kv * (av.y - R.V0) / R.V0);
+        const float2 cgv = P.m_lagged ? A.cgv_lag[b] : A.cgv_seq[b];
+        const float cg = cgv.x, cv = cgv.y;
         const int off = A.ring_off[T.ring_off + v];
         const int deg = A.ring_off[T.ring_off + v + 1] - off;
         const float3 xv = rel_pos(P, A.mx[R.gbase + v], ref);
         const float4 vv = A.mv[R.gbase + v];
         const uint32_t idv = (uint32_t)(R.gbase + v - P.pbase);
-        const uint32_t step = *A.mem_ctr + P.step0;
+        const uint32_t step = A.mem_ctr[A.q] + P.step0;
         for (int l = lane8; l < deg; l += 8) {
             const RingEntry E = A.ring[off + l];
             const RingEntry En = A.ring[off + (l + 1 == deg ? 0 : l + 1)];

@@ -83,10 +83,13 @@ struct MemArgs {
     const float2 *bond;          // (l_m, k_p) per bond
     const float4 *ref_in;        // per-membrane reference point
     float4 *ref_out;             // next reference point (centroid)
-    double2 *av;                 // per-membrane (A, V)
+    double2 *av_out;             // per-membrane (A, V) of these positions
+    float2 *cgv_out;             // their constraint coefficients k_g (A - A0)/A0, k_v (V - V0)/V0
+    const float2 *cgv_seq;       // coefficients K-Apply uses (this step's) ...
+    const float2 *cgv_lag;       // ... or the previous step's, for a lagged replica
     float4 *fext;                // membrane force by load index
-    uint32_t *mem_ctr;           // step counter of the membrane kernels
-    int inc;                     // k_mem_gather advances mem_ctr first
+    uint32_t *mem_ctr;           // [2] step counters of the membrane kernels: this
+    int q;                       // evaluation reads mem_ctr[q], sets mem_ctr[1-q] to it + 1
     int n_rbc, max_nv;
 };
 

@@ -44,11 +44,12 @@ def membrane_defaults(kT: float = 1.0) -> dict:
     random bond force real), reduced volume V0/A0^1.5 of the Evans-Fung cell.
     The local area stiffness k_l = 500 keeps the triangles of the small
     (diameter 5) cells from degenerating: with k_l = 100 a few replicas in a
-    thousand blew up within t = 10 at dt = 0.005, none with 500.
+    thousand blew up within t = 10 at dt = 0.005, none with 500. Area and
+    volume constraints are evaluated at the current positions (lagged_av = 0).
     """
     return dict(kT=kT, p=0.05, x0=1.0 / 2.2, m=2.0, kg=5000.0, kl=500.0,
                 kv=5000.0, kb=20.0 * kT, theta0=0.0, gammaT=6.0, gammaC=3.0,
-                v_ratio=RBC_V_RATIO)
+                v_ratio=RBC_V_RATIO, lagged_av=0)
 
 
 def _base(name, L, periodic, n_types, n_species, seed, rho, dt=0.01, kT=1.0,
