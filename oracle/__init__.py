@@ -57,6 +57,7 @@ class _Sys(C.Structure):
         ('k_react', C.c_double), ('r_src', C.c_int), ('r_dst', C.c_int),
         ('react_types', C.c_uint32),
         ('type', C.c_void_p), ('body', C.c_void_p), ('id', C.c_void_p),
+        ('qr_ms', C.c_double), ('qr_rho', C.c_double),
     ]
 
 
@@ -163,6 +164,9 @@ class Oracle:
         if r:
             s.k_react, s.r_src, s.r_dst, s.react_types = float(_f64(r['k'])), r['src'], r['dst'], r['types']
         s.type, s.body, s.id = _p(self.type), _p(self.body), _p(self.id)
+        q = desc.get('random_flux')
+        if q:
+            s.qr_ms, s.qr_rho = float(_f64(q['m_s'])), float(_f64(q['rho']))
         self.sys = s
         self.mem = None
         self.nrbc = len(desc['rbcs'])

@@ -113,6 +113,24 @@ static void pair_term(const orc_sys *s, const double *pos, const double *vel,
             double kap = s->kappa[(ti * T + tj) * s->ns + k];
             q[k] += -kap * wdc * (conc[i * s->ns + k] - conc[j * s->ns + k]);
         }
+        if (s->qr_ms > 0.0) {
+            /* Eq. 7 with the strength of Eq. 8: eps^2 = m_s^2 kappa rho (C_i + C_j)
+             * and w_RC = w_DC^(1/2). zeta_ij is one standard normal per species
+             * (stream 6 + k/2, the (cos, sin) pair of one draw serving species k,
+             * k+1), signed by the order of the ids so that zeta_ji = -zeta_ij and
+             * the pair exchanges, rather than creates, solute. */
+            double wrc = sqrt(wdc);
+            double sgn = s->id[i] < s->id[j] ? 1.0 : -1.0;
+            double g[2] = {0.0, 0.0};
+            for (int k = 0; k < s->ns; ++k) {
+                if ((k & 1) == 0) orc_normal_pair(s->seed, s->id[i], s->id[j], step, 6u + (uint32_t)(k / 2), g);
+                double kap = s->kappa[(ti * T + tj) * s->ns + k];
+                double csum = conc[i * s->ns + k] + conc[j * s->ns + k];
+                double e2 = s->qr_ms * s->qr_ms * kap * s->qr_rho * csum;
+                double eps = e2 > 0.0 ? sqrt(e2) : 0.0;
+                q[k] += eps * wrc * sgn * g[k & 1] / sqrt(s->dt);
+            }
+        }
     }
     int excluded = s->exclude_same_body && s->body[i] >= 0 && s->body[i] == s->body[j];
     if (r < s->rc && !excluded) {

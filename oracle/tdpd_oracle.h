@@ -38,6 +38,9 @@ typedef struct {
     double k_react; int r_src, r_dst; uint32_t react_types;  /* A->B, rate k */
     const int *type, *body;       /* [n]; body -1 for free particles */
     const uint32_t *id;           /* [n] persistent ids keying the RNG */
+    double qr_ms, qr_rho;         /* random flux (Eq. 7-8): solute mass m_s and
+                                   * density rho in eps^2 = m_s^2 kappa rho (C_i + C_j);
+                                   * m_s = 0: no random flux */
 } orc_sys;
 
 typedef struct orc_mem orc_mem;
@@ -52,7 +55,8 @@ void orc_normal_pair(uint64_t seed, uint32_t i, uint32_t j, uint32_t step,
 void orc_uniform_pair(uint64_t seed, uint32_t i, uint32_t j, uint32_t step,
                       uint32_t stream, uint32_t bits[2], double u[2]);
 
-/* Pairwise tDPD force (Eq. 3) and Fickian flux (Eq. 6) at state (pos, vel, conc)
+/* Pairwise tDPD force (Eq. 3) and Fickian flux (Eq. 6), plus the random flux
+ * of Eq. 7 when qr_ms > 0, at state (pos, vel, conc)
  * and step number `step`. mode 0: all pairs O(n^2); mode 1: cell list with
  * OpenMP. Overwrites F [n*3] and Q [n*ns]. Adds body force to non-frozen
  * particles and the first-order reaction source to Q. */

@@ -477,3 +477,46 @@ def test_lagged_area_volume_uses_previous_totals():
     expect = -(mp['kg'] * (AV0[0, 0] - AV1[0, 0]) / A0[0]) * gA - (mp['kv'] * (AV0[0, 1] - AV1[0, 1]) / V0[0]) * gV
     assert np.linalg.norm(F_lag - F_seq) > 1e-3 * np.linalg.norm(F_seq)
     assert relerr(F_lag - F_seq, expect) < 1e-5
+
+
+def test_random_flux_exchanges_solute_and_scales_with_its_strength():
+    """Eq. 7: each pair's random flux leaves i and enters j (zeta_ji =
+    -zeta_ij), so every species total stays conserved to rounding with the
+    random flux on; the random part is linear in m_s and vanishes at m_s = 0."""
+    d = _cloud(300, (6.0, 6.0, 6.0), 21, ns=3)
+    base = oracle.Oracle(d, mode=1)
+    parts = []
+    for ms in (0.05, 0.1):
+        d['random_flux'] = dict(m_s=ms, rho=3.0)
+        o = oracle.Oracle(d, mode=1)
+        assert np.abs(o.Q.sum(axis=0)).max() < 1e-12 * np.abs(o.Q).sum()
+        parts.append(o.Q - base.Q)
+    assert np.linalg.norm(parts[0]) > 1e-3 * np.linalg.norm(base.Q)
+    assert relerr(parts[1], 2.0 * parts[0]) < 1e-6
+    d['random_flux'] = dict(m_s=0.0, rho=3.0)
+    assert np.array_equal(oracle.Oracle(d, mode=1).Q, base.Q)
+
+
+def test_random_flux_equilibrium_variance_matches_fdt():
+    """Eq. 8 fluctuation-dissipation balance: with the Fickian and random
+    fluxes on fixed particles around a uniform concentration C0, the
+    linearised dynamics dC = -L C dt + B dW has B B^T = 2 m_s^2 rho C0 L
+    (w_RC^2 = w_DC), so the stationary covariance is m_s^2 rho C0 times the
+    projector off the uniform mode: the spread of C over the particles has
+    mean square m_s^2 rho C0 (N - 1)/N, whatever the positions and kappa."""
+    n, L = 400, 5.1
+    rng = np.random.default_rng(5)
+    pos = rng.random((n, 3)) * L
+    ms, rho, c0 = 0.1, 3.0, 1.0
+    d = custom(pos, None, np.full((n, 1), c0), L=(L, L, L), a=0.0, gamma=0.0, sigma=0.0, kappa=0.5,
+               dt=0.01, seed=11)
+    d['random_flux'] = dict(m_s=ms, rho=rho)
+    o = oracle.Oracle(d, mode=1)
+    o.run(1000)                                  # slowest mode relaxes in ~170 steps
+    samples = []
+    for _ in range(100):
+        o.run(20)
+        samples.append(np.var(o.conc[:, 0]))
+    assert np.abs(o.pos - pos.astype(np.float32)).max() == 0.0     # nothing moved
+    expect = ms * ms * rho * c0 * (n - 1) / n
+    assert np.mean(samples) == pytest.approx(expect, rel=0.02)
