@@ -38,17 +38,25 @@ import workloads as W  # noqa: E402
 
 METRIC = 'tDPD particle-steps/s on 1 GB300 (% HBM roofline); batched vs plain at tol'
 UNIT = 'particle-steps/s'
+def _ns10(d):
+    d['kappa'][...] = np.linspace(0.5, 2.0, int(d['n_species']), dtype=np.float32)
+    return d
+
+
 WORKLOADS = {
     'single_rbc': ('single RBC (500-vertex biconcave, WLC-POW, kb=20kT, area/volume constraints, '
                    'membrane viscosity) in tDPD solvent, 20^3 periodic box, rho=3, 24,500 particles, '
-                   '1 species, permeability 0.1, dt=0.01', lambda seed: [W.single_rbc(seed=1002 + seed)]),
+                   '1 species, permeability 0.1, dt=0.005', lambda seed: [W.single_rbc(seed=1002 + seed)]),
     'fluid_4k': ('plain tDPD fluid, 10^3 periodic box, rho=4, 4000 particles, 1 species',
                  lambda seed: [W.fluid_box(seed=1001 + seed)]),
     'fluid_786k': ('plain tDPD fluid, 64^3 periodic box, rho=3, 786,432 particles, 1 species '
                    '(state larger than L2; profiling case)',
                    lambda seed: [W.fluid_box(L=64.0, rho=3.0, seed=2001 + seed)]),
+    'fluid_786k_ns10': ('plain tDPD fluid, 64^3 periodic box, rho=3, 786,432 particles, 10 species '
+                        '(kappa 0.5..2), the multi-species case of the paper\'s fluid benchmark',
+                        lambda seed: [_ns10(W.fluid_box(L=64.0, rho=3.0, n_species=10, seed=2002 + seed))]),
     'channel': ('RBC suspension: 64x32x32 channel with frozen-particle walls, 40 RBCs, 2 species, '
-                'reaction k=0.01, body force 0.05',
+                'reaction k=0.01, body force 0.05, dt=0.005',
                 lambda seed: [W.rbc_channel(seed=1003 + seed)]),
     'ensemble': ('512 independent replicas (cubic boxes 8..16 at rho=3, 0..4 RBCs, log-uniform '
                  'permeability, body force) batched in one graph-captured step',
@@ -212,6 +220,8 @@ def run_native(args):
         d['skin'] = args.skin
         if args.lagged_av and d.get('membrane'):
             d['membrane']['lagged_av'] = 1
+        if args.random_flux > 0:
+            d['random_flux'] = dict(m_s=args.random_flux, rho=3.0)
     n = sum(W.n_mobile(d) for d in descs)
     stream = torch.cuda.Stream()
     if len(descs) == 1:
@@ -293,6 +303,10 @@ def run_native(args):
     n_flux = rho * 4.0 / 3.0 * math.pi * float(d0['rcc']) ** 3
     n_force = rho * 4.0 / 3.0 * math.pi * float(d0['rc']) ** 3
     ops_pp = n_flux * (20 + 4 * (ns - 1)) + n_force * 110
+    if args.random_flux > 0:
+        # one TEA-8 draw + Box-Muller per two species, and ~8 operations per
+        # species, for every pair inside the flux cut-off
+        ops_pp += n_flux * (110 * ((ns + 1) // 2) + 8 * ns)
     skin = 0.3 if args.skin is None else args.skin
     rcut = max(float(d0['rc']), float(d0['rcc']))
     n_list = rho * 4.0 / 3.0 * math.pi * (rcut + skin) ** 3 if skin > 0 else 0.0
@@ -387,6 +401,7 @@ def run_native(args):
             'config': {'workload': WORKLOADS[args.workload][0], 'name': args.workload, 'particles': n,
                        'l2': 'flushed between timed steps (256 MB write)',
                        'area_volume': 'previous step (lagged)' if args.lagged_av else 'current step',
+                       'random_flux': {'m_s': args.random_flux, 'rho': 3.0} if args.random_flux > 0 else 'off',
                        'neighbour_list': {'skin': skin, 'rebuilds_per_step': rebuild_rate} if skin > 0 else 'off (cell stencil every step)',
                        'parallelism': 'replicas only' if world > 1 else 'single GPU'},
             'roofline': roof,
@@ -417,6 +432,8 @@ def main():
     ap.add_argument('--compare-steps', type=int, default=20)
     ap.add_argument('--cells-per-cutoff', type=int, default=0,
                     help='cell-list stencil width m (cells of edge >= rcut/m); 0 = library default')
+    ap.add_argument('--random-flux', type=float, default=0.0, metavar='M_S',
+                    help='random flux of Eq. 7 with solute mass M_S (0: off, as in the paper)')
     ap.add_argument('--lagged-av', action='store_true',
                     help='area/volume constraints from the previous step (the concurrent variant of Sec. 3.3)')
     ap.add_argument('--skin', type=float, default=None,

@@ -39,7 +39,7 @@ extern "C" {
 #endif
 
 #define TDPD_MAX_TYPES 4
-#define TDPD_MAX_SPECIES 8
+#define TDPD_MAX_SPECIES 16
 #define TDPD_MAX_IDS (1 << 24)      /* particles per replica */
 
 typedef enum {
@@ -118,6 +118,18 @@ tdpd_status tdpd_set_kappa(tdpd_sys *s, int type_i, int type_j, int species, flo
 /* Source term Q^S of Eq. 5: dC_dst/dt += k C_src, dC_src/dt -= k C_src on
  * particles whose type bit is set in types. */
 tdpd_status tdpd_set_reaction(tdpd_sys *s, float k, int src, int dst, uint32_t types);
+
+/* Random flux Q^R of Eq. 7 for every species: eps w_RC zeta / sqrt(dt) per
+ * pair inside r_cc, with eps^2 = m_s^2 kappa rho (C~_i + C~_j) (Eq. 8;
+ * negative sums count as zero) and w_RC = w_DC^(1/2). zeta is one standard
+ * normal per pair, step and species (stream 6 + s/2 of the pair generator,
+ * the cosine branch for even s, the sine branch for odd s), taken with sign
+ * + on the side of the smaller id, so each pair exchanges solute. m_s = 0
+ * (the default) leaves it out, as the paper does (m_s << m). rho is the
+ * particle number density of the model, m_s the solute mass. Before commit;
+ * TDPD_EINVAL for negative or non-finite values. Handles that use it run the
+ * general (any species count) pair kernel. */
+tdpd_status tdpd_set_random_flux(tdpd_sys *s, float m_s, float rho);
 
 /* Membrane constants for every membrane of the replica (Sec. 2.2). */
 tdpd_status tdpd_set_membrane(tdpd_sys *s, const tdpd_membrane *m);

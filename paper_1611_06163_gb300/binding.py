@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, 'libtdpd.so')
 
 MAX_TYPES = 4
-MAX_SPECIES = 8
+MAX_SPECIES = 16
 STATUS = {0: 'OK', 1: 'EINVAL', 2: 'ENOMEM', 3: 'ECUDA', 4: 'EOVERFLOW', 5: 'ENONFINITE',
           6: 'ETIMEOUT', 7: 'ESTATE'}
 
@@ -70,6 +70,7 @@ def _load():
         'tdpd_set_stream': ([P, P], I),
         'tdpd_set_lanes': ([P, I], I),
         'tdpd_set_skin': ([P, C.c_float], I),
+        'tdpd_set_random_flux': ([P, C.c_float, C.c_float], I),
         'tdpd_list_rebuilds': ([P, I, C.POINTER(C.c_int64)], I),
         'tdpd_commit': ([P], I),
         'tdpd_step': ([P, I], I),
@@ -194,6 +195,10 @@ def tdpd_list_rebuilds(h, replica=0):
     v = C.c_int64(0)
     _chk(h, lib.tdpd_list_rebuilds(h, int(replica), C.byref(v)))
     return v.value
+
+
+def tdpd_set_random_flux(h, m_s, rho):
+    _chk(h, lib.tdpd_set_random_flux(h, float(m_s), float(rho)))
 
 
 def tdpd_commit(h):
@@ -403,6 +408,9 @@ def create_from(desc, stream_ptr=None):
             tdpd_add_particles(h, p['pos'], p['vel'], p['conc'], p['type'])
         for rb in desc['rbcs']:
             tdpd_add_rbc(h, rb['pos'], rb['vel'], rb['conc'], rb['type'], rb['tri'], rb['rest'])
+        q = desc.get('random_flux')
+        if q:
+            tdpd_set_random_flux(h, q['m_s'], q['rho'])
         if desc.get('skin') is not None:
             tdpd_set_skin(h, desc['skin'])
         if desc.get('lanes') is not None:

@@ -56,6 +56,7 @@ struct RepParams {
     float m_wlc0;            // kT/p
     float m_rand_T, m_rand_C;  // sqrt(2kT/dt) sqrt(2 gT), sqrt(2kT/dt) sqrt(3gC-gT)/3
     int m_lagged;            // area/volume constraints from the previous step's totals
+    float qr_coef;           // random flux: m_s sqrt(rho) (Eq. 7-8); 0: off
 };
 
 // One membrane.

@@ -43,6 +43,7 @@ struct HostRep {
     int nc[3] = {0, 0, 0};
     int m = 2;
     float skin = 0.0f;     // neighbour-list skin of this replica (0: cell mode)
+    float qr_ms = 0.0f, qr_rho = 0.0f;   // random flux (Eq. 7-8); m_s = 0: off
 };
 
 struct Topo {
@@ -330,6 +331,7 @@ RepParams make_params(const HostRep &R, int cell_base, int pbase, int n)
     P.m_rand_T = (float)(s0 * std::sqrt(2.0 * (double)m.gammaT));
     P.m_rand_C = (float)(s0 * std::sqrt(std::max(0.0, 3.0 * (double)m.gammaC - m.gammaT)) / 3.0);
     P.m_lagged = m.lagged_av != 0;
+    P.qr_coef = R.qr_ms > 0.0f ? (float)((double)R.qr_ms * std::sqrt((double)R.qr_rho)) : 0.0f;
     return P;
 }
 
@@ -421,6 +423,8 @@ PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum, 
     a.cellrank = s->cellrank; a.err = s->errw; a.step_ctr = s->step_ctr; a.n = s->N; a.ns = s->ns;
     a.integrate = integrate;
     a.lpp = s->lpp;
+    for (const HostRep &R : s->reps)
+        if (R.qr_ms > 0.0f) a.qr = 1;
     if (s->use_list) {
         a.nl = s->nl; a.nlc = s->nlc; a.cap = s->nl_cap; a.xb = s->xb; a.disp_next = disp_next;
     }
@@ -1106,6 +1110,17 @@ tdpd_status tdpd_set_reaction(tdpd_sys *s, float k, int src, int dst, uint32_t t
     R.r_src = src;
     R.r_dst = dst;
     R.r_types = types;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_random_flux(tdpd_sys *s, float m_s, float rho)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed || s->reps.size() != 1) return fail(s, TDPD_ESTATE, "parameters are fixed after commit or batching");
+    if (!(m_s >= 0.0f && rho >= 0.0f && std::isfinite(m_s) && std::isfinite(rho)))
+        return fail(s, TDPD_EINVAL, "random flux: m_s and rho must be finite and >= 0");
+    s->reps[0].qr_ms = m_s;
+    s->reps[0].qr_rho = rho;
     return TDPD_OK;
 }
 

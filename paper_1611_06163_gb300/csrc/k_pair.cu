@@ -190,6 +190,21 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
             q[0] -= kap[0] * wdc * (ci[0] - cj0);
             for (int s = 1; s < ns; ++s)
                 q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
+            if (NS == 0 && P.qr_coef > 0.0f) {
+                // random flux (Eq. 7): eps w_RC zeta / sqrt(dt), eps^2 =
+                // m_s^2 kappa rho (C_i + C_j), w_RC = w_DC^(1/2) (Eq. 8); one
+                // pair normal per species (the (cos, sin) pair of stream
+                // 6 + s/2), signed by the id order so that zeta_ji = -zeta_ij
+                const uint32_t idi = wi & ID_MASK, idj = wj & ID_MASK;
+                const float amp = (idi < idj ? 1.0f : -1.0f) * P.qr_coef * sqrtf(wdc) * P.inv_sqrt_dt;
+                float2 z = make_float2(0.f, 0.f);
+                for (int s = 0; s < ns; ++s) {
+                    if ((s & 1) == 0)
+                        z = normal2(pair_bits(idi, idj, P.seed_lo, P.seed_hi, step_ctr + P.step0, 6u + (uint32_t)(s >> 1)));
+                    const float cs = ci[s] + (s == 0 ? cj0 : Ct[(size_t)j * ns + s]);
+                    q[s] += amp * sqrtf(fmaxf(kap[s] * cs, 0.0f)) * ((s & 1) ? z.y : z.x);
+                }
+            }
         }
         const bool push = near && r2 < rc2;
         const unsigned bal = __ballot_sync(0xffffffffu, push);
@@ -399,7 +414,11 @@ static void launch_ns(const PairArgs &a, cudaStream_t st)
 void launch_pair(const PairArgs &a, cudaStream_t st)
 {
     if (a.n <= 0) return;
-    if (a.nl) {
+    if (a.qr) {
+        // the random flux lives in the general kernel only
+        if (a.nl) launch_ns<0, true>(a, st);
+        else launch_ns<0, false>(a, st);
+    } else if (a.nl) {
         switch (a.ns) {
         case 1: launch_ns<1, true>(a, st); break;
         case 2: launch_ns<2, true>(a, st); break;

@@ -369,3 +369,23 @@ def test_lagged_area_volume_matches_oracle():
     d['membrane']['lagged_av'] = 0
     _, _, _, (As, Vs) = run_vs_oracle(d, 10)
     assert abs(A[0] - As[0]) / As[0] < 5e-3 and abs(V[0] - Vs[0]) / Vs[0] < 5e-3
+
+
+def test_ten_species_and_random_flux_match_oracle():
+    """N_s = 10 with distinct kappa per species (the general kernel), then
+    with the random flux of Eq. 7 on: F(0), Q(0) and 10 steps against the
+    oracle; species totals conserved by the random flux on the device."""
+    d = W.fluid_box(L=8.0, rho=3.0, n_species=10, seed=61)
+    d['kappa'][...] = np.linspace(0.5, 2.0, 10, dtype=np.float32)
+    F, Q, Fo, Qo = forces_vs_oracle(d)
+    assert normwise(F, Fo) < TOL_FORCE and normwise(Q, Qo) < TOL_FORCE
+    d['random_flux'] = dict(m_s=0.05, rho=3.0)
+    F, Q, Fo, Qo = forces_vs_oracle(d)
+    assert normwise(F, Fo) < TOL_FORCE and normwise(Q, Qo) < TOL_FORCE
+    Q64 = Q.astype(np.float64)
+    assert np.abs(Q64.sum(axis=0)).max() < 1e-5 * np.abs(Q64).sum(axis=0).max()
+    err, obs, o, _ = run_vs_oracle(d, 10)
+    for k, v in err.items():
+        assert v < TOL_TRAJ, (k, v, err)
+    ob = o.observables()
+    assert np.allclose(obs['mass'], ob['mass'], rtol=1e-6)
