@@ -131,6 +131,13 @@ tdpd_status tdpd_set_reaction(tdpd_sys *s, float k, int src, int dst, uint32_t t
  * general (any species count) pair kernel. */
 tdpd_status tdpd_set_random_flux(tdpd_sys *s, float m_s, float rho);
 
+/* Body force profile: 0 (default) the configuration's body force everywhere;
+ * 1 the double Poiseuille forcing of the flow validation (Sec. 4.1): the body
+ * force where z < L_z/2 and its negative where z >= L_z/2, judged at the
+ * position where the force is evaluated. Before commit; TDPD_EINVAL for
+ * another mode. */
+tdpd_status tdpd_set_body_force_profile(tdpd_sys *s, int mode);
+
 /* Membrane constants for every membrane of the replica (Sec. 2.2). */
 tdpd_status tdpd_set_membrane(tdpd_sys *s, const tdpd_membrane *m);
 

@@ -57,7 +57,7 @@ class _Sys(C.Structure):
         ('k_react', C.c_double), ('r_src', C.c_int), ('r_dst', C.c_int),
         ('react_types', C.c_uint32),
         ('type', C.c_void_p), ('body', C.c_void_p), ('id', C.c_void_p),
-        ('qr_ms', C.c_double), ('qr_rho', C.c_double),
+        ('qr_ms', C.c_double), ('qr_rho', C.c_double), ('fbody_flip', C.c_int),
     ]
 
 
@@ -160,6 +160,7 @@ class Oracle:
         s.dt, s.lam = float(_f64(desc['dt'])), float(_f64(desc['lam']))
         s.fbody[:] = _f64(desc['body_force']).tolist()
         s.frozen_types = int(desc['frozen_types'])
+        s.fbody_flip = int(desc.get('body_force_flip', 0))
         r = desc.get('reaction')
         if r:
             s.k_react, s.r_src, s.r_dst, s.react_types = float(_f64(r['k'])), r['src'], r['dst'], r['types']

@@ -149,11 +149,12 @@ static void pair_term(const orc_sys *s, const double *pos, const double *vel,
     }
 }
 
-static void add_sources(const orc_sys *s, const double *conc, double *F, double *Q)
+static void add_sources(const orc_sys *s, const double *pos, const double *conc, double *F, double *Q)
 {
     for (int i = 0; i < s->n; ++i) {
+        const double sg = (s->fbody_flip && pos[3 * i + 2] >= 0.5 * s->L[2]) ? -1.0 : 1.0;
         if (!is_frozen(s, i))
-            for (int c = 0; c < 3; ++c) F[3 * i + c] += s->fbody[c];
+            for (int c = 0; c < 3; ++c) F[3 * i + c] += sg * s->fbody[c];
         if (s->k_react != 0.0 && ((s->react_types >> s->type[i]) & 1u)) {
             double rate = s->k_react * conc[i * s->ns + s->r_src];
             Q[i * s->ns + s->r_src] -= rate;
@@ -247,7 +248,7 @@ int orc_pair_forces(const orc_sys *s, const double *pos, const double *vel,
         free(head);
         free(next);
     }
-    add_sources(s, conc, F, Q);
+    add_sources(s, pos, conc, F, Q);
     return 0;
 }
 

@@ -41,6 +41,8 @@ typedef struct {
     double qr_ms, qr_rho;         /* random flux (Eq. 7-8): solute mass m_s and
                                    * density rho in eps^2 = m_s^2 kappa rho (C_i + C_j);
                                    * m_s = 0: no random flux */
+    int fbody_flip;               /* 1: the body force is -fbody where z >= L_z/2
+                                   * (the double Poiseuille flow of Sec. 4.1) */
 } orc_sys;
 
 typedef struct orc_mem orc_mem;

@@ -71,6 +71,7 @@ def _load():
         'tdpd_set_lanes': ([P, I], I),
         'tdpd_set_skin': ([P, C.c_float], I),
         'tdpd_set_random_flux': ([P, C.c_float, C.c_float], I),
+        'tdpd_set_body_force_profile': ([P, I], I),
         'tdpd_list_rebuilds': ([P, I, C.POINTER(C.c_int64)], I),
         'tdpd_commit': ([P], I),
         'tdpd_step': ([P, I], I),
@@ -199,6 +200,10 @@ def tdpd_list_rebuilds(h, replica=0):
 
 def tdpd_set_random_flux(h, m_s, rho):
     _chk(h, lib.tdpd_set_random_flux(h, float(m_s), float(rho)))
+
+
+def tdpd_set_body_force_profile(h, mode):
+    _chk(h, lib.tdpd_set_body_force_profile(h, int(mode)))
 
 
 def tdpd_commit(h):
@@ -408,6 +413,8 @@ def create_from(desc, stream_ptr=None):
             tdpd_add_particles(h, p['pos'], p['vel'], p['conc'], p['type'])
         for rb in desc['rbcs']:
             tdpd_add_rbc(h, rb['pos'], rb['vel'], rb['conc'], rb['type'], rb['tri'], rb['rest'])
+        if desc.get('body_force_flip'):
+            tdpd_set_body_force_profile(h, 1)
         q = desc.get('random_flux')
         if q:
             tdpd_set_random_flux(h, q['m_s'], q['rho'])

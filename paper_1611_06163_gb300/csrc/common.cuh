@@ -57,6 +57,7 @@ struct RepParams {
     float m_rand_T, m_rand_C;  // sqrt(2kT/dt) sqrt(2 gT), sqrt(2kT/dt) sqrt(3gC-gT)/3
     int m_lagged;            // area/volume constraints from the previous step's totals
     float qr_coef;           // random flux: m_s sqrt(rho) (Eq. 7-8); 0: off
+    int fbody_flip;          // body force negated where z >= L_z/2 (double Poiseuille)
 };
 
 // One membrane.

@@ -44,6 +44,7 @@ struct HostRep {
     int m = 2;
     float skin = 0.0f;     // neighbour-list skin of this replica (0: cell mode)
     float qr_ms = 0.0f, qr_rho = 0.0f;   // random flux (Eq. 7-8); m_s = 0: off
+    int fbody_flip = 0;                  // double Poiseuille forcing
 };
 
 struct Topo {
@@ -332,6 +333,7 @@ RepParams make_params(const HostRep &R, int cell_base, int pbase, int n)
     P.m_rand_C = (float)(s0 * std::sqrt(std::max(0.0, 3.0 * (double)m.gammaC - m.gammaT)) / 3.0);
     P.m_lagged = m.lagged_av != 0;
     P.qr_coef = R.qr_ms > 0.0f ? (float)((double)R.qr_ms * std::sqrt((double)R.qr_rho)) : 0.0f;
+    P.fbody_flip = R.fbody_flip;
     return P;
 }
 
@@ -1121,6 +1123,15 @@ tdpd_status tdpd_set_random_flux(tdpd_sys *s, float m_s, float rho)
         return fail(s, TDPD_EINVAL, "random flux: m_s and rho must be finite and >= 0");
     s->reps[0].qr_ms = m_s;
     s->reps[0].qr_rho = rho;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_body_force_profile(tdpd_sys *s, int mode)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed || s->reps.size() != 1) return fail(s, TDPD_ESTATE, "parameters are fixed after commit or batching");
+    if (mode != 0 && mode != 1) return fail(s, TDPD_EINVAL, "body force profile must be 0 or 1");
+    s->reps[0].fbody_flip = mode;
     return TDPD_OK;
 }
 

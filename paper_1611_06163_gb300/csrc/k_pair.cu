@@ -322,7 +322,12 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
             fx += fm.x; fy += fm.y; fz += fm.z;
         }
         const bool frozen = (P.frozen_mask >> ti) & 1u;
-        if (!frozen) { fx += P.fbody[0]; fy += P.fbody[1]; fz += P.fbody[2]; }
+        if (!frozen) {
+            const float sg = (P.fbody_flip && pi.z >= 0.5f * P.L[2]) ? -1.0f : 1.0f;
+            fx += sg * P.fbody[0];
+            fy += sg * P.fbody[1];
+            fz += sg * P.fbody[2];
+        }
         if (P.k_react != 0.0f && ((P.react_mask >> ti) & 1u)) {
             const float rate = P.k_react * Ct[(size_t)i * ns + P.r_src];
             for (int s = 0; s < ns; ++s) {

@@ -1,0 +1,102 @@
+"""Flow validation of Sec. 4.1 on the device: the transient double Poiseuille
+flow against the series solution of the Stokes start-up problem.
+
+With the body force +f below z = d and -f above it (period 2d), the mean
+velocity u_x(z, t) vanishes at z = 0 and z = d by symmetry, so each half is a
+channel with no-slip walls started from rest:
+
+    u(z, t) = f z (d - z) / (2 nu)
+              - 4 f d^2 / (nu pi^3) sum_k sin(n pi z / d) exp(-n^2 pi^2 nu t / d^2) / n^3,
+    n = 2k + 1,
+
+and u(z + d, t) = -u(z, t). The kinematic viscosity nu of the model is not
+given in the paper; it is fitted to the profiles at all snapshot times
+together, and the test asks the series with that one number to describe the
+whole transient, the fits at early and at late times to agree, and nu to be
+near the mean-field estimate of the dissipative viscosity,
+nu_D = (2 pi / 15) gamma rho int_0^rc w_D(r) r^4 dr (Marsh, Backx and
+Ernst 1997; Groot and Warren 1997), about 6.4 at the paper's parameters
+(w_D = (1 - r/rc)^0.41, rc = 1.58, gamma = 4.5, rho = 4).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_common import B
+
+pytestmark = pytest.mark.gpu
+
+
+def series(z, t, f, d, nu, terms=60):
+    zz = np.mod(z, 2 * d)
+    sign = np.where(zz < d, 1.0, -1.0)
+    zz = np.where(zz < d, zz, zz - d)
+    u = f * zz * (d - zz) / (2 * nu)
+    for k in range(terms):
+        n = 2 * k + 1
+        u -= 4 * f * d * d / (nu * math.pi ** 3) * np.sin(n * math.pi * zz / d) * \
+            math.exp(-n * n * math.pi ** 2 * nu * t / (d * d)) / n ** 3
+    return sign * u
+
+
+def fit_nu(z, profiles, f, d):
+    """Least-squares nu over a log grid, refined once."""
+    def cost(nu):
+        return sum(float(np.sum((u - series(z, t, f, d, nu)) ** 2)) for t, u in profiles)
+    grid = np.exp(np.linspace(math.log(0.1), math.log(30.0), 161))
+    nu = grid[int(np.argmin([cost(x) for x in grid]))]
+    fine = np.linspace(nu / 1.05, nu * 1.05, 81)
+    return float(fine[int(np.argmin([cost(x) for x in fine]))])
+
+
+def test_double_poiseuille_transient_follows_stokes_series():
+    bd = B()
+    L, f = 20.0, 0.2
+    d = W.double_poiseuille(L=L, rho=4.0, f=f, seed=71, Lxy=40.0)     # 128,000 particles
+    h = bd.create_from(d)
+    bd.tdpd_commit(h)
+    dt = float(np.float32(d['dt']))
+    nbins = 20
+    edges = np.linspace(0.0, L, nbins + 1)
+    zc = 0.5 * (edges[1:] + edges[:-1])[:nbins // 2]
+    # the relaxation time d^2/(pi^2 nu) is ~1.5; from t = 1 on the boundary
+    # layers sqrt(nu t) are wider than two cut-offs (the paper's snapshots sit
+    # at the same fractions of its relaxation time, 5.8)
+    times = [1.0, 2.0, 4.0, 8.0, 16.0]
+    profiles = []
+    step = 0
+    for t in times:
+        # average 9 snapshots 0.02 apart centred on t
+        acc = np.zeros(nbins)
+        for k in range(-4, 5):
+            target = int(round((t + 0.02 * k) / dt))
+            bd.tdpd_step(h, target - step)
+            step = target
+            pos, vel, _ = bd.tdpd_read_state(h, 0, 1)
+            idx = np.clip(np.searchsorted(edges, pos[:, 2], side='right') - 1, 0, nbins - 1)
+            acc += np.bincount(idx, weights=vel[:, 0], minlength=nbins) / np.bincount(idx, minlength=nbins)
+        u = acc / 9.0
+        # fold the four equivalent quarter profiles (mirror about d/2, sign
+        # flip in the upper half) onto the lower half
+        h2 = nbins // 2
+        lo = np.arange(h2)
+        profiles.append((t, 0.25 * (u[lo] + u[h2 - 1 - lo] - u[h2 + lo] - u[nbins - 1 - lo])))
+    st = bd.tdpd_replica_status(h)
+    bd.tdpd_destroy(h)
+    assert (st == 0).all()
+    half = L / 2
+    nu = fit_nu(zc, profiles, f, half)
+    umax = max(np.abs(u).max() for _, u in profiles)
+    res = math.sqrt(sum(float(np.sum((u - series(zc, t, f, half, nu)) ** 2)) for t, u in profiles)
+                    / (len(zc) * len(profiles)))
+    r = np.linspace(0.0, float(d['rc']), 20001)
+    wd = (1.0 - r / float(d['rc'])) ** float(d['s_f'])
+    nu_d = 2 * math.pi / 15 * float(d['gamma'][0, 0]) * 4.0 * getattr(np, 'trapezoid', getattr(np, 'trapz', None))(wd * r ** 4, r)
+    assert 0.75 * nu_d < nu < 1.35 * nu_d, (nu, nu_d)
+    assert res < 0.04 * umax, (nu, res, umax)
+    early = fit_nu(zc, profiles[:2], f, half)
+    late = fit_nu(zc, profiles[-2:], f, half)
+    assert abs(early - late) < 0.15 * nu, (early, late, nu)

@@ -520,3 +520,25 @@ def test_random_flux_equilibrium_variance_matches_fdt():
     assert np.abs(o.pos - pos.astype(np.float32)).max() == 0.0     # nothing moved
     expect = ms * ms * rho * c0 * (n - 1) / n
     assert np.mean(samples) == pytest.approx(expect, rel=0.02)
+
+
+def test_flipped_body_force_drives_each_half_oppositely():
+    """Double Poiseuille forcing (Sec. 4.1): +f below z = L/2, -f above. Two
+    free particles, one in each half and moving only along x, follow exact
+    parabolas of opposite curvature; with the flip off both take +f."""
+    r0 = np.array([[2.0, 3.0, 2.5], [2.0, 6.0, 7.5]])
+    f = np.array([0.05, 0.0, 0.0])
+    d = custom(r0, np.zeros((2, 3)), L=(10.0, 10.0, 10.0), body_force=f)
+    d['body_force_flip'] = 1
+    o = oracle.Oracle(d, mode=0)
+    o.run(200)
+    t = 200 * float(np.float32(0.01))
+    f32 = float(np.float32(0.05))
+    assert o.vel[0, 0] == pytest.approx(f32 * t, abs=1e-12)
+    assert o.vel[1, 0] == pytest.approx(-f32 * t, abs=1e-12)
+    x = np.array([2.0 + 0.5 * f32 * t * t, 2.0 - 0.5 * f32 * t * t]) % 10.0
+    assert np.abs(o.pos[:, 0] - x).max() < 1e-12
+    d['body_force_flip'] = 0
+    o = oracle.Oracle(d, mode=0)
+    o.run(200)
+    assert np.abs(o.vel[:, 0] - f32 * t).max() < 1e-12

@@ -106,6 +106,21 @@ def fluid_box(L=10.0, rho=4.0, n_species=1, seed=1001, kT=1.0, **kw):
     return d
 
 
+def double_poiseuille(L=40.0, rho=4.0, f=0.02, seed=1005, Lxy=None):
+    """The flow validation setup of Sec. 4.1: a periodic cube of tDPD fluid
+    (40^3 at rho = 4: 256,000 particles) with a = 18.75, gamma = 4.5,
+    r_c = 1.58 and w_R exponent s = 0.41, driven along x by a body force f
+    below z = L/2 and -f above it (double Poiseuille flow). The paper does
+    not give f. Lxy (default L) sets the box edges along x and y."""
+    Lxy = L if Lxy is None else Lxy
+    d = _base('double_poiseuille', (Lxy, Lxy, L), (1, 1, 1), 1, 1, seed, rho, rc=1.58, s_f=0.41)
+    d['a'][:] = 18.75
+    d['particles'] = fluid_particles(_rng(seed), d['L'], rho, 1)
+    d['body_force'] = np.asarray([f, 0.0, 0.0], np.float32)
+    d['body_force_flip'] = 1
+    return d
+
+
 def place_rbc(mesh_verts, mesh_tri, center, L, rng, kT=1.0, n_species=1, c_value=1.0,
               rest=None):
     """One membrane: vertices translated to ``center`` and wrapped into the box."""
