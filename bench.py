@@ -307,7 +307,7 @@ def run_native(args):
         # one TEA-8 draw + Box-Muller per two species, and ~8 operations per
         # species, for every pair inside the flux cut-off
         ops_pp += n_flux * (110 * ((ns + 1) // 2) + 8 * ns)
-    skin = 0.3 if args.skin is None else args.skin
+    skin = 0.2 if args.skin is None else args.skin
     rcut = max(float(d0['rc']), float(d0['rcc']))
     n_list = rho * 4.0 / 3.0 * math.pi * (rcut + skin) ** 3 if skin > 0 else 0.0
     bytes_pp = 112 + 16 * ns if skin == 0 else 104 + 16 * ns + 16 + 4 * n_list

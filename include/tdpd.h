@@ -180,7 +180,7 @@ tdpd_status tdpd_set_lanes(tdpd_sys *s, int lanes);
  * the last build, which keeps every pair inside the cut-off in the lists
  * (Sec. 3.1 rebuilds the list every few steps). 0 selects cell mode: no
  * lists, the cell stencil is walked and the particles re-sorted every step.
- * Default (not called): 0.3. A replica whose box is too small for the skin
+ * Default (not called): 0.2. A replica whose box is too small for the skin
  * (rcut + 2 skin must not exceed half a periodic edge, and the cells of edge
  * (rcut + skin)/m must fit 2m+1 times) gets a smaller one. The skin changes
  * the order in which pair terms are summed, so results agree to rounding,

@@ -524,7 +524,7 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
 }
 
 constexpr size_t OBS_STAGE = (sizeof(double) * OBS_K + 15) / 16 * 16;
-constexpr float DEFAULT_SKIN = 0.3f;   // neighbour-list skin (length units)
+constexpr float DEFAULT_SKIN = 0.2f;   // neighbour-list skin (length units)
 
 // Pinned staging area: observables, the step counters, the membranes'
 // reference points, then x[3N], v[3N], C[N*ns] in load order.

@@ -29,7 +29,8 @@ namespace tdpd {
 namespace {
 
 constexpr int QCAP = 64;   // queue ring per warp (a push adds at most 32)
-constexpr int UNR = 2;     // candidates loaded per trip of the row loop
+constexpr int UNR = 2;       // candidates loaded per trip of a stencil row (cell mode)
+constexpr int UNR_LIST = 4;  // list entries loaded per trip (list mode)
 
 struct __align__(16) QEntry {
     int j;          // partner slot
@@ -223,21 +224,21 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
         }
     };
     if constexpr (LIST) {
-        // the lane's list, UNR entries per trip (index loads, then partner
+        // the lane's list, UNR_LIST entries per trip (index loads, then partner
         // loads, then the visits in list order); separations by minimum image
         const int *__restrict__ nl = A.nl + (size_t)(gt >> 5) * A.cap * 32 + (gt & 31);
         const int cnt = valid ? A.nlc[gt] : 0;
         const int nit = __reduce_max_sync(0xffffffffu, cnt);
         const float Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];
         const float iLx = P.inv_L[0], iLy = P.inv_L[1], iLz = P.inv_L[2];
-        for (int t = 0; t < nit; t += UNR) {
-            int jj[UNR];
-            float4 pp[UNR];
-            float cc[UNR];
+        for (int t = 0; t < nit; t += UNR_LIST) {
+            int jj[UNR_LIST];
+            float4 pp[UNR_LIST];
+            float cc[UNR_LIST];
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) jj[u] = t + u < cnt ? nl[(size_t)(t + u) * 32] : 0;
+            for (int u = 0; u < UNR_LIST; ++u) jj[u] = t + u < cnt ? nl[(size_t)(t + u) * 32] : 0;
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) {
+            for (int u = 0; u < UNR_LIST; ++u) {
                 pp[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 cc[u] = 0.f;
                 if (t + u < cnt) {
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
                 }
             }
 #pragma unroll
-            for (int u = 0; u < UNR; ++u)
+            for (int u = 0; u < UNR_LIST; ++u)
                 if (u == 0 || t + u < nit) {
                     float dx = pi.x - pp[u].x, dy = pi.y - pp[u].y, dz = pi.z - pp[u].z;
                     dx = __fmaf_rn(-Lx, rintf(dx * iLx), dx);
