@@ -218,6 +218,7 @@ def run_native(args):
     for d in descs:
         d['cells_per_cutoff'] = args.cells_per_cutoff
         d['skin'] = args.skin
+        d['lanes'] = args.lanes or None
         if args.lagged_av and d.get('membrane'):
             d['membrane']['lagged_av'] = 1
         if args.random_flux > 0:
@@ -233,6 +234,8 @@ def run_native(args):
         bd.tdpd_set_stream(h, stream.cuda_stream)
         if args.skin is not None:
             bd.tdpd_set_skin(h, args.skin)
+        if args.lanes:
+            bd.tdpd_set_lanes(h, args.lanes)
     bd.tdpd_commit(h)
     nk = bd.tdpd_launches_per_step(h)
     names = [bd.tdpd_kernel_name(h, k) for k in range(nk)]
@@ -400,6 +403,7 @@ def run_native(args):
             'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
             'config': {'workload': WORKLOADS[args.workload][0], 'name': args.workload, 'particles': n,
                        'l2': 'flushed between timed steps (256 MB write)',
+                       'lanes_per_particle': bd.tdpd_lanes(h),
                        'area_volume': 'previous step (lagged)' if args.lagged_av else 'current step',
                        'random_flux': {'m_s': args.random_flux, 'rho': 3.0} if args.random_flux > 0 else 'off',
                        'neighbour_list': {'skin': skin, 'rebuilds_per_step': rebuild_rate} if skin > 0 else 'off (cell stencil every step)',
@@ -436,6 +440,8 @@ def main():
                     help='random flux of Eq. 7 with solute mass M_S (0: off, as in the paper)')
     ap.add_argument('--lagged-av', action='store_true',
                     help='area/volume constraints from the previous step (the concurrent variant of Sec. 3.3)')
+    ap.add_argument('--lanes', type=int, default=0,
+                    help='lanes per particle of the pair kernel (0: timed at commit)')
     ap.add_argument('--skin', type=float, default=None,
                     help='neighbour-list skin; 0 = cell mode (stencil every step); default: the library\'s')
     args = ap.parse_args()

@@ -173,6 +173,10 @@ tdpd_status tdpd_set_stream(tdpd_sys *s, void *cuda_stream);
  * the paper (a scheduling choice of this implementation). */
 tdpd_status tdpd_set_lanes(tdpd_sys *s, int lanes);
 
+/* Lanes per particle the pair kernel uses (fixed at commit; before commit the
+ * value tdpd_set_lanes set, 0 when timed). */
+int tdpd_lanes(const tdpd_sys *s);
+
 /* Skin of the Verlet neighbour lists of the pair kernel (length units): each
  * particle keeps the partners within max(rc, rcc) + skin found at a list
  * build; a replica rebuilds its lists (and re-sorts its cells) in the step

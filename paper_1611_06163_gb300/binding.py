@@ -70,6 +70,7 @@ def _load():
         'tdpd_set_stream': ([P, P], I),
         'tdpd_set_lanes': ([P, I], I),
         'tdpd_set_skin': ([P, C.c_float], I),
+        'tdpd_lanes': ([P], I),
         'tdpd_set_random_flux': ([P, C.c_float, C.c_float], I),
         'tdpd_set_body_force_profile': ([P, I], I),
         'tdpd_list_rebuilds': ([P, I, C.POINTER(C.c_int64)], I),
@@ -204,6 +205,10 @@ def tdpd_set_random_flux(h, m_s, rho):
 
 def tdpd_set_body_force_profile(h, mode):
     _chk(h, lib.tdpd_set_body_force_profile(h, int(mode)))
+
+
+def tdpd_lanes(h):
+    return lib.tdpd_lanes(h)
 
 
 def tdpd_commit(h):

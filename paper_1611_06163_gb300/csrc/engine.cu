@@ -1275,6 +1275,12 @@ tdpd_status tdpd_set_skin(tdpd_sys *s, float skin)
 
 tdpd_status tdpd_commit(tdpd_sys *s) { return ensure(s); }
 
+int tdpd_lanes(const tdpd_sys *s)
+{
+    if (!s) return 0;
+    return s->committed ? s->lpp : s->lanes_fixed;
+}
+
 tdpd_status tdpd_list_rebuilds(tdpd_sys *s, int r, int64_t *out)
 {
     tdpd_status rc = ensure(s);

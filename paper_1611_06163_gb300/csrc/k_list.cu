@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(128) k_list_build(ListArgs A)
     const float oy = pi.y - (float)cy * P.h[1], oz = pi.z - (float)cz * P.h[2];
     const float eps = 1e-4f * fmaxf(P.h[0], fmaxf(P.h[1], P.h[2]));
     const float rl2 = P.rlist2;
-    int *out = A.nl + (size_t)(gt >> 5) * A.cap * 32 + (gt & 31);
+    int *out = A.nl + (size_t)(gt >> 5) * A.cap * 32 + (gt & 31);   // next entry
+    const int cap = A.cap;
     int c = 0;
     for (int row = sub; row < nrow; row += LPP) {
         RowSeg g = {{0, 0}, {0, 0}, 0.f, 0.f, 0.f};
@@ -92,19 +93,36 @@ __global__ void __launch_bounds__(128) k_list_build(ListArgs A)
             const float px = pi.x + (sg ? g.sx1 : 0.f);
             const int je = g.je[sg];
             // four candidates per trip, their loads in flight together;
-            // appended in slot order
+            // appended in slot order (the capacity test once per trip while
+            // four more entries fit)
             for (int j0 = g.jb[sg]; j0 < je; j0 += 4) {
                 float4 pj[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) pj[u] = j0 + u < je ? A.pos[j0 + u] : make_float4(1e30f, 0.f, 0.f, 0.f);
+                bool ok[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u;
                     const float dx = px - pj[u].x, dy = py - pj[u].y, dz = pz - pj[u].z;
-                    if (j < je && j != i && dx * dx + dy * dy + dz * dz < rl2) {
-                        if (c < A.cap) out[(size_t)c * 32] = j;
-                        ++c;
-                    }
+                    ok[u] = j0 + u != i && dx * dx + dy * dy + dz * dz < rl2;
+                }
+                if (c + 4 <= cap) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (ok[u]) {
+                            *out = j0 + u;
+                            out += 32;
+                            ++c;
+                        }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (ok[u]) {
+                            if (c < cap) {
+                                *out = j0 + u;
+                                out += 32;
+                            }
+                            ++c;
+                        }
                 }
             }
         }
