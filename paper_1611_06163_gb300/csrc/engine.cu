@@ -438,6 +438,7 @@ ListArgs list_args(tdpd_sys *s, const Buffers &b, const uint32_t *rb, int cap)
 {
     ListArgs l{};
     l.pos = b.pos; l.vel = b.vel; l.reps = s->d_reps; l.cell_start = s->cell_start; l.rb = rb;
+    l.n_rep = (int)s->reps.size();
     l.nl = s->nl; l.nlc = s->nlc; l.xb = s->xb; l.err = s->errw; l.n = s->N; l.lpp = s->lpp; l.cap = cap;
     return l;
 }

@@ -67,6 +67,7 @@ template <int LPP>
 __global__ void __launch_bounds__(128) k_list_build(ListArgs A)
 {
     pdl_enter();
+    if (!A.rb[A.n_rep]) return;                       // no replica rebuilds
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = gt / LPP, sub = gt % LPP;
     if (i >= A.n) return;

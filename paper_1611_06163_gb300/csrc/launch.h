@@ -66,6 +66,7 @@ struct ListArgs {
     const RepParams *reps;
     const int *cell_start;
     const uint32_t *rb;          // [n_rep + 1] rebuild flags, rb[n_rep]: any
+    int n_rep;
     int *nl, *nlc;
     float4 *xb;
     uint32_t *err;
