@@ -428,6 +428,7 @@ void launch_pair(const PairArgs &a, cudaStream_t st)
         switch (a.ns) {
         case 1: launch_ns<1, true>(a, st); break;
         case 2: launch_ns<2, true>(a, st); break;
+        case 10: launch_ns<10, true>(a, st); break;     // the paper's ten-species case
         default: launch_ns<0, true>(a, st); break;
         }
     } else {
