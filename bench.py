@@ -38,6 +38,13 @@ import workloads as W  # noqa: E402
 
 METRIC = 'tDPD particle-steps/s on 1 GB300 (% HBM roofline); batched vs plain at tol'
 UNIT = 'particle-steps/s'
+# DRAM bytes (read + write) of one k_pair launch from one ncu capture of the
+# current kernel build (summaries under profiles/), keyed by workload, skin
+# and lane count; the capture is cold-cache, the bench step follows an L2
+# flush, so the two see the same misses.
+PAIR_TRAFFIC = {('single_rbc', 0.2, 4): 12.973312e6, ('fluid_786k', 0.2, 1): 343.278592e6 + 27.528192e6}
+
+
 def _ns10(d):
     d['kappa'][...] = np.linspace(0.5, 2.0, int(d['n_species']), dtype=np.float32)
     return d
@@ -318,8 +325,10 @@ def run_native(args):
     alu_peak = 152 * 128 * sm_max_mhz() * 1e6 / 1e12
     alu = ops_pp * n_all / (pair_ms * 1e-3) / 1e12
     gbs = bytes_pp * n_all / (pair_ms * 1e-3) / 1e9
+    lanes_now = bd.tdpd_lanes(h)
     roof = {'bound': 'alu', 'achieved': alu, 'peak': alu_peak, 'unit': 'Tops/s', 'frac': alu / alu_peak,
-            'traffic': None, 'peak_source': 'derived: 152 SMs x 128 lanes x %.0f MHz (measured max clock)' % sm_max_mhz(),
+            'traffic': (PAIR_TRAFFIC.get((args.workload, skin, lanes_now))
+                        if not args.random_flux and not args.cells_per_cutoff else None), 'peak_source': 'derived: 152 SMs x 128 lanes x %.0f MHz (measured max clock)' % sm_max_mhz(),
             'kernel': 'k_pair', 'ops_per_particle': ops_pp,
             'hbm': {'achieved': gbs, 'peak': hbm, 'unit': 'GB/s', 'frac': gbs / hbm, 'peak_source': src,
                     'bytes_per_particle': bytes_pp},
