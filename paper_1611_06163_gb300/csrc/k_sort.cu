@@ -115,55 +115,75 @@ __global__ void k_rank_gather(Buffers cur, Buffers nxt, const RepParams *__restr
     const bool any = !rb || rb[n_rep] != 0u;
     if (tile_zero && any)
         for (int t = d; t < n_tiles; t += gridDim.x * blockDim.x) tile_zero[t] = 0;
-    if (d >= n) return;
-    int id, src, dst;
-    if (any) {
-        const int2 key = keys[d];
-        id = key.x;
-        src = key.y;
-        const int c = cellrank[src].x;
-        const int lo = cell_start[c], hi = cell_start[c + 1];
-        int rank = 0;
-        for (int e = lo; e < hi; ++e) rank += (keys[e].x < id);
-        dst = lo + rank;
-        // a replica that keeps its list keeps its slots (its cells map onto
-        // its own slot range, so this is a permutation of that range)
-        if (rb && rb[wbits(cur.vel[src].w)] == 0u) dst = src;
-    } else {
-        src = dst = d;
-        id = wbits(cur.pos[d].w) & ID_MASK;
-    }
+    const bool valid = d < n;
+    int id = 0, src = 0, dst = 0;
+    bool pred = false;          // the species rows get the predictor
+    float ldt = 0.0f;
+    if (valid) {
+        if (any) {
+            const int2 key = keys[d];
+            id = key.x;
+            src = key.y;
+            const int c = cellrank[src].x;
+            const int lo = cell_start[c], hi = cell_start[c + 1];
+            int rank = 0;
+            for (int e = lo; e < hi; ++e) rank += (keys[e].x < id);
+            dst = lo + rank;
+            // a replica that keeps its list keeps its slots (its cells map
+            // onto its own slot range, so this is a permutation of that range)
+            if (rb && rb[wbits(cur.vel[src].w)] == 0u) dst = src;
+        } else {
+            src = dst = d;
+            id = wbits(cur.pos[d].w) & ID_MASK;
+        }
 
-    float4 p = cur.pos[src];
-    float4 v = cur.vel[src];
-    float4 f = cur.frc[src];
-    float4 vt = cur.vt[src];
-    const int r = wbits(v.w);
-    const RepParams &P = reps[r];
-    const int type = (int)((uint32_t)wbits(p.w) >> 24);
-    const bool frozen = (P.frozen_mask >> type) & 1u;
-    float4 vtn = make_float4(v.x, v.y, v.z, vt.w);
-    if (predict && !frozen) {
-        bool flip;
-        float3 rn = predict_pos(P, p, v, f, flip);
-        p.x = rn.x; p.y = rn.y; p.z = rn.z;
-        if (flip) { v.x = -v.x; v.y = -v.y; v.z = -v.z; }
-        vtn.x = __fmaf_rn(P.ldt, f.x, v.x);
-        vtn.y = __fmaf_rn(P.ldt, f.y, v.y);
-        vtn.z = __fmaf_rn(P.ldt, f.z, v.z);
+        float4 p = cur.pos[src];
+        float4 v = cur.vel[src];
+        float4 f = cur.frc[src];
+        float4 vt = cur.vt[src];
+        const int r = wbits(v.w);
+        const RepParams &P = reps[r];
+        const int type = (int)((uint32_t)wbits(p.w) >> 24);
+        const bool frozen = (P.frozen_mask >> type) & 1u;
+        float4 vtn = make_float4(v.x, v.y, v.z, vt.w);
+        pred = predict && !frozen;
+        ldt = P.ldt;
+        if (pred) {
+            bool flip;
+            float3 rn = predict_pos(P, p, v, f, flip);
+            p.x = rn.x; p.y = rn.y; p.z = rn.z;
+            if (flip) { v.x = -v.x; v.y = -v.y; v.z = -v.z; }
+            vtn.x = __fmaf_rn(P.ldt, f.x, v.x);
+            vtn.y = __fmaf_rn(P.ldt, f.y, v.y);
+            vtn.z = __fmaf_rn(P.ldt, f.z, v.z);
+        }
+        nxt.pos[dst] = p;
+        nxt.vel[dst] = v;
+        nxt.frc[dst] = f;
+        nxt.vt[dst] = vtn;
+        inv[P.pbase + id] = dst;
     }
-    nxt.pos[dst] = p;
-    nxt.vel[dst] = v;
-    nxt.frc[dst] = f;
-    nxt.vt[dst] = vtn;
-    for (int s = 0; s < ns; ++s) {
-        float cs = cur.C[(size_t)src * ns + s];
-        float qs = cur.Q[(size_t)src * ns + s];
-        nxt.C[(size_t)dst * ns + s] = cs;
-        nxt.Q[(size_t)dst * ns + s] = qs;
-        nxt.Ct[(size_t)dst * ns + s] = (predict && !frozen) ? __fmaf_rn(P.ldt, qs, cs) : cs;
+    // species rows, the warp's 32 particles together: element e of the warp's
+    // ns * 32 values is species e % ns of its particle e / ns, so consecutive
+    // lanes touch consecutive floats of a row (several rows per instruction)
+    const int lane = threadIdx.x & 31;
+    const int total = ns * 32;
+    for (int base = 0; base < total; base += 32) {
+        const int e = base + lane;
+        const int q = e / ns, sp = e - q * ns;           // particle (lane) and species
+        const int sq = __shfl_sync(0xffffffffu, src, q);
+        const int dq = __shfl_sync(0xffffffffu, dst, q);
+        const int pq = __shfl_sync(0xffffffffu, pred ? 1 : 0, q);
+        const float lq = __shfl_sync(0xffffffffu, ldt, q);
+        const int vq = __shfl_sync(0xffffffffu, valid ? 1 : 0, q);
+        if (e < total && vq) {
+            const float cs = cur.C[(size_t)sq * ns + sp];
+            const float qs = cur.Q[(size_t)sq * ns + sp];
+            nxt.C[(size_t)dq * ns + sp] = cs;
+            nxt.Q[(size_t)dq * ns + sp] = qs;
+            nxt.Ct[(size_t)dq * ns + sp] = pq ? __fmaf_rn(lq, qs, cs) : cs;
+        }
     }
-    inv[P.pbase + id] = dst;
 }
 
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
