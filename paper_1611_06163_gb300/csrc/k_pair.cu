@@ -231,12 +231,20 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
         const int nit = __reduce_max_sync(0xffffffffu, cnt);
         const float Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];
         const float iLx = P.inv_L[0], iLy = P.inv_L[1], iLz = P.inv_L[2];
+        // the next trip's indices are loaded while this trip's partners are
+        // fetched, so a trip waits for one load latency, not two
+        int jn[UNR_LIST];
+#pragma unroll
+        for (int u = 0; u < UNR_LIST; ++u) jn[u] = u < cnt ? nl[(size_t)u * 32] : 0;
         for (int t = 0; t < nit; t += UNR_LIST) {
             int jj[UNR_LIST];
             float4 pp[UNR_LIST];
             float cc[UNR_LIST];
 #pragma unroll
-            for (int u = 0; u < UNR_LIST; ++u) jj[u] = t + u < cnt ? nl[(size_t)(t + u) * 32] : 0;
+            for (int u = 0; u < UNR_LIST; ++u) {
+                jj[u] = jn[u];
+                jn[u] = t + UNR_LIST + u < cnt ? nl[(size_t)(t + UNR_LIST + u) * 32] : 0;
+            }
 #pragma unroll
             for (int u = 0; u < UNR_LIST; ++u) {
                 pp[u] = make_float4(0.f, 0.f, 0.f, 0.f);
