@@ -296,7 +296,7 @@ def run_native(args):
     pair_ms = float(mean_k[ipair])
     # The pair kernel is bound by instruction issue, not by memory: its roof
     # is the lane-operation rate 152 SMs x 128 lanes x the maximum SM clock.
-    # Algorithmic operations per particle-step: every
+    # Algorithmic operations per particle-step, counted from the equations: every
     # ordered pair inside the flux cut-off costs 20 + 4 (ns - 1) lane
     # operations, every pair inside the force cut-off another 110 (TEA-8 draw,
     # Box-Muller, Eq. 3); pair counts are the workload's mean density times

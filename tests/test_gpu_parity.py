@@ -171,7 +171,7 @@ def test_edge_positions_and_single_particle():
 
 
 def test_sums_vanish_on_gpu():
-    """P1 on the device: sum of pair forces and of fluxes vanish to rounding."""
+    """On the device: sum of pair forces and of fluxes vanish to rounding."""
     d = W.fluid_box(L=8.0, rho=4.0, n_species=2, seed=13)
     F, Q, Fo, _ = forces_vs_oracle(d, mode=1)
     F = F.astype(np.float64)
@@ -212,7 +212,7 @@ def test_deterministic_and_set_state():
 
 
 def test_batch_equals_replicas_alone():
-    """P12: replicas of uneven size stepped together in one batch give the
+    """Replicas of uneven size stepped together in one batch give the
     same bits as each stepped alone."""
     bd = B()
     reps = W.replica_ensemble(n_rep=5, seed=77, side_lo=8, side_hi=11)

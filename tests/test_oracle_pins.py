@@ -70,7 +70,7 @@ def _cloud(n, L, seed, periodic=(1, 1, 1), **kw):
 
 
 def test_pair_sums_vanish_momentum_and_species():
-    """P1: F_ij = -F_ji and Q_ij = -Q_ji, so sum F = 0, sum Q = 0; central
+    """F_ij = -F_ji and Q_ij = -Q_ji, so sum F = 0, sum Q = 0; central
     forces in an open box also give zero total torque."""
     d = _cloud(700, (7.0, 7.0, 7.0), 1, ns=3)
     o = oracle.Oracle(d, mode=0)
@@ -157,7 +157,7 @@ def test_random_force_variance_matches_sigma_wR():
 
 
 def test_cell_list_equals_all_pairs():
-    """P3: the cell-list mode sums the same pairs as the O(n^2) mode."""
+    """The cell-list mode sums the same pairs as the O(n^2) mode."""
     for L, ns in (((6.0, 6.0, 6.0), 1), ((5.0, 7.0, 6.0), 3)):
         d = _cloud(int(4 * np.prod(L)), L, 5, ns=ns)
         o = oracle.Oracle(d, mode=0)
@@ -173,7 +173,7 @@ def _mode_rate(k, kappa, rho, rcc, s_c):
 
 
 def test_flux_sine_mode_decay_matches_continuum_integral_and_eq9():
-    """P9: for uniformly random particles (g = 1) and C = sin(k x), the Fickian
+    """For uniformly random particles (g = 1) and C = sin(k x), the Fickian
     flux of Eq. 6 projects on the mode with rate
     kappa rho int w_DC(r) (1 - sin(kr)/(kr)) 4 pi r^2 dr, which tends to
     D^F k^2 with D^F from Eq. 9 as k -> 0."""
@@ -221,7 +221,7 @@ def test_free_particle_under_body_force_is_exact_parabola():
 
 
 def test_body_force_momentum_grows_linearly():
-    """P7: pair forces cancel, so sum p(t) = sum p(0) + N f t."""
+    """Pair forces cancel, so sum p(t) = sum p(0) + N f t."""
     d = _cloud(500, (5.0, 5.0, 5.0), 6, body_force=(0.05, -0.01, 0.0))
     o = oracle.Oracle(d, mode=1)
     p0 = o.vel.sum(0)
@@ -232,7 +232,7 @@ def test_body_force_momentum_grows_linearly():
 
 
 def test_reaction_total_follows_scalar_recurrence():
-    """P8: with A->B at rate k on all particles, the total of A obeys the
+    """With A->B at rate k on all particles, the total of A obeys the
     scalar GW-VV recurrence and A + B is conserved; the diffusive flux cancels."""
     rng = np.random.default_rng(7)
     n, kr = 400, 0.5
@@ -257,7 +257,7 @@ def test_reaction_total_follows_scalar_recurrence():
 
 
 def test_conservative_dynamics_conserves_energy():
-    """P10: gamma = sigma = 0 leaves a Hamiltonian soft-sphere system; velocity
+    """With gamma = sigma = 0, a Hamiltonian soft-sphere system; velocity
     Verlet keeps E = K + U bounded to O(dt^2)."""
     rng = np.random.default_rng(8)
     L = 5.0
@@ -302,7 +302,7 @@ def test_observables_definitions():
 
 @pytest.mark.slow
 def test_equilibrium_temperature_fdt():
-    """P6: with sigma^2 = 2 kT gamma and w_D = w_R^2 (Eq. 4) the fluid
+    """With sigma^2 = 2 kT gamma and w_D = w_R^2 (Eq. 4) the fluid
     equilibrates at kT = 1 within 1% (4000 particles, dt = 0.01)."""
     d = W.fluid_box(L=10.0, rho=4.0, seed=1001)
     o = oracle.Oracle(d, mode=1)
@@ -326,7 +326,7 @@ def _perturbed_sphere(n=42, radius=2.0, seed=0, dx=0.08, **mem):
 @pytest.mark.parametrize('parts', [1, 4, 8, 13])
 @pytest.mark.parametrize('theta0', [0.0, 0.1])
 def test_membrane_conservative_forces_are_minus_energy_gradient(parts, theta0):
-    """P4: bond (Eq. 10-11), area/volume (Eq. 14-15) and bending (Eq. 16)
+    """Bond (Eq. 10-11), area/volume (Eq. 14-15) and bending (Eq. 16)
     forces equal -grad of their energies (central differences)."""
     d = _perturbed_sphere(theta0=theta0)
     o = oracle.Oracle(d, mode=1)
@@ -360,7 +360,7 @@ def test_bonds_are_force_free_at_rest_length():
 
 @pytest.mark.parametrize('edge', [1.0, 2.0])
 def test_icosahedron_area_volume_and_angles(edge):
-    """P5: the gather of Eq. 14-15 and the angle of Eq. 16 on a regular
+    """The gather of Eq. 14-15 and the angle of Eq. 16 on a regular
     icosahedron equal the textbook values."""
     row = [r for r in read_golden('icosahedron.txt') if float(r[0]) == edge][0]
     A, V, cth = float(row[1]), float(row[2]), float(row[3])
