@@ -257,7 +257,7 @@ def test_reaction_total_follows_scalar_recurrence():
 
 
 def test_conservative_dynamics_conserves_energy():
-    """With gamma = sigma = 0, a Hamiltonian soft-sphere system; velocity
+    """With gamma = sigma = 0 the soft-sphere system is Hamiltonian; velocity
     Verlet keeps E = K + U bounded to O(dt^2)."""
     rng = np.random.default_rng(8)
     L = 5.0
