@@ -1,0 +1,93 @@
+"""Statistical agreement of long runs, GPU against the FP64 oracle.
+
+Beyond ten steps the two trajectories drift apart (the dynamics amplify
+rounding differences), so they are compared through the statistics they
+sample: the temperature, the self-diffusion coefficient and the decay of a
+concentration profile, each within 1 %. Both start from the same state with
+the same random streams, on a fluid large enough (about 88,000 particles)
+that each statistic is sampled to a few tenths of a per cent.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_common import B, wrap_diff
+
+pytestmark = pytest.mark.gpu
+
+SNAP = 20           # steps between snapshots
+NSNAP = 30          # 600 steps, t = 6
+
+
+def _stats(pos_series, vel_series, conc_series, L):
+    """Unwrapped displacements from successive snapshots (each well under half
+    a box), temperature per snapshot, and the amplitude of the sin(2 pi x/L)
+    mode of the concentration per snapshot."""
+    L = np.asarray(L, np.float64)
+    unwrapped = [np.asarray(pos_series[0], np.float64)]
+    for a, b in zip(pos_series[:-1], pos_series[1:]):
+        unwrapped.append(unwrapped[-1] + wrap_diff(b, a, L))
+    kT = []
+    for v in vel_series:
+        v = np.asarray(v, np.float64)
+        dv = v - v.mean(axis=0)
+        kT.append(float((dv * dv).sum() / (3 * (len(v) - 1))))
+    amp = []
+    for p, c in zip(pos_series, conc_series):
+        s = np.sin(2 * np.pi * np.asarray(p, np.float64)[:, 0] / L[0])
+        amp.append(float(2.0 * np.mean(np.asarray(c, np.float64)[:, 0] * s)))
+    return unwrapped, np.array(kT), np.array(amp)
+
+
+def _msd_coefficient(unwrapped, dt_snap, t0s, lag):
+    out = []
+    for t0 in t0s:
+        i0 = int(round(t0 / dt_snap))
+        i1 = i0 + int(round(lag / dt_snap))
+        d = unwrapped[i1] - unwrapped[i0]
+        out.append(np.mean(np.sum(d * d, axis=1)) / (6.0 * lag))
+    return float(np.mean(out))
+
+
+def test_long_run_temperature_diffusion_and_concentration_profile():
+    bd = B()
+    L = 28.0
+    d = W.fluid_box(L=L, rho=4.0, seed=81)                    # 87,808 particles, dt = 0.01
+    p = d['particles']
+    p['conc'][:, 0] = (0.5 + 0.4 * np.sin(2 * np.pi * p['pos'][:, 0].astype(np.float64) / L)).astype(np.float32)
+    h = bd.create_from(d)
+    bd.tdpd_commit(h)
+    g_pos, g_vel, g_conc = [], [], []
+    for k in range(NSNAP + 1):
+        if k:
+            bd.tdpd_step(h, SNAP)
+        x, v, c = bd.tdpd_read_state(h, 0, 1)
+        g_pos.append(x); g_vel.append(v); g_conc.append(c)
+    st = bd.tdpd_replica_status(h)
+    bd.tdpd_destroy(h)
+    assert (st == 0).all()
+
+    o = oracle.Oracle(d, mode=1)
+    o_pos, o_vel, o_conc = [o.pos.copy()], [o.vel.copy()], [o.conc.copy()]
+    for _ in range(NSNAP):
+        o.run(SNAP)
+        o_pos.append(o.pos.copy()); o_vel.append(o.vel.copy()); o_conc.append(o.conc.copy())
+
+    dts = SNAP * float(np.float32(d['dt']))
+    gu, gkT, gamp = _stats(g_pos, g_vel, g_conc, d['L'])
+    ou, okT, oamp = _stats(o_pos, o_vel, o_conc, d['L'])
+    # temperature over t in [2, 6] (after the random start has relaxed)
+    i2 = int(round(2.0 / dts))
+    assert gkT[i2:].mean() == pytest.approx(okT[i2:].mean(), rel=0.01)
+    assert gkT[i2:].mean() == pytest.approx(1.0, rel=0.03)
+    # self-diffusion from the mean squared displacement over a lag of 4
+    Dg = _msd_coefficient(gu, dts, (1.6, 2.0), 4.0)
+    Do = _msd_coefficient(ou, dts, (1.6, 2.0), 4.0)
+    assert Dg == pytest.approx(Do, rel=0.01), (Dg, Do)
+    # concentration profile: the sine mode decays; its amplitude at t = 2, 4, 6
+    for t in (2.0, 4.0, 6.0):
+        i = int(round(t / dts))
+        assert gamp[i] == pytest.approx(oamp[i], rel=0.01), (t, gamp[i], oamp[i])
+    assert gamp[-1] < 0.9 * gamp[0]
