@@ -91,3 +91,30 @@ def test_long_run_temperature_diffusion_and_concentration_profile():
         i = int(round(t / dts))
         assert gamp[i] == pytest.approx(oamp[i], rel=0.01), (t, gamp[i], oamp[i])
     assert gamp[-1] < 0.9 * gamp[0]
+
+
+def test_rbc_area_and_volume_hold_at_targets_in_solvent():
+    """The single-RBC workload on the device: over t = 5 to 10 the cell's
+    FP64 area and volume stay within 1 % of the targets A0 and V0 of the
+    oracle's membrane model (the cell starts 1.2 % above V0). The penalty of
+    Eq. 14-15 is finite, so thermal undulations and the solvent hold the
+    mean area about 0.5 % below A0."""
+    bd = B()
+    d = W.single_rbc(seed=91)
+    o = oracle.Oracle(d, mode=1)
+    _, _, A0, V0 = o.membrane_rest()
+    h = bd.create_from(d)
+    bd.tdpd_commit(h)
+    bd.tdpd_step(h, 1000)                       # t = 5 at dt = 0.005
+    A, V = [], []
+    for _ in range(20):
+        bd.tdpd_step(h, 50)
+        a, v = bd.tdpd_read_rbc(h, 0, 1)
+        A.append(a[0]); V.append(v[0])
+    st = bd.tdpd_replica_status(h)
+    bd.tdpd_destroy(h)
+    assert (st == 0).all()
+    assert abs(np.mean(A) - A0[0]) / A0[0] < 1e-2
+    assert abs(np.mean(V) - V0[0]) / V0[0] < 1e-2
+    assert np.max(np.abs(np.array(A) - A0[0])) / A0[0] < 2e-2
+    assert np.max(np.abs(np.array(V) - V0[0])) / V0[0] < 2e-2

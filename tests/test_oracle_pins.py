@@ -542,3 +542,22 @@ def test_flipped_body_force_drives_each_half_oppositely():
     o = oracle.Oracle(d, mode=0)
     o.run(200)
     assert np.abs(o.vel[:, 0] - f32 * t).max() < 1e-12
+
+
+def test_membrane_relaxes_to_its_area_and_volume_targets():
+    """Area and volume constraints (Eq. 14-15) hold a cell at its targets: a
+    500-vertex biconcave membrane started 1.2 % above its target volume, with
+    the bond viscosity of Eq. 12 and no thermal noise, settles within 1e-3 of
+    A0 and V0 (the penalty balances the bond and bending forces a few 1e-4
+    off the targets)."""
+    verts, tri = W.biconcave_mesh(500, 8.0)
+    d = membrane_only(verts, tri, L=30.0, kT=0.0)
+    d['dt'] = np.float32(0.005)
+    o = oracle.Oracle(d, mode=1)
+    _, _, A0, V0 = o.membrane_rest()
+    _, AV = o.membrane_forces(parts=0)
+    assert abs(AV[0, 1] - V0[0]) / V0[0] > 0.01
+    o.run(2000)
+    _, AV = o.membrane_forces(parts=0)
+    assert abs(AV[0, 0] - A0[0]) / A0[0] < 1e-3
+    assert abs(AV[0, 1] - V0[0]) / V0[0] < 1e-3
