@@ -69,6 +69,8 @@ struct RbcDev {
     int a0j_off;    // offset of per-triangle rest areas
     int bond_off;   // offset of per-edge (l_m, k_p)
     double A0, V0;
+    double kgA0, kvV0;  // k_g / A0, k_v / V0 (Eq. 14-15 coefficients per unit excess)
+    double inv_nv;      // 1 / nv
 };
 
 // One closed triangulation (shared by every membrane with the same mesh).

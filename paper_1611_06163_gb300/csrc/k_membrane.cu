@@ -92,8 +92,9 @@ __global__ void __launch_bounds__(1024) k_mem_gather(MemArgs A)
         const double Ab = ff_value(v[0]), Vb = ff_value(v[1]);
         A.av_out[b] = make_double2(Ab, Vb);
         // constraint coefficients of Eq. 14-15, once per membrane in binary64
-        A.cgv_out[b] = make_float2((float)(P.m_kg * (Ab - R.A0) / R.A0), (float)(P.m_kv * (Vb - R.V0) / R.V0));
-        const double inv = 1.0 / T.nv;
+        // (divisions by A0, V0 and nv were done once on the host)
+        A.cgv_out[b] = make_float2((float)((Ab - R.A0) * R.kgA0), (float)((Vb - R.V0) * R.kvV0));
+        const double inv = R.inv_nv;
         float c3[3] = {(float)(ref.x + ff_value(v[2]) * inv), (float)(ref.y + ff_value(v[3]) * inv),
                        (float)(ref.z + ff_value(v[4]) * inv)};
         for (int c = 0; c < 3; ++c)
