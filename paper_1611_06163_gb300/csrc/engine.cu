@@ -72,7 +72,6 @@ struct tdpd_sys {
     bool use_list = false;
     int *nl = nullptr, *nlc = nullptr;   // neighbour lists (own allocation: resized by the lane count)
     int nl_cap = 0;
-    bool build_rows = false;             // list build with a warp per particle (timed at commit)
     size_t nl_ints = 0;
     float4 *xb = nullptr;
     uint32_t *disp[2] = {nullptr, nullptr}, *rb = nullptr, *rb_all = nullptr;
@@ -441,7 +440,6 @@ ListArgs list_args(tdpd_sys *s, const Buffers &b, const uint32_t *rb, int cap)
     l.pos = b.pos; l.vel = b.vel; l.reps = s->d_reps; l.cell_start = s->cell_start; l.rb = rb;
     l.n_rep = (int)s->reps.size();
     l.nl = s->nl; l.nlc = s->nlc; l.xb = s->xb; l.err = s->errw; l.n = s->N; l.lpp = s->lpp; l.cap = cap;
-    l.rows = s->build_rows ? 1 : 0;
     return l;
 }
 
@@ -671,34 +669,6 @@ tdpd_status prepare_list(tdpd_sys *s)
         s->nl_ints = need;
     }
     s->nl_cap = cap;
-    // the two list builds give identical lists; keep the faster (the warp
-    // per particle needs at most 32 stencil rows, m <= 2)
-    s->build_rows = false;
-    bool rows_ok = true;
-    for (const HostRep &R : s->reps) rows_ok = rows_ok && (2 * R.m + 1) * (2 * R.m + 1) <= 32;
-    if (rows_ok) {
-        cudaEvent_t e0, e1;
-        CU(cudaEventCreate(&e0));
-        CU(cudaEventCreate(&e1));
-        float ms[2] = {0.f, 0.f};
-        for (int v = 0; v < 2; ++v) {
-            s->build_rows = v == 1;
-            launch_list_build(list_args(s, s->buf[1], s->rb_all, cap), st);   // warm-up
-            cudaEventRecord(e0, st);
-            for (int k = 0; k < 3; ++k) launch_list_build(list_args(s, s->buf[1], s->rb_all, cap), st);
-            cudaEventRecord(e1, st);
-            cudaError_t e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[v], e0, e1);
-            if (e != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return fail(s, TDPD_ECUDA, "list build timing: %s", cudaGetErrorString(e));
-            }
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        s->build_rows = ms[1] < ms[0];
-    }
     launch_list_build(list_args(s, s->buf[1], s->rb_all, cap), st);
     CU(cudaGetLastError());
     return TDPD_OK;

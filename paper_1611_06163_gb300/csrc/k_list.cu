@@ -139,86 +139,6 @@ void launch_rebuild_decide(const uint32_t *disp, uint32_t *disp_clear, uint32_t 
     launch_pdl(k_rebuild_decide, 1, 256, st, disp, disp_clear, rb, reps, n_rep, force, step_ctr, builds);
 }
 
-// The same lists with a warp per particle: the LPP pair lanes of the particle
-// each get G = 32/LPP threads, thread k taking the lane's k-th stencil row
-// (row = sub + k LPP). A first walk counts each row's partners, the group's
-// counts are prefix-summed with shuffles, and a second walk writes every row
-// at its offset, so the list comes out in the order of one thread walking the
-// rows (identical to k_list_build). Two walks of one row each instead of one
-// walk of all the lane's rows: shorter chains for systems too small to hide
-// the per-thread latency. Needs (2m+1)^2 <= 32 rows per particle (m <= 2).
-template <int LPP>
-__global__ void __launch_bounds__(256) k_list_build_rows(ListArgs A)
-{
-    constexpr int G = 32 / LPP;
-    pdl_enter();
-    if (!A.rb[A.n_rep]) return;                       // no replica rebuilds
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int gl = (int)(t / G), k = (int)(t % G);    // pair lane, row index
-    const int i = gl / LPP, sub = gl % LPP;
-    const int ic = i < A.n ? i : 0;
-    const float4 pi = A.pos[ic];
-    const int rep = wbits(A.vel[ic].w);
-    const bool lane_ok = i < A.n && A.rb[rep] != 0u;  // uniform over the group
-    const RepParams &P = A.reps[rep];
-    const int m = P.m_stencil, width = 2 * m + 1, nrow = width * width;
-    const int row = sub + k * LPP;
-    const int cx = cell_coord(pi.x, P.cell_scale[0], P.nc[0]);
-    const int cy = cell_coord(pi.y, P.cell_scale[1], P.nc[1]);
-    const int cz = cell_coord(pi.z, P.cell_scale[2], P.nc[2]);
-    const float oy = pi.y - (float)cy * P.h[1], oz = pi.z - (float)cz * P.h[2];
-    const float eps = 1e-4f * fmaxf(P.h[0], fmaxf(P.h[1], P.h[2]));
-    const float rl2 = P.rlist2;
-    RowSeg g = {{0, 0}, {0, 0}, 0.f, 0.f, 0.f};
-    const bool rok = lane_ok && row < nrow &&
-                     stencil_row(P, A.cell_start, pi, cx, cy, cz, row, oy, oz, eps, rl2 * 1.0002f, g);
-    const float py = pi.y + g.sy, pz = pi.z + g.sz;
-    // the row's partners: visit(j) for each, in slot order
-    auto walk = [&](auto visit) {
-#pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-            const float px = pi.x + (sg ? g.sx1 : 0.f);
-            const int je = g.je[sg];
-            for (int j0 = g.jb[sg]; j0 < je; j0 += 4) {
-                float4 pj[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) pj[u] = j0 + u < je ? A.pos[j0 + u] : make_float4(1e30f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float dx = px - pj[u].x, dy = py - pj[u].y, dz = pz - pj[u].z;
-                    if (j0 + u != i && dx * dx + dy * dy + dz * dz < rl2) visit(j0 + u);
-                }
-            }
-        }
-    };
-    int c = 0;
-    if (rok) walk([&](int) { ++c; });
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o, G);
-        if (k >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, G - 1, G);
-    const int cap = A.cap;
-    int e = incl - c;                                  // this row's first entry
-    if (rok && e < cap) {
-        int *out = A.nl + (size_t)(gl >> 5) * cap * 32 + (gl & 31) + (size_t)e * 32;
-        walk([&](int j) {
-            if (e < cap) {
-                *out = j;
-                out += 32;
-            }
-            ++e;
-        });
-    }
-    if (lane_ok && k == 0) {
-        A.nlc[gl] = min(total, cap);
-        if (total > cap) atomicOr(A.err + rep, 2u);
-        if (sub == 0) A.xb[i] = pi;
-    }
-}
-
 void launch_bin_next(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum, int2 *cellrank,
                      const uint32_t *any, cudaStream_t st)
 {
@@ -229,18 +149,6 @@ void launch_bin_next(const Buffers &b, const RepParams *reps, int n, int *count,
 void launch_list_build(const ListArgs &a, cudaStream_t st)
 {
     if (a.n <= 0) return;
-    if (a.rows && a.cap > 0) {
-        const int g = (int)(((long)a.n * 32 + 255) / 256);
-        switch (a.lpp) {
-        case 1: launch_pdl(k_list_build_rows<1>, g, 256, st, a); break;
-        case 2: launch_pdl(k_list_build_rows<2>, g, 256, st, a); break;
-        case 4: launch_pdl(k_list_build_rows<4>, g, 256, st, a); break;
-        case 8: launch_pdl(k_list_build_rows<8>, g, 256, st, a); break;
-        case 16: launch_pdl(k_list_build_rows<16>, g, 256, st, a); break;
-        default: launch_pdl(k_list_build_rows<32>, g, 256, st, a); break;
-        }
-        return;
-    }
     const int g = (int)(((long)a.n * a.lpp + 127) / 128);
     switch (a.lpp) {
     case 1: launch_pdl(k_list_build<1>, g, 128, st, a); break;

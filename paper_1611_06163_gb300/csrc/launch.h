@@ -71,7 +71,6 @@ struct ListArgs {
     float4 *xb;
     uint32_t *err;
     int n, lpp, cap;             // cap == 0: count only
-    int rows;                    // a warp per particle (k_list_build_rows) instead of a thread per lane
 };
 
 struct MemArgs {
