@@ -68,17 +68,13 @@ struct RbcDev {
     int nv, ntri, ne;
     int a0j_off;    // offset of per-triangle rest areas
     int bond_off;   // offset of per-edge (l_m, k_p)
+    int tri_off;    // offset of its triangles (int[3 ntri]) in the triangle table
+    int fan_off;    // offset of vertex 0's fan in the fan table
+    int fan_stride; // fan entries per vertex: the mesh's largest degree
+    int pad_;
     double A0, V0;
     double kgA0, kvV0;  // k_g / A0, k_v / V0 (Eq. 14-15 coefficients per unit excess)
     double inv_nv;      // 1 / nv
-};
-
-// One closed triangulation (shared by every membrane with the same mesh).
-struct TopoDev {
-    int nv, ntri, ne;
-    int tri_off;    // int[ntri*3]
-    int ring_off;   // int[nv+1] CSR offsets into the ring arrays (absolute)
-    int max_deg;
 };
 
 // Ring (one-ring fan) entry of a vertex v, counter-clockwise seen from
@@ -88,6 +84,16 @@ struct RingEntry {
     int edge;     // edge index of (v, nb[l])
     int tri;      // triangle index of (v, nb[l], nb[l+1])
     int across;   // vertex opposite v across the edge (nb[l], nb[l+1])
+};
+
+// The device form of fan entry l of vertex v, at a fixed stride per vertex
+// (entry v * fan_stride + l of its mesh), with the cyclic neighbours nb[l+1]
+// and nb[l-1] included: a lane reaches all its vertex indices with one
+// 32-byte load and no offset table. Entries past the degree have nb = -1.
+struct __align__(16) FanEntry {
+    int nb, edge, tri, across;
+    int nb_next, nb_prev;
+    int pad0, pad1;
 };
 
 // Programmatic dependent launch: let the next kernel in the stream begin

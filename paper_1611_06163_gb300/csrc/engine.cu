@@ -90,9 +90,8 @@ struct tdpd_sys {
     uint32_t *errw = nullptr, *step_ctr = nullptr;
     RepParams *d_reps = nullptr;
     RbcDev *d_rbcs = nullptr;
-    TopoDev *d_topos = nullptr;
-    int *d_tri = nullptr, *d_ring_off = nullptr;
-    RingEntry *d_ring = nullptr;
+    int *d_tri = nullptr;
+    FanEntry *d_fan = nullptr;
     float *d_a0j = nullptr;
     float2 *d_bond = nullptr;
     float4 *d_ref[2] = {nullptr, nullptr};
@@ -407,7 +406,7 @@ MemArgs mem_args(tdpd_sys *s, int ref_in, int inc)
     const int q = 1 - ref_in;
     MemArgs m{};
     m.mx = s->mx; m.mv = s->mv; m.reps = s->d_reps; m.rbcs = s->d_rbcs;
-    m.topos = s->d_topos; m.tri = s->d_tri; m.ring_off = s->d_ring_off; m.ring = s->d_ring;
+    m.tri = s->d_tri; m.fan = s->d_fan;
     m.a0j = s->d_a0j; m.bond = s->d_bond; m.ref_in = s->d_ref[ref_in]; m.ref_out = s->d_ref[1 - ref_in];
     m.av_out = s->d_av[q]; m.cgv_out = s->d_cgv[q]; m.cgv_seq = s->d_cgv[q];
     m.cgv_lag = inc ? s->d_cgv[1 - q] : s->d_cgv[q];
@@ -883,34 +882,45 @@ tdpd_status commit(tdpd_sys *s)
         if ((rc = upload(s, s->cell_start + NC, tail.data(), tail.size()))) return rc;
     }
     if (s->n_rbc) {
-        std::vector<TopoDev> td;
-        std::vector<int> tri, roff;
-        std::vector<RingEntry> ring;
-        for (const Topo &T : s->topos) {
-            TopoDev D{};
-            D.nv = T.nv; D.ntri = T.ntri; D.ne = T.ne;
-            D.tri_off = (int)tri.size();
-            D.ring_off = (int)roff.size();
+        // per mesh: its triangles, and its fans at a fixed stride (the
+        // largest degree) with each entry's cyclic neighbours
+        std::vector<int> tri, t_tri(s->topos.size()), t_fan(s->topos.size()), t_stride(s->topos.size());
+        std::vector<FanEntry> fan;
+        for (size_t t = 0; t < s->topos.size(); ++t) {
+            const Topo &T = s->topos[t];
             int mx = 0;
             for (int v = 0; v < T.nv; ++v) mx = std::max(mx, T.ring_off[v + 1] - T.ring_off[v]);
-            D.max_deg = mx;
+            t_tri[t] = (int)tri.size();
+            t_fan[t] = (int)fan.size();
+            t_stride[t] = mx;
             tri.insert(tri.end(), T.tri.begin(), T.tri.end());
-            const int rbase = (int)ring.size();
-            for (int v = 0; v <= T.nv; ++v) roff.push_back(rbase + T.ring_off[v]);
-            ring.insert(ring.end(), T.ring.begin(), T.ring.end());
-            td.push_back(D);
+            for (int v = 0; v < T.nv; ++v) {
+                const int o = T.ring_off[v], deg = T.ring_off[v + 1] - o;
+                for (int l = 0; l < mx; ++l) {
+                    FanEntry F{-1, -1, -1, -1, -1, -1, 0, 0};
+                    if (l < deg) {
+                        const RingEntry &E = T.ring[o + l];
+                        F = FanEntry{E.nb, E.edge, E.tri, E.across, T.ring[o + (l + 1) % deg].nb,
+                                     T.ring[o + (l + deg - 1) % deg].nb, 0, 0};
+                    }
+                    fan.push_back(F);
+                }
+            }
         }
-        if ((rc = dalloc(s, &s->d_rbcs, s->n_rbc)) || (rc = dalloc(s, &s->d_topos, td.size())) ||
-            (rc = dalloc(s, &s->d_tri, tri.size())) || (rc = dalloc(s, &s->d_ring_off, roff.size())) ||
-            (rc = dalloc(s, &s->d_ring, ring.size())) || (rc = dalloc(s, &s->d_a0j, a0j.size())) ||
+        for (RbcDev &D : s->h_rbcs) {
+            D.tri_off = t_tri[D.topo];
+            D.fan_off = t_fan[D.topo];
+            D.fan_stride = t_stride[D.topo];
+        }
+        if ((rc = dalloc(s, &s->d_rbcs, s->n_rbc)) || (rc = dalloc(s, &s->d_tri, tri.size())) ||
+            (rc = dalloc(s, &s->d_fan, fan.size())) || (rc = dalloc(s, &s->d_a0j, a0j.size())) ||
             (rc = dalloc(s, &s->d_bond, bond.size())) || (rc = dalloc(s, &s->d_ref[0], s->n_rbc)) ||
             (rc = dalloc(s, &s->d_ref[1], s->n_rbc)) || (rc = dalloc(s, &s->d_av[0], s->n_rbc)) ||
             (rc = dalloc(s, &s->d_av[1], s->n_rbc)) || (rc = dalloc(s, &s->d_cgv[0], s->n_rbc)) ||
             (rc = dalloc(s, &s->d_cgv[1], s->n_rbc)))
             return rc;
-        if ((rc = upload(s, s->d_rbcs, s->h_rbcs.data(), s->n_rbc)) || (rc = upload(s, s->d_topos, td.data(), td.size())) ||
-            (rc = upload(s, s->d_tri, tri.data(), tri.size())) || (rc = upload(s, s->d_ring_off, roff.data(), roff.size())) ||
-            (rc = upload(s, s->d_ring, ring.data(), ring.size())) || (rc = upload(s, s->d_a0j, a0j.data(), a0j.size())) ||
+        if ((rc = upload(s, s->d_rbcs, s->h_rbcs.data(), s->n_rbc)) || (rc = upload(s, s->d_tri, tri.data(), tri.size())) ||
+            (rc = upload(s, s->d_fan, fan.data(), fan.size())) || (rc = upload(s, s->d_a0j, a0j.data(), a0j.size())) ||
             (rc = upload(s, s->d_bond, bond.data(), bond.size())))
             return rc;
     }

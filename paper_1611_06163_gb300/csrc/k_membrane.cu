@@ -42,35 +42,60 @@ __device__ __forceinline__ float3 rel_pos(const RepParams &P, float4 x, float4 r
                        min_image(x.z - ref.z, P.L[2], P.periodic[2]));
 }
 
+// Vertices of a membrane staged in shared memory by K-Gather (larger
+// membranes read their triangle corners from global memory).
+constexpr int GATHER_STAGE_NV = 2048;
+
 // K-Gather: each thread takes at most two triangles and one vertex; the
 // binary32 terms are reduced with compensated float-float sums (warp
 // shuffles, then one warp over the warp totals) and converted to binary64 once.
+// The triangle indices and the vertex positions are loaded together (the
+// positions, relative to the reference point, into shared memory), so a cold
+// start costs two dependent memory round trips, not three.
 __global__ void __launch_bounds__(1024) k_mem_gather(MemArgs A)
 {
     pdl_enter();
     const int b = blockIdx.x;
     if (b == 0 && threadIdx.x == 0) A.mem_ctr[1 - A.q] = A.mem_ctr[A.q] + 1u;   // the next evaluation's
     const RbcDev R = A.rbcs[b];
-    const TopoDev T = A.topos[R.topo];
     const RepParams &P = A.reps[R.rep];
     const float4 ref = A.ref_in[b];
+    const int *tri = A.tri + R.tri_off;
+    __shared__ float4 xs[GATHER_STAGE_NV];
+    const bool staged = R.nv <= GATHER_STAGE_NV;
+    int3 pre[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int t = threadIdx.x + u * blockDim.x;
+        pre[u] = t < R.ntri ? make_int3(tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]) : make_int3(0, 0, 0);
+    }
     FF v[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) v[k] = FF{0.0f, 0.0f};
-    for (int t = threadIdx.x; t < T.ntri; t += blockDim.x) {
-        const int *tv = A.tri + T.tri_off + 3 * t;
-        const float3 x0 = rel_pos(P, A.mx[R.gbase + tv[0]], ref);
-        const float3 x1 = rel_pos(P, A.mx[R.gbase + tv[1]], ref);
-        const float3 x2 = rel_pos(P, A.mx[R.gbase + tv[2]], ref);
-        const float3 n = cross(sub(x1, x0), sub(x2, x0));
-        v[0] = ff_add(v[0], 0.5f * sqrtf(dot(n, n)));
-        v[1] = ff_add(v[1], dot(x0, cross(x1, x2)) * (1.0f / 6.0f));
-    }
-    for (int k = threadIdx.x; k < T.nv; k += blockDim.x) {
+    for (int k = threadIdx.x; k < R.nv; k += blockDim.x) {
         const float3 x = rel_pos(P, A.mx[R.gbase + k], ref);
+        if (staged) xs[k] = make_float4(x.x, x.y, x.z, 0.0f);
         v[2] = ff_add(v[2], x.x);
         v[3] = ff_add(v[3], x.y);
         v[4] = ff_add(v[4], x.z);
+    }
+    __syncthreads();
+    int u = 0;
+    for (int t = threadIdx.x; t < R.ntri; t += blockDim.x, ++u) {
+        const int3 tv = u == 0 ? pre[0] : u == 1 ? pre[1] : make_int3(tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]);
+        float3 x0, x1, x2;
+        if (staged) {
+            x0 = f3(xs[tv.x]);
+            x1 = f3(xs[tv.y]);
+            x2 = f3(xs[tv.z]);
+        } else {
+            x0 = rel_pos(P, A.mx[R.gbase + tv.x], ref);
+            x1 = rel_pos(P, A.mx[R.gbase + tv.y], ref);
+            x2 = rel_pos(P, A.mx[R.gbase + tv.z], ref);
+        }
+        const float3 n = cross(sub(x1, x0), sub(x2, x0));
+        v[0] = ff_add(v[0], 0.5f * sqrtf(dot(n, n)));
+        v[1] = ff_add(v[1], dot(x0, cross(x1, x2)) * (1.0f / 6.0f));
     }
     __shared__ FF sh[32][5];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -141,29 +166,26 @@ __global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) A.mem_ctr[1 - A.q] = A.mem_ctr[A.q] + 1u;
     const int b = blockIdx.y;
     const RbcDev R = A.rbcs[b];
-    const TopoDev T = A.topos[R.topo];
     const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
     const int lane8 = threadIdx.x & 7;
-    const bool live = v < T.nv;
+    const bool live = v < R.nv;
     const RepParams &P = A.reps[R.rep];
     float3 f = make_float3(0.f, 0.f, 0.f);
     if (live) {
         const float4 ref = A.ref_in[b];
         const float2 cgv = P.m_lagged ? A.cgv_lag[b] : A.cgv_seq[b];
         const float cg = cgv.x, cv = cgv.y;
-        const int off = A.ring_off[T.ring_off + v];
-        const int deg = A.ring_off[T.ring_off + v + 1] - off;
+        const FanEntry *fan = A.fan + R.fan_off + (size_t)v * R.fan_stride;
         const float3 xv = rel_pos(P, A.mx[R.gbase + v], ref);
         const float4 vv = A.mv[R.gbase + v];
         const uint32_t idv = (uint32_t)(R.gbase + v - P.pbase);
         const uint32_t step = A.mem_ctr[A.q] + P.step0;
-        for (int l = lane8; l < deg; l += 8) {
-            const RingEntry E = A.ring[off + l];
-            const RingEntry En = A.ring[off + (l + 1 == deg ? 0 : l + 1)];
-            const RingEntry Ep = A.ring[off + (l == 0 ? deg - 1 : l - 1)];
+        for (int l = lane8; l < R.fan_stride; l += 8) {
+            const FanEntry E = fan[l];
+            if (E.nb < 0) break;                      // past the vertex's degree
             const float3 xl = rel_pos(P, A.mx[R.gbase + E.nb], ref);
-            const float3 xn = rel_pos(P, A.mx[R.gbase + En.nb], ref);
-            const float3 xp = rel_pos(P, A.mx[R.gbase + Ep.nb], ref);
+            const float3 xn = rel_pos(P, A.mx[R.gbase + E.nb_next], ref);
+            const float3 xp = rel_pos(P, A.mx[R.gbase + E.nb_prev], ref);
             const float3 xw = rel_pos(P, A.mx[R.gbase + E.across], ref);
 
             // bond (v, nb[l]): Eq. 10-13

@@ -77,10 +77,8 @@ struct MemArgs {
     const float4 *mx, *mv;       // vertex position and v~ by load index
     const RepParams *reps;
     const RbcDev *rbcs;
-    const TopoDev *topos;
-    const int *tri;
-    const int *ring_off;
-    const RingEntry *ring;
+    const int *tri;              // triangle table (RbcDev::tri_off)
+    const FanEntry *fan;         // fan table (RbcDev::fan_off, fan_stride)
     const float *a0j;
     const float2 *bond;          // (l_m, k_p) per bond
     const float4 *ref_in;        // per-membrane reference point
