@@ -138,6 +138,16 @@ tdpd_status tdpd_set_random_flux(tdpd_sys *s, float m_s, float rho);
  * another mode. */
 tdpd_status tdpd_set_body_force_profile(tdpd_sys *s, int mode);
 
+/* Cylindrical wall for the Dirichlet transport validation (Sec. 4.1, Eq. 17):
+ * a mobile particle whose predicted position lies farther than radius from
+ * the axis y = L_y/2, z = L_z/2 (along x) is reflected back across the
+ * cylinder surface and its velocity reversed, as at the bounce-back planes.
+ * The concentration boundary itself comes from frozen particles outside the
+ * cylinder, whose C the integrator never changes. radius 0 (the default)
+ * disables it. Before commit; TDPD_EINVAL unless 0 <= radius and, for
+ * radius > 0, y and z are periodic and 2 radius < min(L_y, L_z). */
+tdpd_status tdpd_set_cylinder_wall(tdpd_sys *s, float radius);
+
 /* Membrane constants for every membrane of the replica (Sec. 2.2). */
 tdpd_status tdpd_set_membrane(tdpd_sys *s, const tdpd_membrane *m);
 

@@ -58,6 +58,7 @@ class _Sys(C.Structure):
         ('react_types', C.c_uint32),
         ('type', C.c_void_p), ('body', C.c_void_p), ('id', C.c_void_p),
         ('qr_ms', C.c_double), ('qr_rho', C.c_double), ('fbody_flip', C.c_int),
+        ('cyl_R', C.c_double),
     ]
 
 
@@ -161,6 +162,7 @@ class Oracle:
         s.fbody[:] = _f64(desc['body_force']).tolist()
         s.frozen_types = int(desc['frozen_types'])
         s.fbody_flip = int(desc.get('body_force_flip', 0))
+        s.cyl_R = float(_f64(desc.get('cylinder_radius', 0.0)))
         r = desc.get('reaction')
         if r:
             s.k_react, s.r_src, s.r_dst, s.react_types = float(_f64(r['k'])), r['src'], r['dst'], r['types']

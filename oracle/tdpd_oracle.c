@@ -732,6 +732,19 @@ int orc_run(const orc_sys *s, const orc_mem *m, double *pos, double *vel, double
                 }
                 rn[3 * i + c] = x;
             }
+            if (s->cyl_R > 0.0) {
+                /* bounce-back at the cylinder: distance d > R from the axis
+                 * becomes 2R - d along the same radial line */
+                const double cy = 0.5 * s->L[1], cz = 0.5 * s->L[2];
+                const double dy = rn[3 * i + 1] - cy, dz = rn[3 * i + 2] - cz;
+                const double d = sqrt(dy * dy + dz * dz);
+                if (d > s->cyl_R) {
+                    const double f = (2.0 * s->cyl_R - d) / d;
+                    rn[3 * i + 1] = cy + dy * f;
+                    rn[3 * i + 2] = cz + dz * f;
+                    flip = 1;
+                }
+            }
             if (flip)
                 for (int c = 0; c < 3; ++c) vel[3 * i + c] = -vel[3 * i + c];
             for (int c = 0; c < 3; ++c) vt[3 * i + c] = vel[3 * i + c] + lam * dt * F[3 * i + c];

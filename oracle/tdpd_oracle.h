@@ -43,6 +43,9 @@ typedef struct {
                                    * m_s = 0: no random flux */
     int fbody_flip;               /* 1: the body force is -fbody where z >= L_z/2
                                    * (the double Poiseuille flow of Sec. 4.1) */
+    double cyl_R;                 /* > 0: mobile particles stay within this distance of
+                                   * the axis y = L_y/2, z = L_z/2 (reflected radially,
+                                   * velocity reversed; the cylinder of Eq. 17) */
 } orc_sys;
 
 typedef struct orc_mem orc_mem;

@@ -73,6 +73,7 @@ def _load():
         'tdpd_lanes': ([P], I),
         'tdpd_set_random_flux': ([P, C.c_float, C.c_float], I),
         'tdpd_set_body_force_profile': ([P, I], I),
+        'tdpd_set_cylinder_wall': ([P, F], I),
         'tdpd_list_rebuilds': ([P, I, C.POINTER(C.c_int64)], I),
         'tdpd_commit': ([P], I),
         'tdpd_step': ([P, I], I),
@@ -205,6 +206,10 @@ def tdpd_set_random_flux(h, m_s, rho):
 
 def tdpd_set_body_force_profile(h, mode):
     _chk(h, lib.tdpd_set_body_force_profile(h, int(mode)))
+
+
+def tdpd_set_cylinder_wall(h, radius):
+    _chk(h, lib.tdpd_set_cylinder_wall(h, float(radius)))
 
 
 def tdpd_lanes(h):
@@ -420,6 +425,8 @@ def create_from(desc, stream_ptr=None):
             tdpd_add_rbc(h, rb['pos'], rb['vel'], rb['conc'], rb['type'], rb['tri'], rb['rest'])
         if desc.get('body_force_flip'):
             tdpd_set_body_force_profile(h, 1)
+        if desc.get('cylinder_radius'):
+            tdpd_set_cylinder_wall(h, desc['cylinder_radius'])
         q = desc.get('random_flux')
         if q:
             tdpd_set_random_flux(h, q['m_s'], q['rho'])

@@ -58,6 +58,8 @@ struct RepParams {
     int m_lagged;            // area/volume constraints from the previous step's totals
     float qr_coef;           // random flux: m_s sqrt(rho) (Eq. 7-8); 0: off
     int fbody_flip;          // body force negated where z >= L_z/2 (double Poiseuille)
+    float cyl_R;             // bounce-back cylinder radius about the x axis through the box centre; 0: none
+    float cyl_c[2];          // the axis: (y, z) = (L_y/2, L_z/2)
 };
 
 // One membrane.
@@ -193,13 +195,12 @@ struct RowSeg {
     float sx1, sy, sz;       // x shift of the second range; y and z shifts
 };
 
-__device__ __forceinline__ bool stencil_row(const RepParams &P, const int *__restrict__ cs, float4 pi, int cx,
-                                            int cy, int cz, int row, float oy, float oz, float eps,
-                                            float rtrim2, RowSeg &g)
+// Row (dy, dz) of the stencil, |dy|, |dz| <= m.
+__device__ __forceinline__ bool stencil_row_d(const RepParams &P, const int *__restrict__ cs, float4 pi, int cx,
+                                              int cy, int cz, int dy, int dz, int m, float oy, float oz,
+                                              float eps, float rtrim2, RowSeg &g)
 {
-    const int m = P.m_stencil, width = 2 * m + 1;
     const float hy = P.h[1], hz = P.h[2];
-    const int dy = row % width - m, dz = row / width - m;
     // distance from particle i to the slab of the row's cells
     const float ay = dy == 0 ? 0.f : (dy > 0 ? (float)dy * hy - oy : oy - (float)(dy + 1) * hy);
     const float az = dz == 0 ? 0.f : (dz > 0 ? (float)dz * hz - oz : oz - (float)(dz + 1) * hz);
@@ -236,6 +237,14 @@ __device__ __forceinline__ bool stencil_row(const RepParams &P, const int *__res
     return true;
 }
 
+__device__ __forceinline__ bool stencil_row(const RepParams &P, const int *__restrict__ cs, float4 pi, int cx,
+                                            int cy, int cz, int row, float oy, float oz, float eps,
+                                            float rtrim2, RowSeg &g)
+{
+    const int m = P.m_stencil, width = 2 * m + 1;
+    return stencil_row_d(P, cs, pi, cx, cy, cz, row % width - m, row / width - m, m, oy, oz, eps, rtrim2, g);
+}
+
 // Fold a coordinate back into [0, L) after a move of less than one box.
 __device__ __forceinline__ float wrap_coord(float x, float L)
 {
@@ -266,6 +275,18 @@ __device__ __forceinline__ float3 predict_pos(const RepParams &P, float4 p, floa
             if (r[c] < P.wall_lo) { r[c] = __fsub_rn(2.0f * P.wall_lo, r[c]); flip = true; }
             else if (r[c] > P.wall_hi) { r[c] = __fsub_rn(2.0f * P.wall_hi, r[c]); flip = true; }
             if (!(r[c] >= 0.0f && r[c] < P.L[c])) r[c] = fminf(fmaxf(r[c], 0.0f), P.L[c] * 0.99999994f);
+        }
+    }
+    if (P.cyl_R > 0.0f) {
+        // bounce-back at the cylinder: a point at distance d > R from the
+        // axis goes to distance 2R - d on the same radial line
+        const float dy = __fsub_rn(r[1], P.cyl_c[0]), dz = __fsub_rn(r[2], P.cyl_c[1]);
+        const float d = __fsqrt_rn(__fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
+        if (d > P.cyl_R) {
+            const float s = __fdiv_rn(__fsub_rn(__fmul_rn(2.0f, P.cyl_R), d), d);
+            r[1] = __fadd_rn(P.cyl_c[0], __fmul_rn(dy, s));
+            r[2] = __fadd_rn(P.cyl_c[1], __fmul_rn(dz, s));
+            flip = true;
         }
     }
     return make_float3(r[0], r[1], r[2]);

@@ -45,6 +45,7 @@ struct HostRep {
     float skin = 0.0f;     // neighbour-list skin of this replica (0: cell mode)
     float qr_ms = 0.0f, qr_rho = 0.0f;   // random flux (Eq. 7-8); m_s = 0: off
     int fbody_flip = 0;                  // double Poiseuille forcing
+    float cyl_R = 0.0f;                  // bounce-back cylinder radius (0: none)
 };
 
 struct Topo {
@@ -333,6 +334,9 @@ RepParams make_params(const HostRep &R, int cell_base, int pbase, int n)
     P.m_lagged = m.lagged_av != 0;
     P.qr_coef = R.qr_ms > 0.0f ? (float)((double)R.qr_ms * std::sqrt((double)R.qr_rho)) : 0.0f;
     P.fbody_flip = R.fbody_flip;
+    P.cyl_R = R.cyl_R;
+    P.cyl_c[0] = 0.5f * R.cfg.L[1];
+    P.cyl_c[1] = 0.5f * R.cfg.L[2];
     return P;
 }
 
@@ -439,6 +443,8 @@ ListArgs list_args(tdpd_sys *s, const Buffers &b, const uint32_t *rb, int cap)
     l.pos = b.pos; l.vel = b.vel; l.reps = s->d_reps; l.cell_start = s->cell_start; l.rb = rb;
     l.n_rep = (int)s->reps.size();
     l.nl = s->nl; l.nlc = s->nlc; l.xb = s->xb; l.err = s->errw; l.n = s->N; l.lpp = s->lpp; l.cap = cap;
+    l.m2 = 1;
+    for (const HostRep &R : s->reps) l.m2 = l.m2 && R.m == 2;
     return l;
 }
 
@@ -1146,6 +1152,18 @@ tdpd_status tdpd_set_body_force_profile(tdpd_sys *s, int mode)
     if (s->committed || s->reps.size() != 1) return fail(s, TDPD_ESTATE, "parameters are fixed after commit or batching");
     if (mode != 0 && mode != 1) return fail(s, TDPD_EINVAL, "body force profile must be 0 or 1");
     s->reps[0].fbody_flip = mode;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_cylinder_wall(tdpd_sys *s, float radius)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed || s->reps.size() != 1) return fail(s, TDPD_ESTATE, "parameters are fixed after commit or batching");
+    const tdpd_config &c = s->reps[0].cfg;
+    if (!(radius >= 0.0f) || !std::isfinite(radius)) return fail(s, TDPD_EINVAL, "cylinder radius must be finite and >= 0");
+    if (radius > 0.0f && (!c.periodic[1] || !c.periodic[2] || !(2.0f * radius < std::min(c.L[1], c.L[2]))))
+        return fail(s, TDPD_EINVAL, "cylinder wall needs periodic y and z and a diameter below min(L_y, L_z)");
+    s->reps[0].cyl_R = radius;
     return TDPD_OK;
 }
 

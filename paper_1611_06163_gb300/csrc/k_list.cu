@@ -13,6 +13,8 @@
 //
 // Layout: entry k of lane l of warp w at nl[(w * cap + k) * 32 + l], so the
 // 32 lanes of a warp read one 128-byte line per entry.
+#include <type_traits>
+
 #include "launch.h"
 
 namespace tdpd {
@@ -63,7 +65,9 @@ __global__ void k_bin_next(Buffers b, const RepParams *__restrict__ reps, int n,
     add_tile_count(tile_sum, c);
 }
 
-template <int LPP>
+// One thread per pair lane. M: the stencil half-width when it is known at
+// compile time (2, the default cell size), else 0 (read per replica).
+template <int LPP, int M>
 __global__ void __launch_bounds__(128) k_list_build(ListArgs A)
 {
     pdl_enter();
@@ -75,7 +79,7 @@ __global__ void __launch_bounds__(128) k_list_build(ListArgs A)
     const int rep = wbits(A.vel[i].w);
     if (!A.rb[rep]) return;
     const RepParams &P = A.reps[rep];
-    const int m = P.m_stencil, width = 2 * m + 1, nrow = width * width;
+    const int m = M > 0 ? M : P.m_stencil, width = 2 * m + 1, nrow = width * width;
     const int cx = cell_coord(pi.x, P.cell_scale[0], P.nc[0]);
     const int cy = cell_coord(pi.y, P.cell_scale[1], P.nc[1]);
     const int cz = cell_coord(pi.z, P.cell_scale[2], P.nc[2]);
@@ -85,17 +89,16 @@ __global__ void __launch_bounds__(128) k_list_build(ListArgs A)
     int *out = A.nl + (size_t)(gt >> 5) * A.cap * 32 + (gt & 31);   // next entry
     const int cap = A.cap;
     int c = 0;
-    for (int row = sub; row < nrow; row += LPP) {
-        RowSeg g = {{0, 0}, {0, 0}, 0.f, 0.f, 0.f};
-        if (!stencil_row(P, A.cell_start, pi, cx, cy, cz, row, oy, oz, eps, rl2 * 1.0002f, g)) continue;
+    // the row's candidates, four per trip with their loads in flight together,
+    // appended in slot order (the capacity test once per trip while four more
+    // entries fit); SELF: the home row, which holds particle i itself
+    auto walk = [&](const RowSeg &g, auto self) {
+        constexpr bool SELF = decltype(self)::value;
         const float py = pi.y + g.sy, pz = pi.z + g.sz;
 #pragma unroll
         for (int sg = 0; sg < 2; ++sg) {
             const float px = pi.x + (sg ? g.sx1 : 0.f);
             const int je = g.je[sg];
-            // four candidates per trip, their loads in flight together;
-            // appended in slot order (the capacity test once per trip while
-            // four more entries fit)
             for (int j0 = g.jb[sg]; j0 < je; j0 += 4) {
                 float4 pj[4];
 #pragma unroll
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(128) k_list_build(ListArgs A)
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const float dx = px - pj[u].x, dy = py - pj[u].y, dz = pz - pj[u].z;
-                    ok[u] = j0 + u != i && dx * dx + dy * dy + dz * dz < rl2;
+                    ok[u] = dx * dx + dy * dy + dz * dz < rl2 && (!SELF || j0 + u != i);
                 }
                 if (c + 4 <= cap) {
 #pragma unroll
@@ -127,6 +130,13 @@ __global__ void __launch_bounds__(128) k_list_build(ListArgs A)
                 }
             }
         }
+    };
+    for (int row = sub; row < nrow; row += LPP) {
+        const int dy = row % width - m, dz = row / width - m;
+        RowSeg g = {{0, 0}, {0, 0}, 0.f, 0.f, 0.f};
+        if (!stencil_row_d(P, A.cell_start, pi, cx, cy, cz, dy, dz, m, oy, oz, eps, rl2 * 1.0002f, g)) continue;
+        if (dy == 0 && dz == 0) walk(g, std::true_type{});
+        else walk(g, std::false_type{});
     }
     A.nlc[gt] = A.cap > 0 ? min(c, A.cap) : c;
     if (A.cap > 0 && c > A.cap) atomicOr(A.err + rep, 2u);
@@ -150,13 +160,24 @@ void launch_list_build(const ListArgs &a, cudaStream_t st)
 {
     if (a.n <= 0) return;
     const int g = (int)(((long)a.n * a.lpp + 127) / 128);
+    if (a.m2) {
+        switch (a.lpp) {
+        case 1: launch_pdl(k_list_build<1, 2>, g, 128, st, a); break;
+        case 2: launch_pdl(k_list_build<2, 2>, g, 128, st, a); break;
+        case 4: launch_pdl(k_list_build<4, 2>, g, 128, st, a); break;
+        case 8: launch_pdl(k_list_build<8, 2>, g, 128, st, a); break;
+        case 16: launch_pdl(k_list_build<16, 2>, g, 128, st, a); break;
+        default: launch_pdl(k_list_build<32, 2>, g, 128, st, a); break;
+        }
+        return;
+    }
     switch (a.lpp) {
-    case 1: launch_pdl(k_list_build<1>, g, 128, st, a); break;
-    case 2: launch_pdl(k_list_build<2>, g, 128, st, a); break;
-    case 4: launch_pdl(k_list_build<4>, g, 128, st, a); break;
-    case 8: launch_pdl(k_list_build<8>, g, 128, st, a); break;
-    case 16: launch_pdl(k_list_build<16>, g, 128, st, a); break;
-    default: launch_pdl(k_list_build<32>, g, 128, st, a); break;
+    case 1: launch_pdl(k_list_build<1, 0>, g, 128, st, a); break;
+    case 2: launch_pdl(k_list_build<2, 0>, g, 128, st, a); break;
+    case 4: launch_pdl(k_list_build<4, 0>, g, 128, st, a); break;
+    case 8: launch_pdl(k_list_build<8, 0>, g, 128, st, a); break;
+    case 16: launch_pdl(k_list_build<16, 0>, g, 128, st, a); break;
+    default: launch_pdl(k_list_build<32, 0>, g, 128, st, a); break;
     }
 }
 

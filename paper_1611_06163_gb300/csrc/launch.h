@@ -71,6 +71,7 @@ struct ListArgs {
     float4 *xb;
     uint32_t *err;
     int n, lpp, cap;             // cap == 0: count only
+    int m2;                      // every replica has the stencil half-width 2
 };
 
 struct MemArgs {

@@ -393,3 +393,31 @@ def test_ten_species_and_random_flux_match_oracle():
         assert v < TOL_TRAJ, (k, v, err)
     ob = o.observables()
     assert np.allclose(obs['mass'], ob['mass'], rtol=1e-6)
+
+
+def test_cylinder_wall_matches_oracle():
+    """The Dirichlet cylinder of Sec. 4.1 at small size (R = 3, 1582
+    particles): frozen reservoir shell at C = 1, bounce-back at the cylinder.
+    Forces at step 0 and 10 steps against the oracle; after 200 steps on the
+    device the fluid is inside R and the shell still holds C = 1."""
+    d = W.cylinder_diffusion(R=3.0, Lx=6.0, seed=33)
+    F, Q, Fo, Qo = forces_vs_oracle(d)
+    assert normwise(F, Fo) < TOL_FORCE and normwise(Q, Qo) < TOL_FORCE
+    err, obs, o, _ = run_vs_oracle(d, 10)
+    for k, v in err.items():
+        assert v < TOL_TRAJ, (k, v, err)
+    bd = B()
+    h = bd.create_from(d)
+    bd.tdpd_commit(h)
+    bd.tdpd_step(h, 200)
+    x, v, c = bd.tdpd_read_state(h, 0, 1)
+    st = bd.tdpd_replica_status(h)
+    bd.tdpd_destroy(h)
+    assert (st == 0).all()
+    wall = d['particles']['type'] == W.WALL
+    cy = 0.5 * float(d['L'][1])
+    rad = np.hypot(x[:, 1].astype(np.float64) - cy, x[:, 2].astype(np.float64) - cy)
+    assert rad[~wall].max() <= 3.0 * (1 + 1e-6)
+    assert np.array_equal(x[wall], d['particles']['pos'][wall])
+    assert np.all(c[wall] == 1.0)
+    assert 0.0 < c[~wall].mean() < 1.0

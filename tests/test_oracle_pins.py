@@ -561,3 +561,52 @@ def test_membrane_relaxes_to_its_area_and_volume_targets():
     _, AV = o.membrane_forces(parts=0)
     assert abs(AV[0, 0] - A0[0]) / A0[0] < 1e-3
     assert abs(AV[0, 1] - V0[0]) / V0[0] < 1e-3
+
+
+def test_cylinder_wall_reflects_radially():
+    """Bounce-back at the cylinder of the transport validation (Sec. 4.1,
+    Eq. 17): a free particle whose predicted position lies outside radius R
+    of the axis lands on the same radial line at distance 2R - d, with x
+    untouched and its velocity reversed; one that stays inside moves freely."""
+    L, R = 10.0, 3.0
+    r0 = np.array([[2.0, 7.0, 7.0], [4.0, 5.0, 6.0]])        # radial 2.83 and 1.0
+    v0 = np.array([[0.5, 20.0, 20.0], [1.0, 2.0, -3.0]])
+    d = custom(r0, v0, L=(L, L, L), a=0.0, gamma=0.0, sigma=0.0, kappa=0.0)
+    d['cylinder_radius'] = np.float32(R)
+    o = oracle.Oracle(d, mode=0)
+    p32 = d['particles']['pos'].astype(np.float64)
+    v32 = d['particles']['vel'].astype(np.float64)
+    dt = float(np.float32(0.01))
+    o.run(1)
+    pred = p32 + dt * v32
+    c = np.array([L / 2, L / 2])
+    # particle 0 crossed the surface
+    u = pred[0, 1:] - c
+    dist = math.hypot(*u)
+    assert dist > R
+    w = o.pos[0, 1:] - c
+    assert math.hypot(*w) == pytest.approx(2 * R - dist, abs=1e-12)
+    assert w[0] * u[1] - w[1] * u[0] == pytest.approx(0.0, abs=1e-12)   # same radial line
+    assert np.dot(w, u) > 0
+    assert o.pos[0, 0] == pytest.approx(pred[0, 0], abs=1e-12)
+    assert np.allclose(o.vel[0], -v32[0], atol=1e-12)
+    # particle 1 stayed inside
+    assert np.allclose(o.pos[1], pred[1], atol=1e-12)
+    assert np.allclose(o.vel[1], v32[1], atol=1e-12)
+
+
+def test_cylinder_keeps_fluid_inside_and_reservoir_fixed():
+    """The small cylinder workload on the oracle: after 20 steps every fluid
+    particle is within R of the axis, the frozen shell has not moved and still
+    holds the boundary concentration, and solute has entered the fluid."""
+    d = W.cylinder_diffusion(R=3.0, Lx=6.0, seed=31)
+    p = d['particles']
+    wall = p['type'] == W.WALL
+    o = oracle.Oracle(d, mode=1)
+    o.run(20)
+    c = 0.5 * d['L'].astype(np.float64)
+    rad = np.hypot(o.pos[:, 1] - c[1], o.pos[:, 2] - c[2])
+    assert rad[~wall].max() <= 3.0 + 1e-12
+    assert np.array_equal(o.pos[wall], p['pos'][wall].astype(np.float64))
+    assert np.all(o.conc[wall] == 1.0)
+    assert o.conc[~wall].sum() > 0.0

@@ -121,6 +121,55 @@ def double_poiseuille(L=40.0, rho=4.0, f=0.02, seed=1005, Lxy=None):
     return d
 
 
+def _annulus(rng, n, r0, r1, L, cy, cz):
+    """n points uniform in the shell r0 <= distance from the axis < r1 of a
+    cylinder along x (length L)."""
+    rad = np.sqrt(r0 * r0 + rng.random(n) * (r1 * r1 - r0 * r0))
+    th = rng.random(n) * 2.0 * math.pi
+    pos = np.empty((n, 3))
+    pos[:, 0] = rng.random(n) * L
+    pos[:, 1] = cy + rad * np.cos(th)
+    pos[:, 2] = cz + rad * np.sin(th)
+    return pos
+
+
+def cylinder_diffusion(R=20.0, Lx=80.0, rho=4.0, kappa=5.0, c0=0.0, cd=1.0, seed=1006):
+    """The transport validation setup of Sec. 4.1 (Eq. 17): tDPD fluid filling
+    a cylinder of radius R along x (R = 20 and length 80 at rho = 4: about
+    402,000 particles), a = 18.75, gamma = 4.5, r_c = r_cc = 1.58, w_R
+    exponent s = 0.41, flux exponent 2, kappa = 5. The fluid starts at
+    concentration c0; frozen wall particles (type WALL) at the same density
+    fill the shell R <= distance < R + r_cc and hold the boundary
+    concentration cd (the paper's effective boundary method is not stated;
+    a frozen reservoir in contact over the flux cut-off stands in for it).
+    Fluid particles are reflected at the cylinder surface. The box is
+    Lx x W x W with W = 2 (R + r_cc) + 1, periodic."""
+    rng = _rng(seed)
+    rcc = 1.58
+    W = float(math.ceil(2.0 * (R + rcc) + 1.0))
+    d = _base('cylinder_diffusion', (Lx, W, W), (1, 1, 1), 3, 1, seed, rho, rc=1.58, s_f=0.41)
+    d['a'][:] = 18.75
+    d['kappa'][:] = np.float32(kappa)
+    d['frozen_types'] = 1 << WALL
+    n_f = int(round(rho * math.pi * R * R * Lx))
+    n_w = int(round(rho * math.pi * ((R + rcc) ** 2 - R * R) * Lx))
+    c = 0.5 * W
+    pf = _annulus(rng, n_f, 0.0, R, Lx, c, c)
+    pw = _annulus(rng, n_w, R, R + rcc, Lx, c, c)
+    pos = np.concatenate([pf, pw]).astype(np.float32)
+    # keep the fluid strictly inside R after rounding to float32
+    r32 = np.sqrt((pos[:n_f, 1].astype(np.float64) - c) ** 2 + (pos[:n_f, 2].astype(np.float64) - c) ** 2)
+    pos[np.flatnonzero(r32 > R * (1 - 1e-6)), 1:] = np.float32(c)
+    vel = np.zeros((n_f + n_w, 3))
+    vel[:n_f] = rng.normal(0.0, 1.0, (n_f, 3))
+    vel[:n_f] -= vel[:n_f].mean(axis=0)
+    conc = np.concatenate([np.full((n_f, 1), c0), np.full((n_w, 1), cd)]).astype(np.float32)
+    typ = np.concatenate([np.full(n_f, SOLVENT), np.full(n_w, WALL)]).astype(np.int32)
+    d['particles'] = dict(pos=pos, vel=vel.astype(np.float32), conc=conc, type=typ)
+    d['cylinder_radius'] = np.float32(R)
+    return d
+
+
 def place_rbc(mesh_verts, mesh_tri, center, L, rng, kT=1.0, n_species=1, c_value=1.0,
               rest=None):
     """One membrane: vertices translated to ``center`` and wrapped into the box."""
