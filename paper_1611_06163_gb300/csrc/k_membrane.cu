@@ -160,7 +160,9 @@ __device__ __forceinline__ Dihedral dihedral(float3 xa, float3 xb, float3 xc, fl
     return D;
 }
 
-__global__ void __launch_bounds__(256) k_mem_forces(MemArgs A)
+// Four CTAs per SM (64 registers, a few spilled to L1): faster than two or
+// three on the ensemble of many membranes.
+__global__ void __launch_bounds__(256, 4) k_mem_forces(MemArgs A)
 {
     pdl_enter();
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) A.mem_ctr[1 - A.q] = A.mem_ctr[A.q] + 1u;
