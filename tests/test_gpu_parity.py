@@ -421,3 +421,31 @@ def test_cylinder_wall_matches_oracle():
     assert np.array_equal(x[wall], d['particles']['pos'][wall])
     assert np.all(c[wall] == 1.0)
     assert 0.0 < c[~wall].mean() < 1.0
+
+
+def test_cylinder_wall_rejects_bad_radius():
+    """tdpd_set_cylinder_wall: a negative or non-finite radius, a diameter not
+    below the box's y and z edges, or a non-periodic z axis give EINVAL;
+    after commit the call gives ESTATE."""
+    bd = B()
+    d = W.fluid_box(L=10.0)
+    h = bd.tdpd_create(bd.config_from(d))
+    for r in (-1.0, float('nan'), float('inf'), 5.0):
+        with pytest.raises(bd.TdpdError) as e:
+            bd.tdpd_set_cylinder_wall(h, r)
+        assert e.value.status == 1, r
+    bd.tdpd_set_cylinder_wall(h, 4.9)
+    bd.tdpd_set_cylinder_wall(h, 0.0)
+    bd.tdpd_destroy(h)
+    c = W.rbc_channel()
+    h = bd.tdpd_create(bd.config_from(c))
+    with pytest.raises(bd.TdpdError) as e:
+        bd.tdpd_set_cylinder_wall(h, 3.0)
+    assert e.value.status == 1
+    bd.tdpd_destroy(h)
+    h = bd.create_from(W.cylinder_diffusion(R=3.0, Lx=6.0))
+    bd.tdpd_commit(h)
+    with pytest.raises(bd.TdpdError) as e:
+        bd.tdpd_set_cylinder_wall(h, 2.0)
+    assert e.value.status == 7
+    bd.tdpd_destroy(h)
