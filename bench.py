@@ -334,10 +334,11 @@ def run_native(args):
                     'bytes_per_particle': bytes_pp},
             'kernel_ms': {nm: float(m) for nm, m in zip(names, mean_k)}}
 
-    # end to end through the public API: host state in (pinned), one step,
-    # observables out
-    pos, vel, conc = bd.tdpd_read_state(h, 0, ns)
-    n0 = W.n_mobile(descs[0])
+    # end to end through the public API: every replica's state in from pinned
+    # host memory (tdpd_set_states: one upload for the whole batch), one step,
+    # the first replica's observables out
+    st_all = [bd.tdpd_read_state(h, r, ns) for r in range(len(descs))]
+    pos, vel, conc = (np.concatenate([x[k] for x in st_all]) for k in range(3))
     hp = torch.from_numpy(pos).pin_memory()
     hv = torch.from_numpy(vel).pin_memory()
     hc = torch.from_numpy(conc).pin_memory()
@@ -345,15 +346,15 @@ def run_native(args):
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        bd.tdpd_set_state(h, 0, hp.numpy(), hv.numpy(), hc.numpy())
+        bd.tdpd_set_states(h, hp.numpy(), hv.numpy(), hc.numpy())
         bd.tdpd_step(h, 1)
         bd.tdpd_read_observables(h, 0)
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e = {'value': world * n0 * e2e_steps / e2e_s, 'unit': UNIT,
+    e2e = {'value': world * n * e2e_steps / e2e_s, 'unit': UNIT,
            'h2d_bytes_per_step': int(pos.nbytes + vel.nbytes + conc.nbytes),
            'd2h_bytes_per_step': 8 * (6 + 2 * bd.MAX_SPECIES),   # the binary64 totals tdpd_read_observables copies
-           'path': 'tdpd_set_state (pinned host) + tdpd_step(1) + tdpd_read_observables'}
+           'path': 'tdpd_set_states (pinned host, every replica) + tdpd_step(1) + tdpd_read_observables'}
 
     # batched vs plain: the same replicas advanced one after another, each by
     # its own handle, against the batch (both back to back on one stream)

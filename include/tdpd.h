@@ -237,6 +237,15 @@ tdpd_status tdpd_sync(tdpd_sys *s);
 tdpd_status tdpd_set_state(tdpd_sys *s, int replica, const float *pos, const float *vel,
                            const float *conc);
 
+/* Replace the state of every replica at once and recompute F, Q at the
+ * current step: pos[3 N], vel[3 N], conc[N ns] hold the replicas one after
+ * another in replica order, each in its load order (N = the total particle
+ * count; the layout tdpd_read_state gives replica by replica). The arrays go
+ * to the device as they are (by DMA when pinned) and are read before the call
+ * returns. TDPD_EINVAL for a null array, a position outside its replica's box
+ * or a non-finite velocity (nothing is changed then). */
+tdpd_status tdpd_set_states(tdpd_sys *s, const float *pos, const float *vel, const float *conc);
+
 /* ------------------------------------------------------------------ read */
 
 tdpd_status tdpd_read_state(tdpd_sys *s, int replica, float *pos, float *vel, float *conc);

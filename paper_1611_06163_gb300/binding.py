@@ -79,6 +79,7 @@ def _load():
         'tdpd_step': ([P, I], I),
         'tdpd_sync': ([P], I),
         'tdpd_set_state': ([P, I, P, P, P], I),
+        'tdpd_set_states': ([P, P, P, P], I),
         'tdpd_read_state': ([P, I, P, P, P], I),
         'tdpd_read_forces': ([P, I, P, P], I),
         'tdpd_read_observables': ([P, I, C.POINTER(tdpd_obs)], I),
@@ -244,6 +245,13 @@ def tdpd_set_state(h, replica, pos, vel, conc=None):
     pos, vel = _f32(pos), _f32(vel)
     conc = None if conc is None else _f32(conc)
     _chk(h, lib.tdpd_set_state(h, replica, _ptr(pos), _ptr(vel), _ptr(conc)))
+
+
+def tdpd_set_states(h, pos, vel, conc):
+    """Every replica's state at once: arrays of all replicas one after
+    another in replica order, each in its load order."""
+    pos, vel, conc = _f32(pos), _f32(vel), _f32(conc)
+    _chk(h, lib.tdpd_set_states(h, _ptr(pos), _ptr(vel), _ptr(conc)))
 
 
 def tdpd_num_particles(h, replica=0):

@@ -1393,6 +1393,35 @@ tdpd_status tdpd_sync(tdpd_sys *s)
     return TDPD_OK;
 }
 
+tdpd_status tdpd_set_states(tdpd_sys *s, const float *pos, const float *vel, const float *conc)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    if (!pos || !vel || !conc) return fail(s, TDPD_EINVAL, "null array");
+    const int N = s->N, ns = s->ns;
+    for (size_t r = 0; r < s->reps.size(); ++r) {
+        const HostRep &R = s->reps[r];
+        const float L0 = R.cfg.L[0], L1 = R.cfg.L[1], L2 = R.cfg.L[2];
+        const int b = s->rep_pbase[r], n = (int)R.type.size();
+        for (int i = b; i < b + n; ++i) {
+            const float *x = pos + 3 * (size_t)i, *v = vel + 3 * (size_t)i;
+            const bool ok = x[0] >= 0.0f && x[0] < L0 && x[1] >= 0.0f && x[1] < L1 && x[2] >= 0.0f && x[2] < L2 &&
+                            std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+            if (!ok) return fail(s, TDPD_EINVAL, "replica %zu particle %d: position outside the box or non-finite velocity", r, i - b);
+        }
+    }
+    CU(cudaEventSynchronize(s->stage_done));
+    for (int b = 0; b < s->n_rbc; ++b)
+        stage_ref(s)[b] = s->h_ref[b] = membrane_ref(s, b, pos + 3 * (size_t)s->rep_pbase[s->h_rbcs[b].rep]);
+    cudaStream_t st = exec_stream(s);
+    CU(cudaMemcpyAsync(s->d_in, pos, sizeof(float) * 3 * (size_t)N, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(s->d_in + 3 * (size_t)N, vel, sizeof(float) * 3 * (size_t)N, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(s->d_in + 6 * (size_t)N, conc, sizeof(float) * (size_t)N * ns, cudaMemcpyHostToDevice, st));
+    if ((rc = init_device(s, false))) return rc;
+    CU(cudaEventSynchronize(s->stage_done));         // the caller's arrays are read
+    return TDPD_OK;
+}
+
 tdpd_status tdpd_set_state(tdpd_sys *s, int r, const float *pos, const float *vel, const float *conc)
 {
     tdpd_status rc = ensure(s);

@@ -449,3 +449,52 @@ def test_cylinder_wall_rejects_bad_radius():
         bd.tdpd_set_cylinder_wall(h, 2.0)
     assert e.value.status == 7
     bd.tdpd_destroy(h)
+
+
+def test_set_states_loads_every_replica_at_once():
+    """tdpd_set_states (all replicas in one upload) gives the same bits as
+    loading the same states replica by replica with tdpd_set_state, then and
+    after 5 steps; an out-of-box position is refused and changes nothing."""
+    bd = B()
+    reps = W.replica_ensemble(n_rep=4, seed=79, side_lo=8, side_hi=11)
+    hs1 = [bd.create_from(r) for r in reps]
+    hs2 = [bd.create_from(r) for r in reps]
+    b1, b2 = bd.tdpd_batch_create(hs1), bd.tdpd_batch_create(hs2)
+    bd.tdpd_set_lanes(b1, 4)
+    bd.tdpd_set_lanes(b2, 4)
+    bd.tdpd_step(b1, 3)
+    bd.tdpd_step(b2, 3)                     # same step counter (it keys the random numbers)
+    states = [bd.tdpd_read_state(b1, r, 1) for r in range(len(reps))]
+    rng = np.random.default_rng(5)
+    new = []
+    for k, (x, v, c) in enumerate(states):
+        L = reps[k]['L']
+        x2 = np.mod(x + rng.uniform(-0.02, 0.02, x.shape).astype(np.float32), L).astype(np.float32)
+        x2 = np.minimum(x2, np.nextafter(L, 0).astype(np.float32))
+        new.append((x2, (v * 0.9).astype(np.float32), (c + 0.1).astype(np.float32)))
+    cat = [np.concatenate([s[k] for s in new]) for k in range(3)]
+    bd.tdpd_set_states(b1, *cat)
+    for r, (x, v, c) in enumerate(new):
+        bd.tdpd_set_state(b2, r, x, v, c)
+    for steps in (0, 5):
+        if steps:
+            bd.tdpd_step(b1, steps)
+            bd.tdpd_step(b2, steps)
+        for r in range(len(reps)):
+            a = bd.tdpd_read_state(b1, r, 1) + bd.tdpd_read_forces(b1, r, 1)
+            b = bd.tdpd_read_state(b2, r, 1) + bd.tdpd_read_forces(b2, r, 1)
+            for p, q in zip(a, b):
+                assert np.array_equal(p, q), (steps, r)
+    before = [bd.tdpd_read_state(b1, r, 1) for r in range(len(reps))]
+    bad = [c.copy() for c in cat]
+    bad[0][-1, 0] = -1.0
+    with pytest.raises(bd.TdpdError) as e:
+        bd.tdpd_set_states(b1, *bad)
+    assert e.value.status == 1
+    after = [bd.tdpd_read_state(b1, r, 1) for r in range(len(reps))]
+    for p, q in zip(before, after):
+        for u, w in zip(p, q):
+            assert np.array_equal(u, w)
+    assert (bd.tdpd_replica_status(b1) == 0).all()
+    for h in [b1, b2] + hs1 + hs2:
+        bd.tdpd_destroy(h)
