@@ -246,6 +246,21 @@ tdpd_status tdpd_set_state(tdpd_sys *s, int replica, const float *pos, const flo
  * or a non-finite velocity (nothing is changed then). */
 tdpd_status tdpd_set_states(tdpd_sys *s, const float *pos, const float *vel, const float *conc);
 
+/* Checkpoint and restart. tdpd_save writes the device state between two
+ * steps to the file path (a binary format of this library: the sorted
+ * state, predicted values, forces, fluxes, neighbour lists, binning,
+ * step and membrane counters, membrane reference points and area/volume
+ * totals, status words). tdpd_load reads it into a committed handle of the
+ * same configuration (same replicas, parameters, particle and membrane
+ * counts, skin and lane count), which then continues exactly as the saved run
+ * would have: the random numbers are keyed on the step, so a restart gives
+ * the same bits. TDPD_EINVAL: the file cannot be opened, is not a checkpoint,
+ * belongs to another configuration or is truncated (in the last case the
+ * handle must be loaded again before use). Both commit an uncommitted handle
+ * first, as tdpd_step does. */
+tdpd_status tdpd_save(tdpd_sys *s, const char *path);
+tdpd_status tdpd_load(tdpd_sys *s, const char *path);
+
 /* ------------------------------------------------------------------ read */
 
 tdpd_status tdpd_read_state(tdpd_sys *s, int replica, float *pos, float *vel, float *conc);

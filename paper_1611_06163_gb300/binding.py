@@ -80,6 +80,8 @@ def _load():
         'tdpd_sync': ([P], I),
         'tdpd_set_state': ([P, I, P, P, P], I),
         'tdpd_set_states': ([P, P, P, P], I),
+        'tdpd_save': ([P, C.c_char_p], I),
+        'tdpd_load': ([P, C.c_char_p], I),
         'tdpd_read_state': ([P, I, P, P, P], I),
         'tdpd_read_forces': ([P, I, P, P], I),
         'tdpd_read_observables': ([P, I, C.POINTER(tdpd_obs)], I),
@@ -252,6 +254,14 @@ def tdpd_set_states(h, pos, vel, conc):
     another in replica order, each in its load order."""
     pos, vel, conc = _f32(pos), _f32(vel), _f32(conc)
     _chk(h, lib.tdpd_set_states(h, _ptr(pos), _ptr(vel), _ptr(conc)))
+
+
+def tdpd_save(h, path):
+    _chk(h, lib.tdpd_save(h, os.fsencode(path)))
+
+
+def tdpd_load(h, path):
+    _chk(h, lib.tdpd_load(h, os.fsencode(path)))
 
 
 def tdpd_num_particles(h, replica=0):

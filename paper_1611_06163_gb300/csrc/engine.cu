@@ -732,6 +732,37 @@ tdpd_status capture(tdpd_sys *s, int p, int len, cudaGraphExec_t *out, cudaEvent
     return TDPD_OK;
 }
 
+// The loaded-state graph and the step graphs (both parities); graphs of an
+// earlier capture (a changed list capacity) are replaced.
+tdpd_status capture_graphs(tdpd_sys *s)
+{
+    tdpd_status rc;
+    for (int p = 0; p < 2; ++p) {
+        if (s->g1[p]) cudaGraphExecDestroy(s->g1[p]);
+        if (s->glong[p]) cudaGraphExecDestroy(s->glong[p]);
+        if (s->gtimed[p]) cudaGraphExecDestroy(s->gtimed[p]);
+        s->g1[p] = s->glong[p] = s->gtimed[p] = nullptr;
+    }
+    if (s->ginit) cudaGraphExecDestroy(s->ginit);
+    s->ginit = nullptr;
+    {
+        cudaGraph_t g;
+        CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+        enqueue_init(s, s->cap, true);
+        cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+        if (e != cudaSuccess) return fail(s, TDPD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&s->ginit, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(s, TDPD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    for (int p = 0; p < 2; ++p) {
+        if ((rc = capture(s, p, 1, &s->g1[p]))) return rc;
+        if ((rc = capture(s, p, GRAPH_LONG, &s->glong[p]))) return rc;
+        if ((rc = capture(s, p, 1, &s->gtimed[p], s->ev))) return rc;
+    }
+    return TDPD_OK;
+}
+
 tdpd_status commit(tdpd_sys *s)
 {
     if (s->committed) return TDPD_OK;
@@ -982,21 +1013,7 @@ tdpd_status commit(tdpd_sys *s)
     CU(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&s->gathered, cudaEventDisableTiming));
-    {
-        cudaGraph_t g;
-        CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-        enqueue_init(s, s->cap, true);
-        cudaError_t e = cudaStreamEndCapture(s->cap, &g);
-        if (e != cudaSuccess) return fail(s, TDPD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&s->ginit, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(s, TDPD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    }
-    for (int p = 0; p < 2; ++p) {
-        if ((rc = capture(s, p, 1, &s->g1[p]))) return rc;
-        if ((rc = capture(s, p, GRAPH_LONG, &s->glong[p]))) return rc;
-        if ((rc = capture(s, p, 1, &s->gtimed[p], s->ev))) return rc;
-    }
+    if ((rc = capture_graphs(s))) return rc;
     CU(cudaStreamSynchronize(exec_stream(s)));
     s->committed = true;
     return TDPD_OK;
@@ -1390,6 +1407,190 @@ tdpd_status tdpd_sync(tdpd_sys *s)
     for (size_t r = 0; r < st.size(); ++r)
         if (st[r] == TDPD_ENONFINITE) return fail(s, TDPD_ENONFINITE, "replica %zu produced a non-finite force", r);
         else if (st[r]) return fail(s, (tdpd_status)st[r], "replica %zu: a neighbour list overflowed", r);
+    return TDPD_OK;
+}
+
+// ------------------------------------------------------------ checkpoint
+// A checkpoint is the device state between two steps, byte for byte: the
+// current buffer (sorted state, predicted values, forces and fluxes), the
+// load-index map, the binning and list state, the step and membrane
+// counters, the membranes' load-order predicted vertices, reference points,
+// area/volume totals and constraint coefficients, and the status words. A
+// handle committed with the same configuration continues from it exactly as
+// the saved run would have (same slots, lists and random streams).
+
+struct CkpHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t N, NC, ns, n_rep, n_rbc, lpp, use_list, nl_cap, parity, n_tiles;
+    int64_t step;
+    uint64_t cfg_hash;      // the device replica and membrane tables
+    uint64_t nl_ints;       // list entries saved (list mode)
+};
+
+constexpr char CKP_MAGIC[8] = {'T', 'D', 'P', 'D', 'C', 'K', 'P', '1'};
+
+uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    for (size_t k = 0; k < n; ++k) {
+        h ^= c[k];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+tdpd_status config_hash(tdpd_sys *s, uint64_t *out)
+{
+    std::vector<RepParams> P(s->reps.size());
+    CU(cudaMemcpy(P.data(), s->d_reps, sizeof(RepParams) * P.size(), cudaMemcpyDeviceToHost));
+    uint64_t h = fnv1a(P.data(), sizeof(RepParams) * P.size());
+    if (s->n_rbc) {
+        std::vector<RbcDev> R(s->n_rbc);
+        CU(cudaMemcpy(R.data(), s->d_rbcs, sizeof(RbcDev) * R.size(), cudaMemcpyDeviceToHost));
+        h = fnv1a(R.data(), sizeof(RbcDev) * R.size(), h);
+    }
+    *out = h;
+    return TDPD_OK;
+}
+
+// (device pointer, bytes) of every saved array, in file order
+std::vector<std::pair<void *, size_t>> ckp_arrays(tdpd_sys *s, int parity, size_t nl_ints)
+{
+    const size_t N = (size_t)s->N, ns = (size_t)s->ns, nr = s->reps.size(), nb = (size_t)s->n_rbc;
+    const Buffers &B = s->buf[parity];
+    std::vector<std::pair<void *, size_t>> v = {
+        {B.pos, 16 * N}, {B.vt, 16 * N}, {B.vel, 16 * N}, {B.frc, 16 * N},
+        {B.C, 4 * N * ns}, {B.Ct, 4 * N * ns}, {B.Q, 4 * N * ns},
+        {s->inv, 4 * N}, {s->count, 4 * (size_t)s->n_tiles * SCAN_TILE},
+        {s->tile_sum[0], 4 * (size_t)s->n_tiles}, {s->tile_sum[1], 4 * (size_t)s->n_tiles},
+        {s->cellrank, 8 * N}, {s->errw, 4 * nr}, {s->step_ctr, 12}};
+    if (s->use_list) {
+        v.push_back({s->disp[0], 4 * nr});
+        v.push_back({s->disp[1], 4 * nr});
+        v.push_back({s->builds, 4 * nr});
+        v.push_back({s->nlc, 4 * N * (size_t)s->lpp});
+        v.push_back({s->xb, 16 * N});
+        v.push_back({s->nl, 4 * nl_ints});
+    }
+    if (nb) {
+        v.push_back({s->mx, 16 * N});
+        v.push_back({s->mv, 16 * N});
+        for (int k = 0; k < 2; ++k) {
+            v.push_back({s->d_ref[k], 16 * nb});
+            v.push_back({s->d_av[k], 16 * nb});
+            v.push_back({s->d_cgv[k], 8 * nb});
+        }
+    }
+    return v;
+}
+
+size_t nl_used_ints(const tdpd_sys *s)
+{
+    return s->use_list ? ((size_t)s->N * s->lpp + 31) / 32 * 32 * (size_t)s->nl_cap : 0;
+}
+
+tdpd_status tdpd_save(tdpd_sys *s, const char *path)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    if (!path) return fail(s, TDPD_EINVAL, "null path");
+    CkpHeader H{};
+    std::memcpy(H.magic, CKP_MAGIC, 8);
+    H.version = 1;
+    H.N = s->N; H.NC = s->NC; H.ns = s->ns; H.n_rep = (int)s->reps.size(); H.n_rbc = s->n_rbc;
+    H.lpp = s->lpp; H.use_list = s->use_list ? 1 : 0; H.nl_cap = s->nl_cap; H.parity = s->parity;
+    H.n_tiles = s->n_tiles; H.step = s->step;
+    H.nl_ints = nl_used_ints(s);
+    CU(cudaStreamSynchronize(exec_stream(s)));
+    if ((rc = config_hash(s, &H.cfg_hash))) return rc;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(s, TDPD_EINVAL, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&H, sizeof H, 1, f) == 1;
+    std::vector<unsigned char> host;
+    for (const auto &a : ckp_arrays(s, s->parity, H.nl_ints)) {
+        if (!ok) break;
+        host.resize(a.second);
+        cudaError_t e = cudaMemcpy(host.data(), a.first, a.second, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return fail(s, TDPD_ECUDA, "checkpoint read-back: %s", cudaGetErrorString(e));
+        }
+        ok = a.second == 0 || std::fwrite(host.data(), 1, a.second, f) == a.second;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(s, TDPD_EINVAL, "writing %s failed", path);
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_load(tdpd_sys *s, const char *path)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    if (!path) return fail(s, TDPD_EINVAL, "null path");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(s, TDPD_EINVAL, "cannot open %s", path);
+    CkpHeader H{};
+    if (std::fread(&H, sizeof H, 1, f) != 1 || std::memcmp(H.magic, CKP_MAGIC, 8) != 0 || H.version != 1) {
+        std::fclose(f);
+        return fail(s, TDPD_EINVAL, "%s is not a checkpoint of this library", path);
+    }
+    uint64_t h = 0;
+    if ((rc = config_hash(s, &h))) { std::fclose(f); return rc; }
+    if (H.N != s->N || H.NC != s->NC || H.ns != s->ns || H.n_rep != (int)s->reps.size() || H.n_rbc != s->n_rbc ||
+        H.use_list != (s->use_list ? 1 : 0) || H.n_tiles != s->n_tiles || H.cfg_hash != h) {
+        std::fclose(f);
+        return fail(s, TDPD_EINVAL, "checkpoint of another configuration (particles, cells, species, replicas, "
+                                    "membranes, list mode or parameters differ)");
+    }
+    if (H.lpp != s->lpp) {
+        std::fclose(f);
+        return fail(s, TDPD_EINVAL, "checkpoint taken with %d lanes per particle, this handle uses %d "
+                                    "(tdpd_set_lanes before commit)", H.lpp, s->lpp);
+    }
+    if (H.parity != 0 && H.parity != 1) {
+        std::fclose(f);
+        return fail(s, TDPD_EINVAL, "corrupt checkpoint header");
+    }
+    // the list layout follows the capacity of the saved run
+    const bool recapture = s->use_list && H.nl_cap != s->nl_cap;
+    if (s->use_list) {
+        const size_t need = ((size_t)s->N * s->lpp + 31) / 32 * 32 * (size_t)H.nl_cap;
+        if (H.nl_cap <= 0 || need != H.nl_ints) {
+            std::fclose(f);
+            return fail(s, TDPD_EINVAL, "corrupt checkpoint header");
+        }
+        if (need > s->nl_ints) {
+            CU(cudaStreamSynchronize(exec_stream(s)));
+            if (s->nl) CU(cudaFree(s->nl));
+            s->nl = nullptr;
+            s->nl_ints = 0;
+            cudaError_t e = cudaMalloc(&s->nl, need * sizeof(int));
+            if (e != cudaSuccess) {
+                std::fclose(f);
+                return fail(s, TDPD_ENOMEM, "neighbour lists (%zu bytes): %s", need * sizeof(int), cudaGetErrorString(e));
+            }
+            s->nl_ints = need;
+        }
+        s->nl_cap = H.nl_cap;
+    }
+    CU(cudaStreamSynchronize(exec_stream(s)));
+    std::vector<unsigned char> host;
+    bool ok = true;
+    for (const auto &a : ckp_arrays(s, H.parity, H.nl_ints)) {
+        host.resize(a.second);
+        if (a.second && std::fread(host.data(), 1, a.second, f) != a.second) { ok = false; break; }
+        cudaError_t e = cudaMemcpy(a.first, host.data(), a.second, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return fail(s, TDPD_ECUDA, "checkpoint upload: %s", cudaGetErrorString(e));
+        }
+    }
+    std::fclose(f);
+    if (!ok) return fail(s, TDPD_EINVAL, "%s is truncated; the handle's state is undefined until the next load", path);
+    s->parity = H.parity;
+    s->step = H.step;
+    if (recapture && (rc = capture_graphs(s))) return rc;
     return TDPD_OK;
 }
 

@@ -498,3 +498,88 @@ def test_set_states_loads_every_replica_at_once():
     assert (bd.tdpd_replica_status(b1) == 0).all()
     for h in [b1, b2] + hs1 + hs2:
         bd.tdpd_destroy(h)
+
+
+def _restart_bitwise(bd, make_handle, n_rep, tmp_path, name):
+    """Run 7 steps, save, run 9 more; a fresh handle loads the checkpoint and
+    runs 9: every replica's state, forces and status agree bit for bit."""
+    a = make_handle()
+    bd.tdpd_step(a, 7)
+    path = str(tmp_path / (name + '.ckp'))
+    bd.tdpd_save(a, path)
+    bd.tdpd_step(a, 9)
+    b = make_handle()
+    bd.tdpd_load(b, path)
+    assert bd.tdpd_current_step(b) == 7
+    bd.tdpd_step(b, 9)
+    for r in range(n_rep):
+        x = bd.tdpd_read_state(a, r, 1) + bd.tdpd_read_forces(a, r, 1)
+        y = bd.tdpd_read_state(b, r, 1) + bd.tdpd_read_forces(b, r, 1)
+        for p, q in zip(x, y):
+            assert np.array_equal(p, q), (name, r)
+    assert np.array_equal(bd.tdpd_replica_status(a), bd.tdpd_replica_status(b))
+    return a, b, path
+
+
+def test_checkpoint_restart_is_bitwise(tmp_path):
+    """tdpd_save / tdpd_load: a restart continues with the same bits (single
+    RBC with lists, the same in cell mode, a batch of replicas); a checkpoint
+    of another configuration, a lane-count mismatch and a file that is not a
+    checkpoint are refused."""
+    bd = B()
+    d = W.single_rbc(seed=95)
+    d['lanes'] = 4
+
+    def one():
+        h = bd.create_from(d)
+        bd.tdpd_commit(h)
+        return h
+    a, b, path = _restart_bitwise(bd, one, 1, tmp_path, 'rbc')
+    ra, _ = bd.tdpd_read_rbc(a, 0, 1)
+    rb_, _ = bd.tdpd_read_rbc(b, 0, 1)
+    assert np.array_equal(ra, rb_)
+    for h in (a, b):
+        bd.tdpd_destroy(h)
+    # another configuration: a different lane count, then a different box
+    d2 = dict(d, lanes=8)
+    h = bd.create_from(d2)
+    bd.tdpd_commit(h)
+    with pytest.raises(bd.TdpdError) as e:
+        bd.tdpd_load(h, path)
+    assert e.value.status == 1 and 'lanes' in str(e.value)
+    bd.tdpd_destroy(h)
+    h = bd.create_from(W.fluid_box(L=10.0, seed=3))
+    bd.tdpd_commit(h)
+    with pytest.raises(bd.TdpdError) as e:
+        bd.tdpd_load(h, path)
+    assert e.value.status == 1
+    junk = tmp_path / 'junk.bin'
+    junk.write_bytes(b'not a checkpoint' * 8)
+    with pytest.raises(bd.TdpdError) as e:
+        bd.tdpd_load(h, str(junk))
+    assert e.value.status == 1
+    bd.tdpd_destroy(h)
+
+    dc = dict(W.fluid_box(L=8.0, seed=97), skin=0.0, lanes=2)
+
+    def cell():
+        h = bd.create_from(dc)
+        bd.tdpd_commit(h)
+        return h
+    a, b, _ = _restart_bitwise(bd, cell, 1, tmp_path, 'cell')
+    for h in (a, b):
+        bd.tdpd_destroy(h)
+
+    reps = W.replica_ensemble(n_rep=4, seed=99, side_lo=8, side_hi=11)
+    parts = []
+
+    def batch():
+        hs = [bd.create_from(r) for r in reps]
+        parts.extend(hs)
+        bt = bd.tdpd_batch_create(hs)
+        bd.tdpd_set_lanes(bt, 4)
+        bd.tdpd_commit(bt)
+        return bt
+    a, b, _ = _restart_bitwise(bd, batch, len(reps), tmp_path, 'batch')
+    for h in [a, b] + parts:
+        bd.tdpd_destroy(h)
