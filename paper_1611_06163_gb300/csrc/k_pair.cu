@@ -30,7 +30,7 @@ namespace {
 
 constexpr int QCAP = 64;   // queue ring per warp (a push adds at most 32)
 constexpr int UNR = 2;       // candidates loaded per trip of a stencil row (cell mode)
-constexpr int UNR_LIST = 4;  // list entries loaded per trip (list mode)
+constexpr int UNR_LIST = 2;  // list entries per trip (list mode; fetched a trip ahead)
 
 struct __align__(16) QEntry {
     int j;          // partner slot
@@ -231,29 +231,42 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
         const int nit = __reduce_max_sync(0xffffffffu, cnt);
         const float Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];
         const float iLx = P.inv_L[0], iLy = P.inv_L[1], iLz = P.inv_L[2];
-        // the next trip's indices are loaded while this trip's partners are
-        // fetched, so a trip waits for one load latency, not two
-        int jn[UNR_LIST];
+        // software pipeline: a trip's partners are fetched one trip ahead
+        // and its indices two trips ahead, so the visits of a trip overlap
+        // the loads of the next one
+        int jj[UNR_LIST], jn[UNR_LIST];
+        float4 pp[UNR_LIST];
+        float cc[UNR_LIST];
 #pragma unroll
-        for (int u = 0; u < UNR_LIST; ++u) jn[u] = u < cnt ? nl[(size_t)u * 32] : 0;
-        for (int t = 0; t < nit; t += UNR_LIST) {
-            int jj[UNR_LIST];
-            float4 pp[UNR_LIST];
-            float cc[UNR_LIST];
+        for (int u = 0; u < UNR_LIST; ++u) jj[u] = u < cnt ? nl[(size_t)u * 32] : 0;
 #pragma unroll
-            for (int u = 0; u < UNR_LIST; ++u) {
-                jj[u] = jn[u];
-                jn[u] = t + UNR_LIST + u < cnt ? nl[(size_t)(t + UNR_LIST + u) * 32] : 0;
+        for (int u = 0; u < UNR_LIST; ++u) {
+            pp[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            cc[u] = 0.f;
+            if (u < cnt) {
+                pp[u] = pos[jj[u]];
+                cc[u] = Ct[(size_t)jj[u] * ns];
             }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR_LIST; ++u) jn[u] = UNR_LIST + u < cnt ? nl[(size_t)(UNR_LIST + u) * 32] : 0;
+        for (int t = 0; t < nit; t += UNR_LIST) {
+            int jq[UNR_LIST];
+            float4 pq[UNR_LIST];
+            float cq[UNR_LIST];
 #pragma unroll
             for (int u = 0; u < UNR_LIST; ++u) {
-                pp[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                cc[u] = 0.f;
-                if (t + u < cnt) {
-                    pp[u] = pos[jj[u]];
-                    cc[u] = Ct[(size_t)jj[u] * ns];
+                jq[u] = jn[u];
+                pq[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                cq[u] = 0.f;
+                if (t + UNR_LIST + u < cnt) {
+                    pq[u] = pos[jq[u]];
+                    cq[u] = Ct[(size_t)jq[u] * ns];
                 }
             }
+#pragma unroll
+            for (int u = 0; u < UNR_LIST; ++u)
+                jn[u] = t + 2 * UNR_LIST + u < cnt ? nl[(size_t)(t + 2 * UNR_LIST + u) * 32] : 0;
 #pragma unroll
             for (int u = 0; u < UNR_LIST; ++u)
                 if (u == 0 || t + u < nit) {
@@ -263,6 +276,12 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
                     dz = __fmaf_rn(-Lz, rintf(dz * iLz), dz);
                     consider(t + u < cnt, jj[u], dx, dy, dz, (uint32_t)wbits(pp[u].w), cc[u]);
                 }
+#pragma unroll
+            for (int u = 0; u < UNR_LIST; ++u) {
+                jj[u] = jq[u];
+                pp[u] = pq[u];
+                cc[u] = cq[u];
+            }
         }
     } else {
         // rows are split round-robin over the LPP lanes of the particle; the
