@@ -118,3 +118,56 @@ def test_rbc_area_and_volume_hold_at_targets_in_solvent():
     assert abs(np.mean(V) - V0[0]) / V0[0] < 1e-2
     assert np.max(np.abs(np.array(A) - A0[0])) / A0[0] < 2e-2
     assert np.max(np.abs(np.array(V) - V0[0])) / V0[0] < 2e-2
+
+
+def test_benchmark_workloads_run_their_full_length():
+    """The 512-replica ensemble and the RBC channel run 2000 steps (t = 10, the
+    configured run length): every replica stays finite, each replica's
+    temperature (relative to its mean flow) stays within 10 % of kT, solute is
+    conserved (Fickian flux is pairwise antisymmetric; the channel's reaction
+    A -> B keeps A + B), and every membrane keeps its area and volume within
+    5 % of the targets."""
+    bd = B()
+    reps = W.replica_ensemble(n_rep=512, seed=1004)
+    hs = [bd.create_from(r) for r in reps]
+    h = bd.tdpd_batch_create(hs)
+    bd.tdpd_commit(h)
+    m0 = [bd.tdpd_read_observables(h, r)['mass'].sum() for r in range(len(reps))]
+    bd.tdpd_step(h, 2000)
+    st = bd.tdpd_replica_status(h)
+    assert (st == 0).all()
+    worst_a = worst_v = 0.0
+    for r, d in enumerate(reps):
+        ob = bd.tdpd_read_observables(h, r)
+        assert ob['step'] == 2000
+        assert abs(ob['kT'] - 1.0) < 0.1, (r, ob['kT'])
+        assert abs(ob['mass'].sum() - m0[r]) <= 1e-4 * max(1.0, abs(m0[r])), r
+        nb = len(d['rbcs'])
+        if nb:
+            o = oracle.Oracle(d, mode=1)
+            _, _, A0, V0 = o.membrane_rest()
+            A, V = bd.tdpd_read_rbc(h, r, nb)
+            worst_a = max(worst_a, float(np.max(np.abs(A - A0) / A0)))
+            worst_v = max(worst_v, float(np.max(np.abs(V - V0) / V0)))
+    print('ensemble after 2000 steps: worst area %.4f, worst volume %.4f' % (worst_a, worst_v))
+    assert worst_a < 0.05 and worst_v < 0.05
+    bd.tdpd_destroy(h)
+    for x in hs:
+        bd.tdpd_destroy(x)
+
+    d = W.rbc_channel()
+    h = bd.create_from(d)
+    bd.tdpd_commit(h)
+    m0 = bd.tdpd_read_observables(h, 0)['mass'].sum()
+    bd.tdpd_step(h, 2000)
+    assert (bd.tdpd_replica_status(h) == 0).all()
+    ob = bd.tdpd_read_observables(h, 0)
+    assert abs(ob['kT'] - 1.0) < 0.1, ob['kT']
+    assert abs(ob['mass'].sum() - m0) <= 1e-4 * max(1.0, abs(m0))
+    o = oracle.Oracle(d, mode=1)
+    _, _, A0, V0 = o.membrane_rest()
+    A, V = bd.tdpd_read_rbc(h, 0, len(d['rbcs']))
+    print('channel after 2000 steps: worst area %.4f, worst volume %.4f'
+          % (np.max(np.abs(A - A0) / A0), np.max(np.abs(V - V0) / V0)))
+    assert np.max(np.abs(A - A0) / A0) < 0.05 and np.max(np.abs(V - V0) / V0) < 0.05
+    bd.tdpd_destroy(h)
