@@ -94,3 +94,39 @@ def test_training_reduces_loss_and_spread_is_member_deviation():
     assert np.allclose(spread, sd / np.abs(each.astype(np.float64).mean(0)), rtol=1e-3, atol=1e-6)
     rel = np.abs(mean - Yt) / (np.abs(Yt) + 0.1)
     assert np.median(rel) < 0.05
+
+
+def test_training_and_prediction_throughput():
+    """Timing of the surrogate's kernels at the sweep's sizes (5 members,
+    4096 training samples; 2048 candidates to rank): Adam steps per second
+    and samples per second, and the multiply-adds per second against the
+    FP32 FMA rate of 152 SMs x 128 lanes x 2 flops x the SM clock (reported;
+    the matrices are too small to fill the GPU, so the kernels are bound by
+    launch latency)."""
+    import time
+    bd = B()
+    M, n = 5, 4096
+    X, Y = _data(n, 21)
+    h = bd.tdpd_mlp_create(M)
+    bd.tdpd_mlp_set_params(h, S.init_params(3, M))
+    bd.tdpd_mlp_set_data(h, X, Y)
+    bd.tdpd_mlp_train(h, 20, 1e-3, M)                        # warm-up
+    steps = 500
+    t0 = time.perf_counter()
+    bd.tdpd_mlp_train(h, steps, 1e-3, M)
+    t_step = (time.perf_counter() - t0) / steps
+    Xc, _ = _data(2048, 22)
+    bd.tdpd_mlp_predict(h, Xc, M)
+    reps = 200
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        bd.tdpd_mlp_predict(h, Xc, M)
+    t_pred = (time.perf_counter() - t0) / reps
+    bd.tdpd_mlp_destroy(h)
+    macs = 4 * 64 + 64 * 64 + 64 * 2                          # per sample and member, forward
+    flops_step = 2 * 3 * macs * n * M                         # forward + two backward products
+    peak = 152 * 128 * 2 * 2.07e9
+    print('mlp: Adam step %.1f us (%.0f samples/s, %.2f TFLOP/s = %.2f %% of FP32 FMA peak); '
+          'predict 2048 x %d members %.1f us' % (t_step * 1e6, n / t_step, flops_step / t_step / 1e12,
+                                                 100 * flops_step / t_step / peak, M, t_pred * 1e6))
+    assert t_step < 2e-3 and t_pred < 5e-3
