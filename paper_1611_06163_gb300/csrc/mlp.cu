@@ -73,17 +73,26 @@ __global__ void __launch_bounds__(TPB) k_mlp_fwd(const float *__restrict__ param
             }
         }
         float y0 = w[OB3], y1 = w[OB3 + 1];
-        for (int o = 0; o < HID; ++o) {
-            float z = w[OB2 + o];
+        // four outputs at a time: four independent multiply-add chains
+        for (int o0 = 0; o0 < HID; o0 += 4) {
+            float z[4];
 #pragma unroll
-            for (int i = 0; i < HID; ++i) z = fmaf(w[OW2 + o * HID + i], h1[i], z);
-            const float h = gelu(z);
-            if (TRAIN) {
-                Z2[base + o] = z;
-                H2[base + o] = h;
+            for (int q = 0; q < 4; ++q) z[q] = w[OB2 + o0 + q];
+#pragma unroll
+            for (int i = 0; i < HID; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) z[q] = fmaf(w[OW2 + (o0 + q) * HID + i], h1[i], z[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int o = o0 + q;
+                const float h = gelu(z[q]);
+                if (TRAIN) {
+                    Z2[base + o] = z[q];
+                    H2[base + o] = h;
+                }
+                y0 = fmaf(w[OW3 + o], h, y0);
+                y1 = fmaf(w[OW3 + HID + o], h, y1);
             }
-            y0 = fmaf(w[OW3 + o], h, y0);
-            y1 = fmaf(w[OW3 + HID + o], h, y1);
         }
         const size_t yo = ((size_t)mbr * n + s) * OUT;
         Y[yo] = y0;
@@ -128,22 +137,30 @@ __global__ void __launch_bounds__(TPB) k_mlp_delta(const float *__restrict__ par
         d2[o] = g * gelu_grad(Z2[base + o]);
         D2[base + o] = d2[o];
     }
-    for (int i = 0; i < HID; ++i) {
-        float a = 0.0f;
+    for (int i0 = 0; i0 < HID; i0 += 4) {
+        float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int o = 0; o < HID; ++o) a = fmaf(d2[o], w[OW2 + o * HID + i], a);
-        D1[base + i] = a * gelu_grad(Z1[base + i]);
+        for (int o = 0; o < HID; ++o)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a[q] = fmaf(d2[o], w[OW2 + o * HID + i0 + q], a[q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) D1[base + i0 + q] = a[q] * gelu_grad(Z1[base + i0 + q]);
     }
 }
 
-// Gradient of one parameter per thread: a float-float compensated sum over
-// the samples, in sample order.
-__global__ void __launch_bounds__(TPB) k_mlp_grad(const float *__restrict__ X, const float *__restrict__ H1,
-                                                  const float *__restrict__ H2, const float *__restrict__ D1,
-                                                  const float *__restrict__ D2, const float *__restrict__ D3,
-                                                  int n, float *grad)
+// Gradient of one parameter per thread, in two passes: each CTA row c sums
+// the samples [c GCH, (c+1) GCH) in sample order (float-float compensated,
+// the loads of several samples in flight), then k_mlp_grad_sum adds the
+// chunks' partial sums in chunk order. The order is fixed, so the gradient
+// is deterministic.
+constexpr int GCH = 128;
+
+__global__ void __launch_bounds__(TPB) k_mlp_grad_part(const float *__restrict__ X, const float *__restrict__ H1,
+                                                       const float *__restrict__ H2, const float *__restrict__ D1,
+                                                       const float *__restrict__ D2, const float *__restrict__ D3,
+                                                       int n, float2 *part)
 {
-    const int mbr = blockIdx.y;
+    const int mbr = blockIdx.z, c = blockIdx.y;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= NP) return;
     const float *A = nullptr, *Bv = nullptr;   // gradient = sum_s A[s][ra] * Bv[s][rb] (Bv null: 1)
@@ -155,12 +172,28 @@ __global__ void __launch_bounds__(TPB) k_mlp_grad(const float *__restrict__ X, c
     else if (p < OW3) { A = D2; ra = p - OB2; }
     else if (p < OB3) { A = D3; wa = OUT; oa = (size_t)mbr * n * OUT; ra = (p - OW3) / HID; Bv = H2; rb = (p - OW3) % HID; }
     else { A = D3; wa = OUT; oa = (size_t)mbr * n * OUT; ra = p - OB3; }
+    const int s0 = c * GCH, s1 = min(n, s0 + GCH);
     FF acc{0.0f, 0.0f};
     if (Bv) {
-        for (int s = 0; s < n; ++s)
+#pragma unroll 8
+        for (int s = s0; s < s1; ++s)
             acc = ff_add(acc, A[oa + (size_t)s * wa + ra] * Bv[ob + (size_t)s * wb + rb]);
     } else {
-        for (int s = 0; s < n; ++s) acc = ff_add(acc, A[oa + (size_t)s * wa + ra]);
+#pragma unroll 8
+        for (int s = s0; s < s1; ++s) acc = ff_add(acc, A[oa + (size_t)s * wa + ra]);
+    }
+    part[((size_t)mbr * gridDim.y + c) * NP + p] = make_float2(acc.hi, acc.lo);
+}
+
+__global__ void __launch_bounds__(TPB) k_mlp_grad_sum(const float2 *__restrict__ part, int nch, float *grad)
+{
+    const int mbr = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    FF acc{0.0f, 0.0f};
+    for (int c = 0; c < nch; ++c) {
+        const float2 q = part[((size_t)mbr * nch + c) * NP + p];
+        acc = ff_add(acc, FF{q.x, q.y});
     }
     grad[(size_t)mbr * NP + p] = acc.hi + acc.lo;
 }
@@ -188,6 +221,7 @@ struct tdpd_mlp {
     float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     float *X = nullptr, *T = nullptr, *Z1 = nullptr, *H1 = nullptr, *Z2 = nullptr, *H2 = nullptr;
     float *D1 = nullptr, *D2 = nullptr, *D3 = nullptr, *Y = nullptr, *loss_part = nullptr;
+    float *gpart = nullptr;     // [members][chunks][NP] float-float partial gradients
     double mx[IN] = {}, sx[IN] = {}, my[OUT] = {}, sy[OUT] = {};
     bool have_data = false;
     cudaStream_t st = nullptr;
@@ -221,10 +255,12 @@ tdpd_status alloc_data(tdpd_mlp *m, int n)
     cudaStreamSynchronize(m->st);
     free_data(m);
     const size_t M = m->members;
-    float **bufs[] = {&m->X, &m->T, &m->Z1, &m->H1, &m->Z2, &m->H2, &m->D1, &m->D2, &m->D3, &m->Y, &m->loss_part};
+    float **bufs[] = {&m->X, &m->T, &m->Z1, &m->H1, &m->Z2, &m->H2, &m->D1, &m->D2, &m->D3, &m->Y, &m->loss_part,
+                      &m->gpart};
     const size_t sizes[] = {(size_t)n * IN, (size_t)n * OUT, M * n * HID, M * n * HID, M * n * HID, M * n * HID,
-                            M * n * HID, M * n * HID, M * n * OUT, M * n * OUT, M * ((n + TPB - 1) / TPB)};
-    for (int k = 0; k < 11; ++k) {
+                            M * n * HID, M * n * HID, M * n * OUT, M * n * OUT, M * ((n + TPB - 1) / TPB),
+                            2 * M * ((n + GCH - 1) / GCH) * NP};
+    for (int k = 0; k < 12; ++k) {
         void *p = nullptr;
         if (cudaMalloc(&p, sizes[k] * sizeof(float)) != cudaSuccess) {
             free_data(m);
@@ -243,8 +279,11 @@ tdpd_status forward_backward(tdpd_mlp *m, double *loss)
     k_mlp_fwd<true><<<gs, TPB, 0, m->st>>>(m->params, m->X, m->T, m->n, m->Z1, m->H1, m->Z2, m->H2, m->D3, m->Y,
                                            m->loss_part);
     k_mlp_delta<<<gs, TPB, 0, m->st>>>(m->params, m->Z1, m->Z2, m->D3, m->n, m->D2, m->D1);
-    k_mlp_grad<<<dim3((NP + TPB - 1) / TPB, m->members), TPB, 0, m->st>>>(m->X, m->H1, m->H2, m->D1, m->D2, m->D3,
-                                                                          m->n, m->grad);
+    const int nch = (m->n + GCH - 1) / GCH;
+    k_mlp_grad_part<<<dim3((NP + TPB - 1) / TPB, nch, m->members), TPB, 0, m->st>>>(
+        m->X, m->H1, m->H2, m->D1, m->D2, m->D3, m->n, reinterpret_cast<float2 *>(m->gpart));
+    k_mlp_grad_sum<<<dim3((NP + TPB - 1) / TPB, m->members), TPB, 0, m->st>>>(
+        reinterpret_cast<const float2 *>(m->gpart), nch, m->grad);
     MCU(cudaGetLastError());
     if (loss) {
         const int nb = (m->n + TPB - 1) / TPB;
