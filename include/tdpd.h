@@ -246,6 +246,19 @@ tdpd_status tdpd_set_state(tdpd_sys *s, int replica, const float *pos, const flo
  * or a non-finite velocity (nothing is changed then). */
 tdpd_status tdpd_set_states(tdpd_sys *s, const float *pos, const float *vel, const float *conc);
 
+/* Device-memory variants for callers whose arrays live on the GPU (a torch
+ * tensor's data pointer, say); the caller keeps ownership of its arrays.
+ * tdpd_set_states_device: as tdpd_set_states with device pointers; the
+ * check of positions and velocities runs on the device (TDPD_EINVAL, nothing
+ * changed, on a violation), membranes' reference points are taken from a
+ * host copy of the positions; returns when the arrays have been read.
+ * tdpd_read_state_device: enqueues on the library's stream (tdpd_set_stream)
+ * a copy of replica r's state in load order into pos[3 n], vel[3 n],
+ * conc[n ns] (any may be NULL) and returns at once: synchronise that stream
+ * before reading them. */
+tdpd_status tdpd_set_states_device(tdpd_sys *s, const float *pos, const float *vel, const float *conc);
+tdpd_status tdpd_read_state_device(tdpd_sys *s, int replica, float *pos, float *vel, float *conc);
+
 /* Checkpoint and restart. tdpd_save writes the device state between two
  * steps to the file path (a binary format of this library: the sorted
  * state, predicted values, forces, fluxes, neighbour lists, binning,

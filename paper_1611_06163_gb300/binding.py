@@ -80,6 +80,8 @@ def _load():
         'tdpd_sync': ([P], I),
         'tdpd_set_state': ([P, I, P, P, P], I),
         'tdpd_set_states': ([P, P, P, P], I),
+        'tdpd_set_states_device': ([P, P, P, P], I),
+        'tdpd_read_state_device': ([P, I, P, P, P], I),
         'tdpd_save': ([P, C.c_char_p], I),
         'tdpd_load': ([P, C.c_char_p], I),
         'tdpd_read_state': ([P, I, P, P, P], I),
@@ -254,6 +256,19 @@ def tdpd_set_states(h, pos, vel, conc):
     another in replica order, each in its load order."""
     pos, vel, conc = _f32(pos), _f32(vel), _f32(conc)
     _chk(h, lib.tdpd_set_states(h, _ptr(pos), _ptr(vel), _ptr(conc)))
+
+
+def tdpd_set_states_device(h, pos_ptr, vel_ptr, conc_ptr):
+    """tdpd_set_states with device pointers (integers, e.g. a CUDA
+    tensor's data_ptr())."""
+    _chk(h, lib.tdpd_set_states_device(h, C.c_void_p(pos_ptr), C.c_void_p(vel_ptr), C.c_void_p(conc_ptr)))
+
+
+def tdpd_read_state_device(h, replica, pos_ptr, vel_ptr, conc_ptr):
+    """Enqueue a load-order copy of the replica's state into device arrays
+    (integer pointers; 0 skips one) on the library's stream."""
+    _chk(h, lib.tdpd_read_state_device(h, int(replica), C.c_void_p(pos_ptr or None), C.c_void_p(vel_ptr or None),
+                                       C.c_void_p(conc_ptr or None)))
 
 
 def tdpd_save(h, path):

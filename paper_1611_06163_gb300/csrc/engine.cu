@@ -104,6 +104,7 @@ struct tdpd_sys {
     unsigned *d_obs_done = nullptr;
     float *d_in = nullptr;              // uploaded x, v, C of a loaded state (load order)
     int4 *d_wstat = nullptr;            // fixed bits of each particle (load order)
+    uint32_t *d_flag = nullptr;         // check result of a state loaded from device memory
     cudaGraphExec_t ginit = nullptr;    // forces of a loaded state
     // pinned host staging of loaded states and observables (async copies);
     // stage_done marks the end of the last copies out of it
@@ -544,13 +545,13 @@ size_t stage_bytes(int N, int ns, int n_rbc)
 
 // Reference point of membrane b (centroid of its unwrapped vertices) from the
 // load-order positions p of its replica.
-float4 membrane_ref(const tdpd_sys *s, int b, const float *p)
+// verts: the membrane's own vertices (float[3 nv])
+float4 membrane_ref_v(const tdpd_sys *s, int b, const float *verts)
 {
     const RbcDev &D = s->h_rbcs[b];
     const HostRep &R = s->reps[D.rep];
-    const int first = D.gbase - s->rep_pbase[D.rep];
     std::vector<double> x;
-    unwrap(R, s->topos[D.topo], p + 3 * (size_t)first, x);
+    unwrap(R, s->topos[D.topo], verts, x);
     double c[3] = {0, 0, 0};
     for (int v = 0; v < D.nv; ++v)
         for (int k = 0; k < 3; ++k) c[k] += x[3 * v + k];
@@ -561,6 +562,13 @@ float4 membrane_ref(const tdpd_sys *s, int b, const float *p)
         cf[k] = (float)y;
     }
     return make_float4(cf[0], cf[1], cf[2], 0.f);
+}
+
+// p: the replica's load-order positions
+float4 membrane_ref(const tdpd_sys *s, int b, const float *p)
+{
+    const RbcDev &D = s->h_rbcs[b];
+    return membrane_ref_v(s, b, p + 3 * (size_t)(D.gbase - s->rep_pbase[D.rep]));
 }
 
 // Forces of a freshly loaded state: pack the uploaded load-order arrays into
@@ -969,7 +977,7 @@ tdpd_status commit(tdpd_sys *s)
         s->h_obs = reinterpret_cast<double *>(s->h_stage);
         CU(cudaEventCreateWithFlags(&s->stage_done, cudaEventDisableTiming));
         if ((rc = dalloc(s, &s->d_obs_tot, OBS_K)) || (rc = dalloc(s, &s->d_obs_done, 1)) || (rc = dalloc(s, &s->d_in, (size_t)N * (6 + ns))) ||
-            (rc = dalloc(s, &s->d_wstat, N)))
+            (rc = dalloc(s, &s->d_wstat, N)) || (rc = dalloc(s, &s->d_flag, 1)))
             return rc;
         std::vector<int4> ws(N);
         int rb0 = 0;
@@ -1591,6 +1599,46 @@ tdpd_status tdpd_load(tdpd_sys *s, const char *path)
     s->parity = H.parity;
     s->step = H.step;
     if (recapture && (rc = capture_graphs(s))) return rc;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_set_states_device(tdpd_sys *s, const float *pos, const float *vel, const float *conc)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    if (!pos || !vel || !conc) return fail(s, TDPD_EINVAL, "null array");
+    const int N = s->N, ns = s->ns;
+    cudaStream_t st = exec_stream(s);
+    CU(cudaMemsetAsync(s->d_flag, 0, sizeof(uint32_t), st));
+    launch_check_state(pos, vel, s->d_wstat, s->d_reps, N, s->d_flag, st);
+    uint32_t bad = 0;
+    CU(cudaMemcpyAsync(&bad, s->d_flag, sizeof bad, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (bad) return fail(s, TDPD_EINVAL, "a position outside its replica's box or a non-finite velocity");
+    CU(cudaEventSynchronize(s->stage_done));
+    if (s->n_rbc) {
+        // the membranes' reference points come from their vertices (host)
+        std::vector<float> hp(3 * (size_t)N);
+        CU(cudaMemcpyAsync(hp.data(), pos, sizeof(float) * 3 * (size_t)N, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        for (int b = 0; b < s->n_rbc; ++b)
+            stage_ref(s)[b] = s->h_ref[b] = membrane_ref_v(s, b, hp.data() + 3 * (size_t)s->h_rbcs[b].gbase);
+    }
+    CU(cudaMemcpyAsync(s->d_in, pos, sizeof(float) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(s->d_in + 3 * (size_t)N, vel, sizeof(float) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(s->d_in + 6 * (size_t)N, conc, sizeof(float) * (size_t)N * ns, cudaMemcpyDeviceToDevice, st));
+    return init_device(s, false);
+}
+
+tdpd_status tdpd_read_state_device(tdpd_sys *s, int r, float *pos, float *vel, float *conc)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    HostRep *R = rep_of(s, r);
+    if (!R) return fail(s, TDPD_EINVAL, "bad replica");
+    launch_unpack_state(s->buf[s->parity], s->inv, s->rep_pbase[r], (int)R->type.size(), s->ns, pos, vel, conc,
+                        s->d_flag, exec_stream(s));
+    CU(cudaGetLastError());
     return TDPD_OK;
 }
 

@@ -257,6 +257,67 @@ __global__ void k_pack_state(const float *__restrict__ x3, const float *__restri
     }
 }
 
+// Load-order copy of slots [base, base + n) of the current buffer: entry i
+// of the output is the particle at slot inv[base + i] (a slot outside the
+// range sets *bad and is skipped).
+__global__ void k_unpack_state(Buffers b, const int *__restrict__ inv, int base, int n, int ns, float *pos,
+                               float *vel, float *conc, uint32_t *bad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = inv[base + i];
+    if (k < base || k >= base + n) {
+        atomicOr(bad, 1u);
+        return;
+    }
+    if (pos) {
+        const float4 p = b.pos[k];
+        pos[3 * (size_t)i] = p.x;
+        pos[3 * (size_t)i + 1] = p.y;
+        pos[3 * (size_t)i + 2] = p.z;
+    }
+    if (vel) {
+        const float4 v = b.vel[k];
+        vel[3 * (size_t)i] = v.x;
+        vel[3 * (size_t)i + 1] = v.y;
+        vel[3 * (size_t)i + 2] = v.z;
+    }
+    if (conc)
+        for (int sp = 0; sp < ns; ++sp) conc[(size_t)i * ns + sp] = b.C[(size_t)k * ns + sp];
+}
+
+// A loaded state's validity: every position inside its replica's box and
+// every velocity finite; a violation sets *bad.
+__global__ void k_check_state(const float *__restrict__ x3, const float *__restrict__ v3,
+                              const int4 *__restrict__ wstat, const RepParams *__restrict__ reps, int n,
+                              uint32_t *bad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const RepParams &P = reps[wstat[i].y];
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float x = x3[3 * (size_t)i + c], v = v3[3 * (size_t)i + c];
+        ok = ok && x >= 0.0f && x < P.L[c] && isfinite(v);
+    }
+    if (!ok) atomicOr(bad, 1u);
+}
+
+void launch_unpack_state(const Buffers &b, const int *inv, int base, int n, int ns, float *pos, float *vel,
+                         float *conc, uint32_t *bad, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_unpack_state<<<(n + 255) / 256, 256, 0, st>>>(b, inv, base, n, ns, pos, vel, conc, bad);
+}
+
+void launch_check_state(const float *x3, const float *v3, const int4 *wstat, const RepParams *reps, int n,
+                        uint32_t *bad, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_check_state<<<(n + 255) / 256, 256, 0, st>>>(x3, v3, wstat, reps, n, bad);
+}
+
 void launch_pack_state(const float *in, const int4 *wstat, const Buffers &b, float4 *mx, float4 *mv, int n,
                        int ns, cudaStream_t st)
 {

@@ -98,6 +98,13 @@ struct MemArgs {
 // membrane or -1, 0) per particle; membrane vertices also to mx, mv
 void launch_pack_state(const float *in, const int4 *wstat, const Buffers &b, float4 *mx, float4 *mv, int n,
                        int ns, cudaStream_t st);
+// load-order device copies of a replica's slots [base, base + n) (any of the
+// outputs may be null); *bad set if the slot map is corrupt
+void launch_unpack_state(const Buffers &b, const int *inv, int base, int n, int ns, float *pos, float *vel,
+                         float *conc, uint32_t *bad, cudaStream_t st);
+// *bad set if a position lies outside its replica's box or a velocity is not finite
+void launch_check_state(const float *x3, const float *v3, const int4 *wstat, const RepParams *reps, int n,
+                        uint32_t *bad, cudaStream_t st);
 void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum,
                      int2 *cellrank, cudaStream_t st);
 // exclusive scan of count[0, n_tiles * SCAN_TILE) into cell_start; reads the

@@ -583,3 +583,46 @@ def test_checkpoint_restart_is_bitwise(tmp_path):
     a, b, _ = _restart_bitwise(bd, batch, len(reps), tmp_path, 'batch')
     for h in [a, b] + parts:
         bd.tdpd_destroy(h)
+
+
+def test_device_pointer_state_io():
+    """tdpd_set_states_device / tdpd_read_state_device with CUDA tensors: the
+    same bits as the host calls; a position outside the box is refused on
+    the device and changes nothing."""
+    import torch
+    bd = B()
+    reps = W.replica_ensemble(n_rep=3, seed=83, side_lo=8, side_hi=10)
+    hs1 = [bd.create_from(r) for r in reps]
+    hs2 = [bd.create_from(r) for r in reps]
+    b1, b2 = bd.tdpd_batch_create(hs1), bd.tdpd_batch_create(hs2)
+    for b in (b1, b2):
+        bd.tdpd_set_lanes(b, 4)
+        bd.tdpd_step(b, 4)
+    st = [bd.tdpd_read_state(b1, r, 1) for r in range(len(reps))]
+    cat = [np.concatenate([x[k] for x in st]) for k in range(3)]
+    cat[1] = (cat[1] * 0.5).astype(np.float32)
+    dev = [torch.from_numpy(a).cuda() for a in cat]
+    torch.cuda.synchronize()
+    bd.tdpd_set_states_device(b1, *(t.data_ptr() for t in dev))
+    bd.tdpd_set_states(b2, *cat)
+    bd.tdpd_step(b1, 3)
+    bd.tdpd_step(b2, 3)
+    for r in range(len(reps)):
+        n = bd.tdpd_num_particles(b1, r)
+        out = [torch.empty((n, 3), device='cuda'), torch.empty((n, 3), device='cuda'), torch.empty((n, 1), device='cuda')]
+        bd.tdpd_read_state_device(b1, r, *(t.data_ptr() for t in out))
+        bd.tdpd_sync(b1)
+        host = bd.tdpd_read_state(b2, r, 1)
+        for t, h_ in zip(out, host):
+            assert np.array_equal(t.cpu().numpy(), h_), r
+    before = [bd.tdpd_read_state(b1, r, 1) for r in range(len(reps))]
+    dev[0][5, 1] = -0.5
+    torch.cuda.synchronize()
+    with pytest.raises(bd.TdpdError) as e:
+        bd.tdpd_set_states_device(b1, *(t.data_ptr() for t in dev))
+    assert e.value.status == 1
+    for r in range(len(reps)):
+        for u, w in zip(before[r], bd.tdpd_read_state(b1, r, 1)):
+            assert np.array_equal(u, w)
+    for h in [b1, b2] + hs1 + hs2:
+        bd.tdpd_destroy(h)
