@@ -6,8 +6,9 @@
  * red blood cell simulations with transport dissipative particle dynamics"
  * (arXiv:1611.06163), Sec. 2:
  *   - pairwise conservative, dissipative and random forces (Eq. 1-4),
- *   - Fickian concentration flux per species (Eq. 5-6; the random flux Q^R is
- *     dropped as in Sec. 2.1; Q^S is a first-order reaction A -> B),
+ *   - Fickian concentration flux per species (Eq. 5-6; the random flux Q^R
+ *     of Eq. 7-8 is off by default, as Sec. 2.1 drops it, and available
+ *     through tdpd_set_random_flux; Q^S is a first-order reaction A -> B),
  *   - membrane forces: WLC + POW bonds (Eq. 10-11), bond viscosity and random
  *     force (Eq. 12-13), global/local area and global volume constraints
  *     (Eq. 14-15), bending (Eq. 16),
@@ -27,7 +28,8 @@
  *   - A particle's id is its load-order index within its replica; the pairwise
  *     random numbers are keyed on ids (Sec. 3.1 "particle signatures").
  *   - Work is enqueued on the stream given to tdpd_set_stream (default: the
- *     library's own stream). tdpd_step does not synchronise; reads do.
+ *     library's own stream). tdpd_step does not synchronise; reads into host
+ *     memory do (tdpd_read_state_device, into device memory, does not).
  */
 #ifndef TDPD_H
 #define TDPD_H
