@@ -693,8 +693,10 @@ tdpd_status autotune(tdpd_sys *s)
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_lpp = s->lpp;
+    // the fastest of five timed launches per lane count; then the fewest
+    // lanes within 3 % of the best (they are no slower once the caches are
+    // cold, and near-equal times would otherwise flip between runs)
+    std::vector<std::pair<int, float>> t;
     for (int lpp = 1; lpp <= 32; lpp *= 2) {
         if (lpp > 1 && (long)s->N * lpp > 4000000L) break;
         s->lpp = lpp;
@@ -702,8 +704,8 @@ tdpd_status autotune(tdpd_sys *s)
         if (s->use_list && (rc = prepare_list(s))) return rc;
         const PairArgs a = pair_args(s, s->buf[1], 0, s->tile_sum[1], s->disp[1]);
         launch_pair(a, st);                       // warm-up
-        float tot = 0.f;
-        for (int k = 0; k < 3; ++k) {
+        float fastest = 1e30f;
+        for (int k = 0; k < 5; ++k) {
             cudaEventRecord(e0, st);
             launch_pair(a, st);
             cudaEventRecord(e1, st);
@@ -715,12 +717,17 @@ tdpd_status autotune(tdpd_sys *s)
                 cudaEventDestroy(e1);
                 return fail(s, TDPD_ECUDA, "autotune: %s", cudaGetErrorString(e));
             }
-            tot += ms;
+            fastest = std::min(fastest, ms);
         }
-        if (tot < best) { best = tot; best_lpp = lpp; }
+        t.push_back({lpp, fastest});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    float best = 1e30f;
+    for (const auto &x : t) best = std::min(best, x.second);
+    int best_lpp = t.empty() ? s->lpp : t.back().first;
+    for (const auto &x : t)
+        if (x.second <= 1.03f * best) { best_lpp = x.first; break; }
     s->lpp = best_lpp;
     tdpd_status rc;
     if (s->use_list && (rc = prepare_list(s))) return rc;
