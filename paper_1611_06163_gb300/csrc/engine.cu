@@ -449,11 +449,18 @@ ListArgs list_args(tdpd_sys *s, const Buffers &b, const uint32_t *rb, int cap)
     return l;
 }
 
+// Up to this many replicas every binning CTA takes the rebuild decision
+// itself (it reads each replica's maximum), saving the one-CTA decision
+// kernel's launch; more replicas keep the separate kernel.
+constexpr int DECIDE_INLINE_MAX = 16;
+bool inline_decide(const tdpd_sys *s) { return (int)s->reps.size() <= DECIDE_INLINE_MAX; }
+
 // Kernel kinds one step launches, in order (indices into KERNEL_NAMES).
 std::vector<int> step_kernels(const tdpd_sys *s)
 {
     std::vector<int> k;
-    if (s->use_list) k = {6, 7, 0, 1, 2, 8};
+    if (s->use_list && inline_decide(s)) k = {7, 0, 1, 2, 8};
+    else if (s->use_list) k = {6, 7, 0, 1, 2, 8};
     else k = {0, 1, 2};
     if (s->n_rbc) { k.push_back(3); k.push_back(4); }
     k.push_back(5);
@@ -496,10 +503,16 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         // rebuild the lists of the replicas whose particles moved more than
         // half their skin; the others keep their lists and their slots
         const uint32_t *any = s->rb + nrep;
-        launch_rebuild_decide(s->disp[p], s->disp[1 - p], s->rb, s->d_reps, nrep, 0, s->step_ctr, s->builds, st);
-        mark();
-        launch_bin_next(cur, s->d_reps, s->N, s->count, s->tile_sum[0], s->cellrank, any, st);
-        mark();
+        if (inline_decide(s)) {
+            const DecideArgs d{s->disp[p], s->disp[1 - p], s->rb, s->step_ctr, s->builds, nrep};
+            launch_bin_next(cur, s->d_reps, s->N, s->count, s->tile_sum[0], s->cellrank, any, st, d);
+            mark();
+        } else {
+            launch_rebuild_decide(s->disp[p], s->disp[1 - p], s->rb, s->d_reps, nrep, 0, s->step_ctr, s->builds, st);
+            mark();
+            launch_bin_next(cur, s->d_reps, s->N, s->count, s->tile_sum[0], s->cellrank, any, st);
+            mark();
+        }
         launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[0], s->tile_sum[1], s->step_ctr, 0, st, any);
         mark();
         launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st, any);

@@ -13,6 +13,7 @@
 //
 // Layout: entry k of lane l of warp w at nl[(w * cap + k) * 32 + l], so the
 // 32 lanes of a warp read one 128-byte line per entry.
+#include <algorithm>
 #include <type_traits>
 
 #include "launch.h"
@@ -41,11 +42,33 @@ __global__ void k_rebuild_decide(const uint32_t *__restrict__ disp, uint32_t *di
 
 // Cell and rank of the position each particle will have at the next force
 // evaluation (the predictor of the gather), for the sort of a rebuild step.
+// With D.disp set (few replicas) the rebuild decision is taken here instead
+// of in k_rebuild_decide: every CTA reads the replicas' maxima itself, and
+// CTA 0 records the decision as k_rebuild_decide would.
 __global__ void k_bin_next(Buffers b, const RepParams *__restrict__ reps, int n, int *count, int *tile_sum,
-                           int2 *cellrank, const uint32_t *any)
+                           int2 *cellrank, const uint32_t *any, DecideArgs D)
 {
     pdl_enter();
-    if (!*any) return;
+    if (D.disp) {
+        int a = 0;
+        for (int r = threadIdx.x; r < D.n_rep; r += blockDim.x) {
+            const bool rebuild = __uint_as_float(D.disp[r]) > reps[r].half_skin2;
+            a |= rebuild;
+            if (blockIdx.x == 0) {
+                D.rb[r] = rebuild ? 1u : 0u;
+                D.disp_clear[r] = 0u;
+                if (rebuild) D.builds[r] += 1u;
+            }
+        }
+        a = __syncthreads_or(a);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            D.rb[D.n_rep] = a ? 1u : 0u;
+            *D.step_ctr += 1u;
+        }
+        if (!a) return;
+    } else if (!*any) {
+        return;
+    }
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     int c = -1;
     if (k < n) {
@@ -150,10 +173,10 @@ void launch_rebuild_decide(const uint32_t *disp, uint32_t *disp_clear, uint32_t 
 }
 
 void launch_bin_next(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum, int2 *cellrank,
-                     const uint32_t *any, cudaStream_t st)
+                     const uint32_t *any, cudaStream_t st, const DecideArgs &d)
 {
-    if (n <= 0) return;
-    launch_pdl(k_bin_next, (n + 255) / 256, 256, st, b, reps, n, count, tile_sum, cellrank, any);
+    if (n <= 0 && !d.disp) return;
+    launch_pdl(k_bin_next, std::max(1, (n + 255) / 256), 256, st, b, reps, n, count, tile_sum, cellrank, any, d);
 }
 
 void launch_list_build(const ListArgs &a, cudaStream_t st)

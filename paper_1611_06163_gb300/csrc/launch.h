@@ -127,10 +127,17 @@ void launch_pair(const PairArgs &a, cudaStream_t st);
 // step counter and counts each replica's rebuilds in builds
 void launch_rebuild_decide(const uint32_t *disp, uint32_t *disp_clear, uint32_t *rb, const RepParams *reps,
                            int n_rep, int force, uint32_t *step_ctr, uint32_t *builds, cudaStream_t st);
+// the rebuild decision folded into k_bin_next (disp null: taken by
+// k_rebuild_decide before it); the fields as for launch_rebuild_decide
+struct DecideArgs {
+    const uint32_t *disp;
+    uint32_t *disp_clear, *rb, *step_ctr, *builds;
+    int n_rep;
+};
 // cell and rank of each particle's next predicted position (list mode, when
 // any replica rebuilds)
 void launch_bin_next(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum, int2 *cellrank,
-                     const uint32_t *any, cudaStream_t st);
+                     const uint32_t *any, cudaStream_t st, const DecideArgs &d = DecideArgs{});
 void launch_list_build(const ListArgs &a, cudaStream_t st);
 // pdl: launched as a programmatic dependent of the previous kernel on st
 void launch_mem_gather(const MemArgs &a, cudaStream_t st, bool pdl);
