@@ -304,7 +304,8 @@ def run_native(args):
     # per species), v, F (16 B each), C, Q (4 B per species); write v, F, C, Q;
     # plus the next binning's (cell, rank) 8 B = 112 + 16 ns bytes. With
     # neighbour lists the binning is replaced by the list entries (4 B per
-    # partner within rcut + skin) and the position at the last build (16 B).
+    # partner within rcut + skin) and the position at the last build (16 B);
+    # the lists the kernel builds on rebuild steps are counted below.
     ns = int(descs[0]['n_species'])
     n_all = sum(W.n_particles(d) for d in descs)
     vol = sum(float(np.prod(d['L'])) for d in descs)
@@ -321,6 +322,12 @@ def run_native(args):
     rcut = max(float(d0['rc']), float(d0['rcc']))
     n_list = rho * 4.0 / 3.0 * math.pi * (rcut + skin) ** 3 if skin > 0 else 0.0
     bytes_pp = 112 + 16 * ns if skin == 0 else 104 + 16 * ns + 16 + 4 * n_list
+    if skin > 0:
+        # on a rebuild step the pair kernel first builds its lanes' lists:
+        # at least one distance test (9 operations) and one 4-byte write per
+        # list entry, and the 16-byte build position, at the measured rate
+        ops_pp += rebuild_rate * 9 * n_list
+        bytes_pp += rebuild_rate * (4 * n_list + 16)
     hbm, src = peaks()
     alu_peak = 152 * 128 * sm_max_mhz() * 1e6 / 1e12
     alu = ops_pp * n_all / (pair_ms * 1e-3) / 1e12

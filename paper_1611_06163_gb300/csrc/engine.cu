@@ -421,7 +421,10 @@ MemArgs mem_args(tdpd_sys *s, int ref_in, int inc)
 }
 
 // disp_next: where list mode records the displacements of the next positions
-PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum, uint32_t *disp_next = nullptr)
+// build_rb (list mode): the replicas whose lanes build their lists inside
+// the pair kernel first (a rebuild step)
+PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum, uint32_t *disp_next = nullptr,
+                   const uint32_t *build_rb = nullptr)
 {
     PairArgs a{};
     a.tile_sum = tile_sum;
@@ -433,6 +436,12 @@ PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum, 
         if (R.qr_ms > 0.0f) a.qr = 1;
     if (s->use_list) {
         a.nl = s->nl; a.nlc = s->nlc; a.cap = s->nl_cap; a.xb = s->xb; a.disp_next = disp_next;
+        if (build_rb) {
+            a.rb = build_rb;
+            a.nl_w = s->nl; a.nlc_w = s->nlc; a.xb_w = s->xb;
+            a.m2 = 1;
+            for (const HostRep &R : s->reps) a.m2 = a.m2 && R.m == 2;
+        }
     }
     return a;
 }
@@ -459,8 +468,8 @@ bool inline_decide(const tdpd_sys *s) { return (int)s->reps.size() <= DECIDE_INL
 std::vector<int> step_kernels(const tdpd_sys *s)
 {
     std::vector<int> k;
-    if (s->use_list && inline_decide(s)) k = {7, 0, 1, 2, 8};
-    else if (s->use_list) k = {6, 7, 0, 1, 2, 8};
+    if (s->use_list && inline_decide(s)) k = {7, 0, 1, 2};
+    else if (s->use_list) k = {6, 7, 0, 1, 2};
     else k = {0, 1, 2};
     if (s->n_rbc) { k.push_back(3); k.push_back(4); }
     k.push_back(5);
@@ -520,8 +529,7 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st,
                            s->rb, nrep, s->tile_sum[0], s->n_tiles);
         mark();
-        launch_list_build(list_args(s, nxt, s->rb, s->nl_cap), st);
-        mark();
+        // the lists of rebuilding replicas: built by the pair kernel's lanes
     } else {
         launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[p], s->tile_sum[1 - p], s->step_ctr, 1, st);
         mark();
@@ -538,7 +546,7 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         mark();
     }
     if (branch) cudaStreamWaitEvent(st, s->join, 0);
-    launch_pair(pair_args(s, nxt, 1, s->tile_sum[1 - p], s->disp[1 - p]), st);
+    launch_pair(pair_args(s, nxt, 1, s->tile_sum[1 - p], s->disp[1 - p], s->use_list ? s->rb : nullptr), st);
     mark();
     if (branch && s->all_lagged) cudaStreamWaitEvent(st, s->gathered, 0);
 }

@@ -23,6 +23,7 @@
 // Every unordered pair is evaluated from both sides; the random number is
 // keyed on (min id, max id, step), so both sides draw the same xi_ij.
 #include "launch.h"
+#include "list_lane.cuh"
 
 namespace tdpd {
 
@@ -226,7 +227,17 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
     if constexpr (LIST) {
         // the lane's list, UNR_LIST entries per trip (index loads, then partner
         // loads, then the visits in list order); separations by minimum image
-        const int *__restrict__ nl = A.nl + (size_t)(gt >> 5) * A.cap * 32 + (gt & 31);
+        if (A.rb && valid && A.rb[rep]) {
+            // rebuild step: this lane's list first (the lists are only ever
+            // read by the lane that owns them, so no other thread waits)
+            ListArgs L{};
+            L.pos = pos; L.vel = A.b.vel; L.reps = A.reps; L.cell_start = A.cell_start; L.rb = A.rb;
+            L.nl = A.nl_w; L.nlc = A.nlc_w; L.xb = A.xb_w; L.err = A.err; L.n = A.n; L.lpp = LPP; L.cap = A.cap;
+            if (A.m2) build_lane<LPP, 2>(L, gt, i, sub, pi, rep);
+            else build_lane<LPP, 0>(L, gt, i, sub, pi, rep);
+        }
+        // (plain loads: on a rebuild step this thread has just written them)
+        const int *nl = A.nl + (size_t)(gt >> 5) * A.cap * 32 + (gt & 31);
         const int cnt = valid ? A.nlc[gt] : 0;
         const int nit = __reduce_max_sync(0xffffffffu, cnt);
         const float Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];

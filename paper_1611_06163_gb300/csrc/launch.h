@@ -58,6 +58,13 @@ struct PairArgs {
     int cap;                     // entries per lane
     const float4 *xb;            // [n] positions at the last list build
     uint32_t *disp_next;         // [n_rep] max squared displacement (float bits) of the next positions
+    // rebuild steps: rb (null: no build in the kernel) flags the replicas
+    // whose lanes build their own lists first (into nl_w, nlc_w, xb_w: the
+    // same arrays as nl, nlc, xb); m2: every replica has stencil half-width 2
+    const uint32_t *rb;
+    int *nl_w, *nlc_w;
+    float4 *xb_w;
+    int m2;
 };
 
 // Neighbour-list build over the cell stencil of radius sqrt(rlist2).
