@@ -42,7 +42,7 @@ UNIT = 'particle-steps/s'
 # current kernel build (summaries under profiles/), keyed by workload, skin
 # and lane count; the capture is cold-cache, the bench step follows an L2
 # flush, so the two see the same misses.
-PAIR_TRAFFIC = {('single_rbc', 0.2, 4): 12.963840e6, ('fluid_786k', 0.2, 1): 342.917888e6 + 26.148096e6}
+PAIR_TRAFFIC = {}
 
 
 def _ns10(d):
