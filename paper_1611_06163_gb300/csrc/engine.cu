@@ -464,12 +464,24 @@ ListArgs list_args(tdpd_sys *s, const Buffers &b, const uint32_t *rb, int cap)
 constexpr int DECIDE_INLINE_MAX = 16;
 bool inline_decide(const tdpd_sys *s) { return (int)s->reps.size() <= DECIDE_INLINE_MAX; }
 
+// List mode with one or two species (and no random flux): the pair kernel
+// (its one- and two-species forms) builds the lists of rebuilding replicas
+// itself; otherwise k_list_build runs before it.
+bool pair_builds_lists(const tdpd_sys *s)
+{
+    if (!s->use_list || s->ns > 2) return false;
+    for (const HostRep &R : s->reps)
+        if (R.qr_ms > 0.0f) return false;
+    return true;
+}
+
 // Kernel kinds one step launches, in order (indices into KERNEL_NAMES).
 std::vector<int> step_kernels(const tdpd_sys *s)
 {
     std::vector<int> k;
     if (s->use_list && inline_decide(s)) k = {7, 0, 1, 2};
     else if (s->use_list) k = {6, 7, 0, 1, 2};
+    if (s->use_list && !pair_builds_lists(s)) k.push_back(8);
     else k = {0, 1, 2};
     if (s->n_rbc) { k.push_back(3); k.push_back(4); }
     k.push_back(5);
@@ -529,7 +541,10 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st,
                            s->rb, nrep, s->tile_sum[0], s->n_tiles);
         mark();
-        // the lists of rebuilding replicas: built by the pair kernel's lanes
+        if (!pair_builds_lists(s)) {
+            launch_list_build(list_args(s, nxt, s->rb, s->nl_cap), st);
+            mark();
+        }
     } else {
         launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[p], s->tile_sum[1 - p], s->step_ctr, 1, st);
         mark();
@@ -546,7 +561,8 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         mark();
     }
     if (branch) cudaStreamWaitEvent(st, s->join, 0);
-    launch_pair(pair_args(s, nxt, 1, s->tile_sum[1 - p], s->disp[1 - p], s->use_list ? s->rb : nullptr), st);
+    launch_pair(pair_args(s, nxt, 1, s->tile_sum[1 - p], s->disp[1 - p], pair_builds_lists(s) ? s->rb : nullptr),
+                st);
     mark();
     if (branch && s->all_lagged) cudaStreamWaitEvent(st, s->gathered, 0);
 }

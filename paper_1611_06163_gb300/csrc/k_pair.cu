@@ -227,14 +227,18 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
     if constexpr (LIST) {
         // the lane's list, UNR_LIST entries per trip (index loads, then partner
         // loads, then the visits in list order); separations by minimum image
-        if (A.rb && valid && A.rb[rep]) {
+        if constexpr (NS == 1 || NS == 2) {
             // rebuild step: this lane's list first (the lists are only ever
-            // read by the lane that owns them, so no other thread waits)
-            ListArgs L{};
-            L.pos = pos; L.vel = A.b.vel; L.reps = A.reps; L.cell_start = A.cell_start; L.rb = A.rb;
-            L.nl = A.nl_w; L.nlc = A.nlc_w; L.xb = A.xb_w; L.err = A.err; L.n = A.n; L.lpp = LPP; L.cap = A.cap;
-            if (A.m2) build_lane<LPP, 2>(L, gt, i, sub, pi, rep);
-            else build_lane<LPP, 0>(L, gt, i, sub, pi, rep);
+            // read by the lane that owns them, so no other thread waits);
+            // the kernels for more species keep the separate list build
+            // (the build's registers would cost them more than the launch)
+            if (A.rb && valid && A.rb[rep]) {
+                ListArgs L{};
+                L.pos = pos; L.vel = A.b.vel; L.reps = A.reps; L.cell_start = A.cell_start; L.rb = A.rb;
+                L.nl = A.nl_w; L.nlc = A.nlc_w; L.xb = A.xb_w; L.err = A.err; L.n = A.n; L.lpp = LPP; L.cap = A.cap;
+                if (A.m2) build_lane<LPP, 2>(L, gt, i, sub, pi, rep);
+                else build_lane<LPP, 0>(L, gt, i, sub, pi, rep);
+            }
         }
         // (plain loads: on a rebuild step this thread has just written them)
         const int *nl = A.nl + (size_t)(gt >> 5) * A.cap * 32 + (gt & 31);
