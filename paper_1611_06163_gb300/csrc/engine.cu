@@ -479,10 +479,13 @@ bool pair_builds_lists(const tdpd_sys *s)
 std::vector<int> step_kernels(const tdpd_sys *s)
 {
     std::vector<int> k;
-    if (s->use_list && inline_decide(s)) k = {7, 0, 1, 2};
-    else if (s->use_list) k = {6, 7, 0, 1, 2};
-    if (s->use_list && !pair_builds_lists(s)) k.push_back(8);
-    else k = {0, 1, 2};
+    if (s->use_list) {
+        if (inline_decide(s)) k = {7, 0, 1, 2};
+        else k = {6, 7, 0, 1, 2};
+        if (!pair_builds_lists(s)) k.push_back(8);
+    } else {
+        k = {0, 1, 2};
+    }
     if (s->n_rbc) { k.push_back(3); k.push_back(4); }
     k.push_back(5);
     return k;
