@@ -497,7 +497,9 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
 {
     const Buffers &cur = s->buf[p], &nxt = s->buf[1 - p];
     int e = 0;
-    auto mark = [&]() { if (ev) cudaEventRecordWithFlags(ev[e++], st, cudaEventRecordExternal); };
+    auto mark = [&]() {
+        if (ev && e < s->n_ev) cudaEventRecordWithFlags(ev[e++], st, cudaEventRecordExternal);
+    };
     // The membrane kernels read the predicted vertices the last pair kernel
     // wrote in load order, so they need not wait for the sort: in a plain
     // step they run on a side stream beside scan, scatter and gather, and the
@@ -780,7 +782,11 @@ tdpd_status capture(tdpd_sys *s, int p, int len, cudaGraphExec_t *out, cudaEvent
     CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < len; ++k) enqueue_step(s, (p + k) & 1, s->cap, ev);
     cudaError_t e = cudaStreamEndCapture(s->cap, &g);
-    if (e != cudaSuccess) return fail(s, TDPD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    if (e == cudaSuccess) e = cudaGetLastError();   // a launch or event record refused during capture
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(s, TDPD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
     e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(s, TDPD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
