@@ -40,9 +40,10 @@ METRIC = 'tDPD particle-steps/s on 1 GB300 (% HBM roofline); batched vs plain at
 UNIT = 'particle-steps/s'
 # DRAM bytes (read + write) of one k_pair launch from one ncu capture of the
 # current kernel build (summaries under profiles/), keyed by workload, skin
-# and lane count; the capture is cold-cache, the bench step follows an L2
-# flush, so the two see the same misses.
-PAIR_TRAFFIC = {}
+# and lane count: launches with and without a list rebuild, weighted by the
+# workload's rebuild rate (0.2725, 0.5); the capture is cold-cache, the bench
+# step follows an L2 flush, so the two see the same misses.
+PAIR_TRAFFIC = {('single_rbc', 0.2, 4): 11.53886e6, ('fluid_786k', 0.2, 1): 418.1664e6}
 
 
 def _ns10(d):
