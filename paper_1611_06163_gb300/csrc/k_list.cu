@@ -13,6 +13,10 @@
 //
 // Layout: entry k of lane l of warp w at nl[(w * cap + k) * 32 + l], so the
 // 32 lanes of a warp read one 128-byte line per entry.
+//
+// k_list_build builds the lists of a loaded state; on a rebuild step the pair
+// kernel's one- and two-species forms build their own lanes' lists
+// (list_lane.cuh), and k_list_build runs only for the other forms.
 #include <algorithm>
 #include <type_traits>
 

@@ -4,7 +4,8 @@
 //     the next predicted position for the next step's sort;
 //   - list mode: over the lane's Verlet list (k_list.cu), separations by
 //     minimum image; the epilogue records how far the next position has moved
-//     from the list build instead of binning.
+//     from the list build instead of binning. On a rebuild step the one- and
+//     two-species forms first build the lane's own list (list_lane.cuh).
 //
 // Layout of the work in cell mode:
 //   - cells have edge >= rcut/m, so the partners of particle i lie in the
