@@ -26,20 +26,9 @@ import pytest
 
 import workloads as W
 from gpu_common import B
+from analytic import series, bessel_series
 
 pytestmark = pytest.mark.gpu
-
-
-def series(z, t, f, d, nu, terms=60):
-    zz = np.mod(z, 2 * d)
-    sign = np.where(zz < d, 1.0, -1.0)
-    zz = np.where(zz < d, zz, zz - d)
-    u = f * zz * (d - zz) / (2 * nu)
-    for k in range(terms):
-        n = 2 * k + 1
-        u -= 4 * f * d * d / (nu * math.pi ** 3) * np.sin(n * math.pi * zz / d) * \
-            math.exp(-n * n * math.pi ** 2 * nu * t / (d * d)) / n ** 3
-    return sign * u
 
 
 def fit_nu(z, profiles, f, d):
@@ -100,17 +89,6 @@ def test_double_poiseuille_transient_follows_stokes_series():
     early = fit_nu(zc, profiles[:2], f, half)
     late = fit_nu(zc, profiles[-2:], f, half)
     assert abs(early - late) < 0.15 * nu, (early, late, nu)
-
-
-def bessel_series(r, t, D, R, terms=80):
-    """(C - C0)/(CD - C0) of Eq. 17 for a cylinder of radius R started at C0
-    with the surface held at CD."""
-    sp = pytest.importorskip('scipy.special')
-    lam = sp.jn_zeros(0, terms) / R
-    out = np.ones_like(r, dtype=np.float64)
-    for l in lam:
-        out -= 2.0 / R * sp.j0(l * r) / (l * sp.j1(l * R)) * math.exp(-D * l * l * t)
-    return out
 
 
 def test_cylinder_dirichlet_diffusion_follows_bessel_series():
