@@ -13,7 +13,9 @@
  *  - r_ij = r_i - r_j, v_ij = v_i - v_j, e_ij = r_ij/|r_ij|; F_ij acts on i.
  *  - xi_ij from TEA (Sec. 3.1 names TEA on particle signatures) keyed on
  *    (min id, max id) with key (seed, step, stream); Box-Muller, cos branch.
- *  - Q^R is dropped (Sec. 2.1 drops it since m_s << m); Q^S is a first-order
+ *  - Q^R (Eq. 7-8) is off unless qr_ms > 0 (Sec. 2.1 drops it since
+ *    m_s << m): eps^2 = m_s^2 kappa rho (C~_i + C~_j), w_RC = w_DC^(1/2), one
+ *    pair normal per species signed by the id order; Q^S is a first-order
  *    reaction A->B on the reacting types.
  *  - Integrator: Groot-Warren modified velocity Verlet with lambda (the paper
  *    cites GW for the DPD equations but names no scheme).
@@ -26,6 +28,17 @@
  *    j, positive where the surface is convex.
  *  - Volume: sum of signed tetrahedra of each outward triangle with the origin
  *    of the membrane's unwrapped coordinates.
+ *  - Area/volume constraints from the current positions, or (lagged) from the
+ *    previous evaluation's totals (the concurrent variant of Sec. 3.3).
+ *  - Walls: bounce-back at the planes z = wall_lo, wall_hi, or at a cylinder
+ *    of radius cyl_R about the x axis through the box centre (the Dirichlet
+ *    cylinder of Eq. 17, whose boundary concentration is held by frozen
+ *    particles): position reflected, velocity reversed.
+ *
+ * Parity unpinned: the physical calibration of the membrane constants (the
+ * RBC stretching data the paper fits is not available); the forces, fluxes,
+ * integrator and reductions are pinned by the CPU tests (closed forms,
+ * gradients of energies, conservation laws, published TEA vectors).
  */
 #include "tdpd_oracle.h"
 
