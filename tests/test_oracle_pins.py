@@ -610,3 +610,112 @@ def test_cylinder_keeps_fluid_inside_and_reservoir_fixed():
     assert np.array_equal(o.pos[wall], p['pos'][wall].astype(np.float64))
     assert np.all(o.conc[wall] == 1.0)
     assert o.conc[~wall].sum() > 0.0
+
+
+def test_planar_walls_reflect_and_reverse():
+    """Bounce-back at the planar walls of the channel workload (the reading
+    of the wall treatment Sec. 4.2 cites but does not state): a particle
+    whose predicted z passes wall_hi (wall_lo) lands at 2 wall_hi - z
+    (2 wall_lo - z) with x, y as predicted and its velocity reversed before
+    the corrector adds the force; a particle that stays between the walls
+    moves freely. With no pair forces the force is the body force f, so the
+    corrector gives v' = -v + dt f after a reflection and v + dt f without."""
+    L, lo, hi = 10.0, 1.0, 9.0
+    r0 = np.array([[2.0, 3.0, 8.9], [4.0, 5.0, 1.05], [6.0, 7.0, 5.0]])
+    v0 = np.array([[0.5, -1.0, 30.0], [1.0, 2.0, -20.0], [0.3, 0.2, -0.4]])
+    f = np.array([0.05, -0.02, 0.1])
+    d = custom(r0, v0, L=(L, L, L), periodic=(1, 1, 0), a=0.0, gamma=0.0, sigma=0.0, kappa=0.0,
+               body_force=f)
+    d['wall_lo'], d['wall_hi'] = np.float32(lo), np.float32(hi)
+    o = oracle.Oracle(d, mode=0)
+    p32 = d['particles']['pos'].astype(np.float64)
+    v32 = d['particles']['vel'].astype(np.float64)
+    f32 = d['body_force'].astype(np.float64)
+    dt = float(np.float32(0.01))
+    o.run(1)
+    pred = p32 + dt * v32 + 0.5 * dt * dt * f32
+    assert pred[0, 2] > hi and pred[1, 2] < lo and lo < pred[2, 2] < hi
+    assert o.pos[0, 2] == pytest.approx(2 * hi - pred[0, 2], abs=1e-12)
+    assert o.pos[1, 2] == pytest.approx(2 * lo - pred[1, 2], abs=1e-12)
+    assert np.allclose(o.pos[:2, :2], pred[:2, :2], atol=1e-12)
+    assert np.allclose(o.vel[:2], -v32[:2] + dt * f32, atol=1e-12)
+    assert np.allclose(o.pos[2], pred[2], atol=1e-12)
+    assert np.allclose(o.vel[2], v32[2] + dt * f32, atol=1e-12)
+
+
+def _two_icosahedra(exclude=1, only_first=False):
+    """Two regular icosahedra (edge 0.8 < r_c, so the vertices of one cell
+    are inside each other's force range) whose faces come within r_c of each
+    other, with random velocities and concentrations."""
+    v, t = icosahedron(0.8)
+    rng = np.random.default_rng(17)
+    d = membrane_only(v, t, L=12.0, vel=rng.normal(0, 1, v.shape))
+    d['a'][:] = 25.0
+    d['gamma'][:] = 4.5
+    d['sigma'][:] = 3.0
+    d['kappa'][:] = 1.0
+    d['exclude_same_body'] = exclude
+    r = d['rbcs'][0]
+    r['conc'] = rng.random((12, 1)).astype(np.float32)
+    if not only_first:
+        r2 = dict(r)
+        r2['pos'] = (r['pos'].astype(np.float64) + [1.3, 0.2, 0.1]).astype(np.float32)
+        r2['vel'] = rng.normal(0, 1, v.shape).astype(np.float32)
+        r2['conc'] = rng.random((12, 1)).astype(np.float32)
+        d['rbcs'] = [r, r2]
+    return d
+
+
+def test_same_membrane_pairs_feel_no_force_but_exchange_flux():
+    """The membrane-solvent reading of Sec. 2.2: vertices of one membrane
+    exert no Eq. 3 force on each other, but exchange the Eq. 6 flux; vertices
+    of two different membranes interact fully. One cell alone: every pair
+    force is zero, the flux is not. Two cells: the force on a vertex of the
+    first equals its force with the exclusion off minus its force from its
+    own cell (the first cell alone, exclusion off, same ids and step), and
+    the flux does not depend on the exclusion."""
+    o1 = oracle.Oracle(_two_icosahedra(1, only_first=True), mode=0)
+    F1, Q1 = o1.pair_forces()
+    assert np.all(F1 == 0.0)
+    assert np.abs(Q1).max() > 1e-2
+    o1n = oracle.Oracle(_two_icosahedra(0, only_first=True), mode=0)
+    Fself, Q1n = o1n.pair_forces()
+    assert np.abs(Fself).max() > 1.0              # the same pairs do interact when not excluded
+    assert np.array_equal(Q1, Q1n)
+    oe = oracle.Oracle(_two_icosahedra(1), mode=0)
+    on = oracle.Oracle(_two_icosahedra(0), mode=0)
+    Fe, Qe = oe.pair_forces()
+    Fn, Qn = on.pair_forces()
+    assert np.abs(Fe[:12]).max() > 1.0            # cross-membrane pairs interact
+    assert np.allclose(Fe[:12], Fn[:12] - Fself, rtol=0, atol=1e-12 * np.abs(Fn).max())
+    assert np.allclose(Qe, Qn, rtol=0, atol=1e-15)
+    # the second cell: its own-cell forces are the first cell's pattern moved
+    assert np.allclose(Fe.sum(0), 0.0, atol=1e-10 * np.abs(Fe).max())
+
+
+def test_unwrap_across_periodic_faces_is_translation_invariant():
+    """Area, volume (Eq. 14-15) and every membrane force of a cell do not
+    change when the cell is translated across a periodic corner of the box so
+    that its vertices are wrapped to three faces: the oracle rebuilds the
+    cell by minimum images along its edges before summing. Without the
+    unwrap the wrapped coordinates would give a different area and volume
+    (checked by summing the triangles of the raw wrapped positions)."""
+    d = _perturbed_sphere(n=162, radius=3.0, seed=9, theta0=0.1)
+    L = float(d['L'][0])
+    rng = np.random.default_rng(2)
+    vel = rng.normal(0, 1, (162, 3))
+    o = oracle.Oracle(d, mode=1)
+    p0 = o.pos.copy()
+    F0, AV0 = o.membrane_forces(pos=p0, vel=vel, parts=15)
+    shift = np.array([L / 2 - 0.4, L / 2 + 0.3, -L / 2 + 0.2])
+    p1 = p0 + shift
+    p1 -= np.floor(p1 / L) * L
+    for c in range(3):
+        assert p1[:, c].min() < 2.0 and p1[:, c].max() > L - 2.0   # split across every axis
+    F1, AV1 = o.membrane_forces(pos=p1, vel=vel, parts=15)
+    assert np.allclose(AV1, AV0, rtol=1e-11, atol=0)
+    assert np.allclose(F1, F0, rtol=0, atol=1e-9 * np.abs(F0).max())
+    tri = d['rbcs'][0]['tri']
+    a, b, c = p1[tri[:, 0]], p1[tri[:, 1]], p1[tri[:, 2]]
+    raw_area = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1).sum()
+    assert abs(raw_area - AV0[0, 0]) > 0.1 * AV0[0, 0]
