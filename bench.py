@@ -1,9 +1,13 @@
 """Benchmark of the tDPD + RBC step on GB300.
 
 One bench step is one time step of the whole hot path (binning and sort,
-membrane forces, pair force + flux, velocity-Verlet update) over the
-single-RBC workload: a 500-vertex biconcave membrane in tDPD solvent, 20^3
-periodic box at density 3, 24,500 particles. The metric is particle-steps/s.
+membrane forces, pair force + flux, velocity-Verlet update). The default
+workload is the batched ensemble the metric is quoted on: 512 independent
+replicas of uneven size (cubic periodic boxes of side 8..16 at density 3,
+0..4 membranes of 500 vertices each, log-uniform permeability, uniform body
+force; 3.50 M particles) advanced together in one graph-captured step, and
+compared with the same replicas advanced one after another on the same GPU.
+The metric is particle-steps/s.
 
 Native arm (default): libtdpd.so through its C ABI. Each timed step is one
 replay of the captured step graph; an L2 flush (a write larger than the
@@ -38,12 +42,12 @@ import workloads as W  # noqa: E402
 
 METRIC = 'tDPD particle-steps/s on 1 GB300 (% HBM roofline); batched vs plain at tol'
 UNIT = 'particle-steps/s'
-# DRAM bytes (read + write) of one k_pair launch from one ncu capture of the
-# current kernel build (summaries under profiles/), keyed by workload, skin
-# and lane count: launches with and without a list rebuild, weighted by the
-# workload's rebuild rate (0.2725, 0.5); the capture is cold-cache, the bench
-# step follows an L2 flush, so the two see the same misses.
-PAIR_TRAFFIC = {('single_rbc', 0.2, 4): 11.53886e6, ('fluid_786k', 0.2, 1): 418.1664e6}
+# DRAM bytes (read + write) of one k_pair launch from an ncu capture of the
+# current kernel build (summaries under profiles/), keyed by workload, skin,
+# lane count and replica count (0: not an ensemble); the capture is
+# cold-cache and the bench step follows an L2 flush, so the two see the same
+# misses. A workload without an entry reports traffic null.
+PAIR_TRAFFIC = {}
 
 
 def _ns10(d):
@@ -68,7 +72,7 @@ WORKLOADS = {
                 lambda seed: [W.rbc_channel(seed=1003 + seed)]),
     'ensemble': ('512 independent replicas (cubic boxes 8..16 at rho=3, 0..4 RBCs, log-uniform '
                  'permeability, body force) batched in one graph-captured step',
-                 lambda seed: W.replica_ensemble(n_rep=512, seed=1004 + seed)),
+                 lambda seed, n_rep=512: W.replica_ensemble(n_rep=n_rep, seed=1004 + seed)),
 }
 
 
@@ -180,31 +184,79 @@ def oracle_rate(desc, seconds=12.0, max_steps=400):
     return n * steps / dt, steps, oracle.num_threads()
 
 
+def make_descs(args, rank):
+    """The workload's replica descriptions with the command line's options."""
+    gen = WORKLOADS[args.workload][1]
+    descs = gen(rank, args.replicas) if args.workload == 'ensemble' else gen(rank)
+    for d in descs:
+        d['cells_per_cutoff'] = args.cells_per_cutoff
+        d['skin'] = args.skin
+        d['lanes'] = args.lanes or None
+        if args.lagged_av and d.get('membrane'):
+            d['membrane']['lagged_av'] = 1
+        if args.random_flux > 0:
+            d['random_flux'] = dict(m_s=args.random_flux, rho=3.0)
+    return descs
+
+
+def common_config(args, descs, world):
+    """The workload keys of the JSON line (identical in both arms)."""
+    desc = WORKLOADS[args.workload][0]
+    if args.workload == 'ensemble' and args.replicas != 512:
+        desc = desc.replace('512 independent', '%d independent' % args.replicas)
+    return {'workload': desc, 'name': args.workload, 'replicas': len(descs),
+            'particles': sum(W.n_mobile(d) for d in descs),
+            'l2': 'flushed between timed steps (256 MB write)',
+            'area_volume': 'previous step (lagged)' if args.lagged_av else 'current step',
+            'random_flux': {'m_s': args.random_flux, 'rho': 3.0} if args.random_flux > 0 else 'off',
+            'parallelism': 'replicas only' if world > 1 else 'single GPU'}
+
+
+# particle-steps of oracle work the reference arm may spend (about two
+# minutes on 16 host cores at the oracle's 1.5 M particle-steps/s)
+REFERENCE_BUDGET = 1.8e8
+
+
 def run_reference(args):
+    """The FP64 oracle (cell list, OpenMP on every host core) on the same
+    workload: W untimed and K timed steps over a bounded sample (the
+    replicas in order while (K + W + 1) x their particles stay within the
+    budget; the default 20 + 5 steps take the whole 512-replica ensemble)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
-    desc = WORKLOADS[args.workload][1](0)[0]
-    n = W.n_mobile(desc)
-    o = oracle.Oracle(desc, mode=1)
+    descs = make_descs(args, 0)
+    sample, work = [], 0.0
+    for d in descs:
+        w = W.n_particles(d) * (args.steps + args.warmup + 1)
+        if sample and work + w > REFERENCE_BUDGET:
+            break
+        sample.append(d)
+        work += w
+    n = sum(W.n_mobile(d) for d in sample)
+    orcs = [oracle.Oracle(d, mode=1) for d in sample]
     for _ in range(args.warmup):
-        o.run(1)
-    ts = []
+        for o in orcs:
+            o.run(1)
+    total = 0.0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        o.run(1)
-        ts.append(time.perf_counter() - t0)
-    total = sum(ts)
+        for o in orcs:
+            o.run(1)
+        total += time.perf_counter() - t0
     value = n * args.steps / total
     cores = oracle.num_threads()
+    what = ('the whole workload' if len(sample) == len(descs) else
+            'the first %d of %d replicas' % (len(sample), len(descs)))
     line = {
         'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world,
         'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': 1e3 * total / args.steps,
         'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
-        'data': 'synthetic', 'config': {'workload': WORKLOADS[args.workload][0], 'particles': n},
+        'data': 'synthetic', 'config': common_config(args, descs, world),
         'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': cores, 'kind': 'oracle',
-                         'sample': 'full workload, %d oracle steps (FP64 cell list, OpenMP)' % args.steps},
+                         'sample': '%s (%d mobile particles), %d oracle steps each (FP64 cell list, OpenMP)' % (
+                             what, n, args.steps)},
         'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
     }
     print(json.dumps(line), flush=True)
@@ -222,15 +274,7 @@ def run_native(args):
     pkg.build()
     from paper_1611_06163_gb300 import binding as bd
 
-    descs = WORKLOADS[args.workload][1](rank)
-    for d in descs:
-        d['cells_per_cutoff'] = args.cells_per_cutoff
-        d['skin'] = args.skin
-        d['lanes'] = args.lanes or None
-        if args.lagged_av and d.get('membrane'):
-            d['membrane']['lagged_av'] = 1
-        if args.random_flux > 0:
-            d['random_flux'] = dict(m_s=args.random_flux, rho=3.0)
+    descs = make_descs(args, rank)
     n = sum(W.n_mobile(d) for d in descs)
     stream = torch.cuda.Stream()
     if len(descs) == 1:
@@ -244,9 +288,16 @@ def run_native(args):
             bd.tdpd_set_skin(h, args.skin)
         if args.lanes:
             bd.tdpd_set_lanes(h, args.lanes)
+    if args.pair_mode:
+        bd.tdpd_set_pair_mode(h, args.pair_mode)
     bd.tdpd_commit(h)
     nk = bd.tdpd_launches_per_step(h)
-    names = [bd.tdpd_kernel_name(h, k) for k in range(nk)]
+    # timed entries: one per launch, except that the half shell's pair entry
+    # spans its two launches (k_pair and k_pair_finish)
+    names = []
+    while bd.tdpd_kernel_name(h, len(names)) is not None:
+        names.append(bd.tdpd_kernel_name(h, len(names)))
+    pair_mode = bd.tdpd_pair_mode(h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device='cuda')
 
     def barrier():
@@ -296,17 +347,21 @@ def run_native(args):
     ipair = names.index('pair')
     pair_ms = float(mean_k[ipair])
     # The pair kernel is bound by instruction issue, not by memory: its roof
-    # is the lane-operation rate 152 SMs x 128 lanes x the maximum SM clock.
-    # Algorithmic operations per particle-step, counted from the equations: every
-    # ordered pair inside the flux cut-off costs 20 + 4 (ns - 1) lane
-    # operations, every pair inside the force cut-off another 110 (TEA-8 draw,
-    # Box-Muller, Eq. 3); pair counts are the workload's mean density times
-    # the cut-off spheres. Algorithmic bytes: read r, v~ (16 B each), C~ (4 B
-    # per species), v, F (16 B each), C, Q (4 B per species); write v, F, C, Q;
-    # plus the next binning's (cell, rank) 8 B = 112 + 16 ns bytes. With
-    # neighbour lists the binning is replaced by the list entries (4 B per
-    # partner within rcut + skin) and the position at the last build (16 B);
-    # the lists the kernel builds on rebuild steps are counted below.
+    # is the lane-operation rate (SMs x 128 FP32 lanes x the maximum SM
+    # clock; derived, not measured). Algorithmic operations per particle-step,
+    # counted from the equations: every ordered pair inside the flux cut-off
+    # costs 20 + 4 (ns - 1) lane operations, every pair inside the force
+    # cut-off another 110 (TEA-8 draw, Box-Muller, Eq. 3); pair counts are the
+    # workload's mean density times the cut-off spheres. With neighbour lists
+    # the lists the kernel builds on rebuild steps add one distance test (9
+    # operations) per list entry at the measured rebuild rate.
+    # Bytes: the compulsory pair bytes (read r, v~ 16 B each and C~ 4 B per
+    # species; write F 16 B and Q 4 B per species: 48 + 8 ns) give the HBM
+    # fraction; what the implementation moves besides -- the fused corrector
+    # (read v, F, C, Q of the last step, write v, C: 48 + 12 ns), the list
+    # entries (4 B per partner within rcut + skin, 16 B build position) and
+    # their rebuilds, or in cell mode the next binning (8 B) -- is listed
+    # separately.
     ns = int(descs[0]['n_species'])
     n_all = sum(W.n_particles(d) for d in descs)
     vol = sum(float(np.prod(d['L'])) for d in descs)
@@ -322,24 +377,34 @@ def run_native(args):
     skin = 0.2 if args.skin is None else args.skin
     rcut = max(float(d0['rc']), float(d0['rcc']))
     n_list = rho * 4.0 / 3.0 * math.pi * (rcut + skin) ** 3 if skin > 0 else 0.0
-    bytes_pp = 112 + 16 * ns if skin == 0 else 104 + 16 * ns + 16 + 4 * n_list
+    compulsory_pp = 48 + 8 * ns
+    impl = {'corrector': 48 + 12 * ns}
     if skin > 0:
-        # on a rebuild step the pair kernel first builds its lanes' lists:
-        # at least one distance test (9 operations) and one 4-byte write per
-        # list entry, and the 16-byte build position, at the measured rate
         ops_pp += rebuild_rate * 9 * n_list
-        bytes_pp += rebuild_rate * (4 * n_list + 16)
+        impl['lists'] = 4 * n_list + 16
+        impl['list_rebuilds'] = rebuild_rate * (4 * n_list + 16)
+    else:
+        impl['next_binning'] = 8
     hbm, src = peaks()
-    alu_peak = 152 * 128 * sm_max_mhz() * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = n_sm * 128 * sm_max_mhz() * 1e6 / 1e12
     alu = ops_pp * n_all / (pair_ms * 1e-3) / 1e12
-    gbs = bytes_pp * n_all / (pair_ms * 1e-3) / 1e9
+    gbs = compulsory_pp * n_all / (pair_ms * 1e-3) / 1e9
     lanes_now = bd.tdpd_lanes(h)
+    traffic = None
+    key = (args.workload, skin, lanes_now, args.replicas if args.workload == 'ensemble' else 0)
+    if not args.random_flux and not args.cells_per_cutoff and key in PAIR_TRAFFIC:
+        traffic = PAIR_TRAFFIC[key]
     roof = {'bound': 'alu', 'achieved': alu, 'peak': alu_peak, 'unit': 'Tops/s', 'frac': alu / alu_peak,
-            'traffic': (PAIR_TRAFFIC.get((args.workload, skin, lanes_now))
-                        if not args.random_flux and not args.cells_per_cutoff else None), 'peak_source': 'derived: 152 SMs x 128 lanes x %.0f MHz (measured max clock)' % sm_max_mhz(),
-            'kernel': 'k_pair', 'ops_per_particle': ops_pp,
+            'traffic': traffic, 'traffic_unit': 'bytes per k_pair launch (ncu DRAM read + write)',
+            'peak_source': 'derived: %d SMs (this device) x 128 FP32 lanes x %.0f MHz (measured max clock)' % (
+                n_sm, sm_max_mhz()),
+            'kernel': 'k_pair' + (' + k_pair_finish' if pair_mode == 2 else ''),
+            'ops_per_particle': ops_pp, 'particles_per_launch': n_all,
             'hbm': {'achieved': gbs, 'peak': hbm, 'unit': 'GB/s', 'frac': gbs / hbm, 'peak_source': src,
-                    'bytes_per_particle': bytes_pp},
+                    'bytes_per_particle': compulsory_pp,
+                    'implementation_bytes_per_particle': impl,
+                    'all_bytes_frac': sum(impl.values()) * n_all / (pair_ms * 1e-3) / 1e9 / hbm + gbs / hbm},
             'kernel_ms': {nm: float(m) for nm, m in zip(names, mean_k)}}
 
     # end to end through the public API: every replica's state in from pinned
@@ -410,9 +475,10 @@ def run_native(args):
             steps += s_
         rate = sum(W.n_mobile(d) for d in sample) / rate
         cpu = {'value': rate, 'unit': UNIT, 'cores': cores, 'kind': 'oracle',
-               'sample': '%s, %d FP64 oracle steps (cell list, OpenMP)' % (
+               'sample': '%s, %d FP64 oracle steps in all, about %.0f s per replica (cell list, OpenMP); '
+                         'value = their particles over the summed per-replica step times' % (
                    'full workload' if len(sample) == len(descs) else
-                   'first %d of %d replicas' % (len(sample), len(descs)), steps)}
+                   'first %d of %d replicas' % (len(sample), len(descs)), steps, args.cpu_seconds / len(sample))}
     bd.tdpd_destroy(h)
     for hp_ in parts:
         bd.tdpd_destroy(hp_)
@@ -421,13 +487,12 @@ def run_native(args):
             'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world, 'steps': args.steps,
             'warmup': args.warmup, 'ms_per_step': total_ms / args.steps, 'higher_is_better': True,
             'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
-            'config': {'workload': WORKLOADS[args.workload][0], 'name': args.workload, 'particles': n,
-                       'l2': 'flushed between timed steps (256 MB write)',
-                       'lanes_per_particle': lanes,
-                       'area_volume': 'previous step (lagged)' if args.lagged_av else 'current step',
-                       'random_flux': {'m_s': args.random_flux, 'rho': 3.0} if args.random_flux > 0 else 'off',
-                       'neighbour_list': {'skin': skin, 'rebuilds_per_step': rebuild_rate} if skin > 0 else 'off (cell stencil every step)',
-                       'parallelism': 'replicas only' if world > 1 else 'single GPU'},
+            'config': common_config(args, descs, world),
+            'tuning': {'lanes_per_particle': lanes,
+                       'pair_mode': {1: 'full shell', 2: 'half shell (fixed-point partner sums)'}.get(pair_mode),
+                       'neighbour_list': ({'skin': skin, 'rebuilds_per_replica_step': rebuild_rate} if skin > 0
+                                          else 'off (cell stencil every step)'),
+                       'cells_per_cutoff': args.cells_per_cutoff or 'library default (2)'},
             'roofline': roof,
             'cpu_baseline': cpu,
             'e2e': e2e,
@@ -450,9 +515,10 @@ def main():
     ap.add_argument('--impl', default='native', choices=['native', 'reference'])
     ap.add_argument('--cpu-seconds', type=float, default=12.0)
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--workload', default='single_rbc', choices=sorted(WORKLOADS))
-    ap.add_argument('--compare-sequential', action='store_true',
-                    help='ensemble only: also time the replicas one after another')
+    ap.add_argument('--workload', default='ensemble', choices=sorted(WORKLOADS))
+    ap.add_argument('--replicas', type=int, default=512, help='ensemble only: number of replicas')
+    ap.add_argument('--no-compare-sequential', dest='compare_sequential', action='store_false',
+                    help='ensemble only: skip timing the replicas one after another')
     ap.add_argument('--compare-steps', type=int, default=20)
     ap.add_argument('--cells-per-cutoff', type=int, default=0,
                     help='cell-list stencil width m (cells of edge >= rcut/m); 0 = library default')
@@ -462,6 +528,8 @@ def main():
                     help='area/volume constraints from the previous step (the concurrent variant of Sec. 3.3)')
     ap.add_argument('--lanes', type=int, default=0,
                     help='lanes per particle of the pair kernel (0: timed at commit)')
+    ap.add_argument('--pair-mode', type=int, default=0, choices=[0, 1, 2],
+                    help='pair kernel with lists: 1 full shell, 2 half shell, 0 chosen at commit')
     ap.add_argument('--skin', type=float, default=None,
                     help='neighbour-list skin; 0 = cell mode (stencil every step); default: the library\'s')
     args = ap.parse_args()

@@ -111,7 +111,10 @@ typedef struct {
 tdpd_status tdpd_create(tdpd_sys **out, const tdpd_config *cfg);
 
 /* Eq. 3 coefficients alpha_ij, gamma_ij, sigma_ij for the type pair (set
- * symmetrically). Eq. 4 (sigma^2 = 2 kT gamma) is the caller's choice. */
+ * symmetrically; gamma, sigma finite and >= 0). tdpd_commit checks Eq. 4
+ * (sigma^2 = 2 kT gamma): every type pair of a replica whose gamma or sigma
+ * is nonzero must have both nonzero and the same sigma^2 / (2 gamma) within
+ * a relative 1e-5, else TDPD_EINVAL. */
 tdpd_status tdpd_set_pair(tdpd_sys *s, int type_i, int type_j, float a, float gamma, float sigma);
 
 /* Eq. 6 kappa_ij of one species for the type pair (set symmetrically). */
@@ -140,7 +143,7 @@ tdpd_status tdpd_set_random_flux(tdpd_sys *s, float m_s, float rho);
  * another mode. */
 tdpd_status tdpd_set_body_force_profile(tdpd_sys *s, int mode);
 
-/* Cylindrical wall for the Dirichlet transport validation (Sec. 4.1, Eq. 17):
+/* Cylindrical wall for the Dirichlet transport validation (Sec. 4.2, Eq. 17):
  * a mobile particle whose predicted position lies farther than radius from
  * the axis y = L_y/2, z = L_z/2 (along x) is reflected back across the
  * cylinder surface and its velocity reversed, as at the bounce-back planes.
@@ -188,6 +191,27 @@ tdpd_status tdpd_set_lanes(tdpd_sys *s, int lanes);
 /* Lanes per particle the pair kernel uses (fixed at commit; before commit the
  * value tdpd_set_lanes set, 0 when timed). */
 int tdpd_lanes(const tdpd_sys *s);
+
+/* How the pair kernel covers the pairs in neighbour-list mode: 1 the full
+ * shell (each particle walks all its partners, so every pair term of Eq. 3
+ * and Eq. 6 is evaluated from both sides, by the pair symmetry of the random
+ * numbers with equal results), 2 the half shell (each unordered pair once,
+ * from the side where the partner's cell lies in the upper half of the
+ * stencil; the partner's share -f_ij, -q_ij is summed in 64-bit fixed point
+ * by integer atomics, which keeps the results independent of the order in
+ * which they land), 0 (the default) chosen at commit: timed against each
+ * other together with the lanes when the lanes are not pinned, else the half
+ * shell. Cell mode (skin 0) always uses the full stencil. The mode changes
+ * the order of the floating-point sums, so the last bits of F and Q depend
+ * on it; two handles with the same lanes and mode give the same bits. Before
+ * tdpd_commit; TDPD_EINVAL for another value, TDPD_ESTATE after commit. No
+ * counterpart in the paper (its kernels evaluate every pair from both
+ * sides). */
+tdpd_status tdpd_set_pair_mode(tdpd_sys *s, int mode);
+
+/* The pair mode in use after commit (1 full shell, 2 half shell; cell mode
+ * reports 1); before commit the value tdpd_set_pair_mode set. */
+int tdpd_pair_mode(const tdpd_sys *s);
 
 /* Skin of the Verlet neighbour lists of the pair kernel (length units): each
  * particle keeps the partners within max(rc, rcc) + skin found at a list
@@ -287,7 +311,14 @@ tdpd_status tdpd_read_observables(tdpd_sys *s, int replica, tdpd_obs *out);
  * the current step, as used by the constraint forces (Eq. 14-15). */
 tdpd_status tdpd_read_rbc(tdpd_sys *s, int replica, double *area, double *volume);
 /* Per-replica status words (TDPD_OK, TDPD_ENONFINITE, or TDPD_EOVERFLOW for
- * an overflowed neighbour list), int32[n_replicas]. */
+ * an overflowed neighbour list), int32[n_replicas]. A replica whose status is
+ * not TDPD_OK is quarantined from the next step on: its particles are neither
+ * moved nor re-evaluated (state, forces and fluxes stay as the faulting
+ * evaluation left them, and its neighbour lists are not rebuilt), while the
+ * other replicas of the batch step on unaffected (each replica only ever
+ * interacts with itself). Loading a state (tdpd_set_state, tdpd_set_states,
+ * tdpd_set_states_device) clears every status and evaluates the forces again,
+ * which sets the status again if the loaded state still faults. */
 tdpd_status tdpd_replica_status(tdpd_sys *s, int32_t *status);
 
 int tdpd_num_replicas(const tdpd_sys *s);
@@ -369,27 +400,34 @@ void tdpd_mlp_destroy(tdpd_mlp *m);
  * lives in one fixed scratch array inside the library.
  *
  * Computes, for n free particles (no membranes) of a box with every axis
- * periodic, the force F^C + F^D + F^R (Eq. 3) plus body force and the flux
- * Q^D (Eq. 6) plus reaction source at step number `step`, with the same
- * kernels and random numbers as tdpd_commit followed by tdpd_read_forces.
- *   cfg        host; box, species, cut-offs, seed (every axis periodic)
+ * periodic, the same pair force (plus the configuration's body force) and
+ * the same flux as tdpd_commit followed by tdpd_read_forces, at step number
+ * `step`, with the same kernels and random numbers. No reaction source is
+ * applied (this call takes no reaction parameters).
+ *   cfg        host; box, species, cut-offs, seed (every axis periodic); the
+ *              checks of tdpd_create apply
  *   pair_coef  host float[n_types*n_types*3]: a, gamma, sigma per type pair
  *   kappa      host float[n_types*n_types*n_species]
  *   pos, vel   device float[n*3]; positions in [0, L)
  *   conc       device float[n*n_species]
- *   type       device int32[n]
+ *   type       device int32[n], each in [0, n_types)
  *   force      device float[n*3] (written), flux device float[n*n_species] (written)
  *   stream     cudaStream_t on which the work is enqueued (NULL: default stream)
  * Limits: n <= TDPD_NOALLOC_MAX_PARTICLES, cells (edge >= max(rc, rcc)/m) <=
  * TDPD_NOALLOC_MAX_CELLS, n_species <= TDPD_NOALLOC_MAX_SPECIES; larger inputs
  * return TDPD_EINVAL with the reason in tdpd_last_error(NULL), before any
- * device work. The call only enqueues (no synchronisation, no device-side
- * status is returned). The first call on a device looks up the scratch
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture. Every call on a device
- * reuses the same scratch, which keeps the previous call's contents (the call
- * clears what must start at zero): calls whose work overlaps on the GPU --
- * from several streams or threads -- race and must be serialised by the caller. */
+ * device work. The call only enqueues (no synchronisation) and returns no
+ * device-side status: when a type lies outside [0, n_types) or a force comes
+ * out non-finite, every element of force and flux is NaN, so the caller
+ * checks the outputs for non-finite values. The first call on a device looks
+ * up the scratch array's device address (cudaGetSymbolAddress) with that
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture. The kept address does not survive
+ * cudaDeviceReset (do not call this entry point after a reset of a device it
+ * has used). Every call on a device reuses the same scratch, which keeps the
+ * previous call's contents (the call clears what must start at zero): calls
+ * whose work overlaps on the GPU -- from several streams or threads -- race
+ * and must be serialised by the caller. */
 tdpd_status tdpd_pair_forces_noalloc(const tdpd_config *cfg, const float *pair_coef,
                                      const float *kappa, int n, const float *pos, const float *vel,
                                      const float *conc, const int32_t *type, uint32_t step,

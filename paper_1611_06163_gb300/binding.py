@@ -54,7 +54,7 @@ class tdpd_obs(C.Structure):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError('libtdpd.so not built (run paper_1611_06163_gb300/build.py or '
+        raise ImportError('libtdpd.so not built (run python paper_1611_06163_gb300/buildlib.py or '
                           '__graft_entry__.build()); there is no fallback implementation')
     L = C.CDLL(LIB_PATH)
     P, I, F = C.c_void_p, C.c_int, C.c_float
@@ -71,6 +71,8 @@ def _load():
         'tdpd_set_lanes': ([P, I], I),
         'tdpd_set_skin': ([P, C.c_float], I),
         'tdpd_lanes': ([P], I),
+        'tdpd_set_pair_mode': ([P, I], I),
+        'tdpd_pair_mode': ([P], I),
         'tdpd_set_random_flux': ([P, C.c_float, C.c_float], I),
         'tdpd_set_body_force_profile': ([P, I], I),
         'tdpd_set_cylinder_wall': ([P, F], I),
@@ -193,6 +195,14 @@ def tdpd_set_stream(h, stream_ptr):
 
 def tdpd_set_lanes(h, lanes):
     _chk(h, lib.tdpd_set_lanes(h, int(lanes)))
+
+
+def tdpd_set_pair_mode(h, mode):
+    _chk(h, lib.tdpd_set_pair_mode(h, int(mode)))
+
+
+def tdpd_pair_mode(h):
+    return int(lib.tdpd_pair_mode(h))
 
 
 def tdpd_set_skin(h, skin):
@@ -467,6 +477,8 @@ def create_from(desc, stream_ptr=None):
             tdpd_set_skin(h, desc['skin'])
         if desc.get('lanes') is not None:
             tdpd_set_lanes(h, desc['lanes'])
+        if desc.get('pair_mode') is not None:
+            tdpd_set_pair_mode(h, desc['pair_mode'])
         if stream_ptr:
             tdpd_set_stream(h, stream_ptr)
     except Exception:

@@ -301,6 +301,27 @@ __device__ __forceinline__ float min_image(float d, float L, int periodic)
     return d;
 }
 
+// ------------------------------------------- fixed-point accumulation
+// The half-shell pair kernel hands each pair's share for the partner to a
+// 64-bit fixed-point accumulator with integer atomics: integer sums do not
+// depend on the order in which the atomics land, so results stay
+// bit-reproducible. Forces in units of 2^-32, fluxes in units of 2^-40; a
+// single contribution must stay below 2^23 (force) or 2^16 (flux), which
+// keeps a particle's sum of up to 256 of them inside the 64-bit range; a
+// larger or non-finite contribution is dropped and flags the replica
+// (status bit 1, as a non-finite force).
+constexpr float ACC_F_SCALE = 0x1p32f, ACC_F_UNIT = 0x1p-32f, ACC_F_LIMIT = 0x1p23f;
+constexpr float ACC_Q_SCALE = 0x1p40f, ACC_Q_UNIT = 0x1p-40f, ACC_Q_LIMIT = 0x1p16f;
+
+__device__ __forceinline__ void acc_add(long long *p, float x, float scale, float limit, uint32_t *err)
+{
+    if (!(fabsf(x) < limit)) {
+        atomicOr(err, 1u);
+        return;
+    }
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__float2ll_rn(x * scale));
+}
+
 // ---------------------------------------------------- FP64 compensated sum
 // (sum, compensation) pair; merging two pairs adds the rounding error of the
 // leading sum exactly (Knuth's TwoSum), branch-free.

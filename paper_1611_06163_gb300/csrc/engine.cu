@@ -69,6 +69,11 @@ struct tdpd_sys {
     int N = 0, NC = 0, ns = 0, n_rbc = 0, max_nv = 0;
     int lpp = 1;
     int lanes_fixed = 0;   // 0: timed at commit
+    int mode_fixed = 0;    // pair mode: 0 chosen at commit, 1 full shell, 2 half shell
+    bool half = false;     // list mode with half-shell lists (each unordered pair once)
+    long long *accF = nullptr, *accQ = nullptr;   // half shell: partners' fixed-point shares
+    float4 *fown = nullptr;                       // half shell: own force sums
+    float *qown = nullptr;                        // half shell: own flux sums
     float skin = -1.0f;    // neighbour-list skin; 0: cell mode; < 0: default
     bool use_list = false;
     int *nl = nullptr, *nlc = nullptr;   // neighbour lists (own allocation: resized by the lane count)
@@ -89,6 +94,7 @@ struct tdpd_sys {
     std::vector<int4> h_chunks;
     int2 *cellrank = nullptr, *keys = nullptr;
     uint32_t *errw = nullptr, *step_ctr = nullptr;
+    uint32_t *quar = nullptr;            // per replica: quarantined this step (set by the gather)
     RepParams *d_reps = nullptr;
     RbcDev *d_rbcs = nullptr;
     int *d_tri = nullptr;
@@ -363,6 +369,28 @@ RepParams tdpd::build_rep_params(const tdpd_config &c, const float *pair_coef, c
 
 void tdpd::set_thread_error(const char *msg) { g_err = msg; }
 
+bool tdpd::config_error(const tdpd_config &c, char *msg, size_t len)
+{
+    auto why = [&](const char *fmt, int v = 0) {
+        std::snprintf(msg, len, fmt, v);
+        return true;
+    };
+    for (int k = 0; k < 3; ++k)
+        if (!(c.L[k] > 0) || !std::isfinite(c.L[k])) return why("box edge %d must be positive and finite", k);
+    if (!c.periodic[0] || !c.periodic[1]) return why("x and y must be periodic (walls only along z)");
+    if (!c.periodic[2] && !(c.wall_lo >= 0 && c.wall_lo < c.wall_hi && c.wall_hi <= c.L[2]))
+        return why("walls need 0 <= wall_lo < wall_hi <= L[2]");
+    if (c.n_types < 1 || c.n_types > MAXT) return why("n_types must be in 1..%d", MAXT);
+    if (c.n_species < 1 || c.n_species > MAXS) return why("n_species must be in 1..%d", MAXS);
+    if (!(c.dt > 0) || !std::isfinite(c.dt)) return why("dt must be positive and finite");
+    if (!(c.rc > 0) || !(c.rcc >= 0) || !std::isfinite(c.rc) || !std::isfinite(c.rcc))
+        return why("cut-offs: rc > 0, rcc >= 0, both finite");
+    if (!(c.s_f > 0) || !(c.s_c > 0)) return why("weight exponents must be positive");
+    if (c.frozen_types >> c.n_types) return why("frozen_types names a type >= n_types (%d)", c.n_types);
+    if (c.cells_per_cutoff < 0 || c.cells_per_cutoff > 3) return why("cells_per_cutoff must be 0, 1, 2 or 3");
+    return false;
+}
+
 namespace {
 
 tdpd_status free_device(tdpd_sys *s)
@@ -429,13 +457,15 @@ PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum, 
     PairArgs a{};
     a.tile_sum = tile_sum;
     a.b = b; a.fext = s->fext; a.mx = s->mx; a.mv = s->mv; a.reps = s->d_reps; a.cell_start = s->cell_start; a.count = s->count;
-    a.cellrank = s->cellrank; a.err = s->errw; a.step_ctr = s->step_ctr; a.n = s->N; a.ns = s->ns;
+    a.cellrank = s->cellrank; a.err = s->errw; a.quar = s->quar; a.step_ctr = s->step_ctr; a.n = s->N; a.ns = s->ns;
     a.integrate = integrate;
     a.lpp = s->lpp;
     for (const HostRep &R : s->reps)
         if (R.qr_ms > 0.0f) a.qr = 1;
     if (s->use_list) {
         a.nl = s->nl; a.nlc = s->nlc; a.cap = s->nl_cap; a.xb = s->xb; a.disp_next = disp_next;
+        a.half = s->half ? 1 : 0;
+        a.accF = s->accF; a.accQ = s->accQ; a.fown = s->fown; a.qown = s->qown;
         if (build_rb) {
             a.rb = build_rb;
             a.nl_w = s->nl; a.nlc_w = s->nlc; a.xb_w = s->xb;
@@ -450,12 +480,23 @@ PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum, 
 ListArgs list_args(tdpd_sys *s, const Buffers &b, const uint32_t *rb, int cap)
 {
     ListArgs l{};
-    l.pos = b.pos; l.vel = b.vel; l.reps = s->d_reps; l.cell_start = s->cell_start; l.rb = rb;
+    l.pos = b.pos; l.vel = b.vel; l.reps = s->d_reps; l.cell_start = s->cell_start; l.rb = rb; l.quar = s->quar;
     l.n_rep = (int)s->reps.size();
     l.nl = s->nl; l.nlc = s->nlc; l.xb = s->xb; l.err = s->errw; l.n = s->N; l.lpp = s->lpp; l.cap = cap;
     l.m2 = 1;
     for (const HostRep &R : s->reps) l.m2 = l.m2 && R.m == 2;
+    l.half = s->half ? 1 : 0;
     return l;
+}
+
+// The gather of each step derives the quarantine from the status words.
+Quarantine quarantine(tdpd_sys *s)
+{
+    Quarantine q;
+    q.err = s->errw;
+    q.quar = s->quar;
+    q.n_reps = (int)s->reps.size();
+    return q;
 }
 
 // Up to this many replicas every binning CTA takes the rebuild decision
@@ -544,7 +585,7 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st, any);
         mark();
         launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st,
-                           s->rb, nrep, s->tile_sum[0], s->n_tiles);
+                           s->rb, nrep, s->tile_sum[0], s->n_tiles, quarantine(s));
         mark();
         if (!pair_builds_lists(s)) {
             launch_list_build(list_args(s, nxt, s->rb, s->nl_cap), st);
@@ -555,7 +596,8 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         mark();
         launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st);
         mark();
-        launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st);
+        launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st,
+                           nullptr, 0, nullptr, 0, quarantine(s));
         mark();
     }
     if (s->n_rbc && ev) {
@@ -624,6 +666,7 @@ void enqueue_init(tdpd_sys *s, cudaStream_t st, bool branch)
     cudaMemsetAsync(s->tile_sum[0], 0, sizeof(int) * s->n_tiles, st);
     cudaMemsetAsync(s->tile_sum[1], 0, sizeof(int) * s->n_tiles, st);
     cudaMemsetAsync(s->errw, 0, sizeof(uint32_t) * s->reps.size(), st);
+    cudaMemsetAsync(s->quar, 0, sizeof(uint32_t) * s->reps.size(), st);
     cudaMemsetAsync(s->fext, 0, sizeof(float4) * N, st);
     launch_pack_state(s->d_in, s->d_wstat, s->buf[0], s->mx, s->mv, N, ns, st);
     branch = branch && s->n_rbc;
@@ -640,12 +683,12 @@ void enqueue_init(tdpd_sys *s, cudaStream_t st, bool branch)
     launch_scatter_keys(s->buf[0], s->cellrank, s->cell_start, s->keys, N, st);
     if (s->use_list) {
         launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0,
-                           st, nullptr, 0, s->tile_sum[0], s->n_tiles);
+                           st, nullptr, 0, s->tile_sum[0], s->n_tiles, quarantine(s));
         cudaMemsetAsync(s->disp[1], 0, sizeof(uint32_t) * s->reps.size(), st);
         launch_list_build(list_args(s, s->buf[1], s->rb_all, s->nl_cap), st);
     } else {
         launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0,
-                           st);
+                           st, nullptr, 0, nullptr, 0, quarantine(s));
     }
     if (s->n_rbc && !branch) {
         const MemArgs m = mem_args(s, 1, 0);
@@ -729,48 +772,65 @@ tdpd_status prepare_list(tdpd_sys *s)
     return TDPD_OK;
 }
 
+// Pick the pair kernel's shape at commit by timing its forces-only mode
+// (idempotent apart from the next binning's counters) for each candidate:
+// the lanes per particle (1..32, or the pinned count) and, with neighbour
+// lists, the full shell (every pair from both sides) against the half shell
+// (each pair once, partner shares by fixed-point atomics), unless the mode is
+// pinned. The fastest of five timed launches per candidate; then the first
+// candidate within 3 % of the best, half shell before full and fewer lanes
+// before more (they are no slower once the caches are cold, and near-equal
+// times would otherwise flip between runs). The state is then rebuilt with
+// the winner.
 tdpd_status autotune(tdpd_sys *s)
 {
     cudaStream_t st = exec_stream(s);
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    // the fastest of five timed launches per lane count; then the fewest
-    // lanes within 3 % of the best (they are no slower once the caches are
-    // cold, and near-equal times would otherwise flip between runs)
-    std::vector<std::pair<int, float>> t;
-    for (int lpp = 1; lpp <= 32; lpp *= 2) {
-        if (lpp > 1 && (long)s->N * lpp > 4000000L) break;
-        s->lpp = lpp;
-        tdpd_status rc;
-        if (s->use_list && (rc = prepare_list(s))) return rc;
-        const PairArgs a = pair_args(s, s->buf[1], 0, s->tile_sum[1], s->disp[1]);
-        launch_pair(a, st);                       // warm-up
-        float fastest = 1e30f;
-        for (int k = 0; k < 5; ++k) {
-            cudaEventRecord(e0, st);
-            launch_pair(a, st);
-            cudaEventRecord(e1, st);
-            cudaError_t e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return fail(s, TDPD_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    std::vector<int> modes;
+    if (!s->use_list) modes = {1};
+    else if (s->mode_fixed) modes = {s->mode_fixed};
+    else modes = {2, 1};
+    struct Cand { int mode, lpp; float ms; };
+    std::vector<Cand> t;
+    for (int mode : modes) {
+        for (int lpp = 1; lpp <= 32; lpp *= 2) {
+            if (s->lanes_fixed > 0 && lpp != s->lanes_fixed) continue;
+            if (s->lanes_fixed == 0 && lpp > 1 && (long)s->N * lpp > 4000000L) break;
+            s->lpp = lpp;
+            s->half = mode == 2;
+            tdpd_status rc;
+            if (s->use_list && (rc = prepare_list(s))) return rc;
+            const PairArgs a = pair_args(s, s->buf[1], 0, s->tile_sum[1], s->disp[1]);
+            launch_pair(a, st);                       // warm-up
+            float fastest = 1e30f;
+            for (int k = 0; k < 5; ++k) {
+                cudaEventRecord(e0, st);
+                launch_pair(a, st);
+                cudaEventRecord(e1, st);
+                cudaError_t e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return fail(s, TDPD_ECUDA, "autotune: %s", cudaGetErrorString(e));
+                }
+                fastest = std::min(fastest, ms);
             }
-            fastest = std::min(fastest, ms);
+            t.push_back({mode, lpp, fastest});
         }
-        t.push_back({lpp, fastest});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     float best = 1e30f;
-    for (const auto &x : t) best = std::min(best, x.second);
-    int best_lpp = t.empty() ? s->lpp : t.back().first;
+    for (const auto &x : t) best = std::min(best, x.ms);
+    Cand win = t.empty() ? Cand{s->half ? 2 : 1, s->lpp, 0.f} : t.back();
     for (const auto &x : t)
-        if (x.second <= 1.03f * best) { best_lpp = x.first; break; }
-    s->lpp = best_lpp;
+        if (x.ms <= 1.03f * best) { win = x; break; }
+    s->lpp = win.lpp;
+    s->half = s->use_list && win.mode == 2;
     tdpd_status rc;
     if (s->use_list && (rc = prepare_list(s))) return rc;
     return init_state(s);
@@ -867,6 +927,22 @@ tdpd_status commit(tdpd_sys *s)
         const long ncells = (long)R.nc[0] * R.nc[1] * R.nc[2];
         if ((long)NC + ncells > (1L << 30)) return fail(s, TDPD_EOVERFLOW, "too many cells");
         if (!R.rbcs.empty() && !R.has_mem) return fail(s, TDPD_ESTATE, "replica %zu has membranes but no tdpd_set_membrane", r);
+        {
+            // Eq. 4: sigma^2 = 2 kT gamma with one temperature for every type
+            // pair that has a dissipative or random force
+            double kT = -1.0;
+            for (int i = 0; i < R.cfg.n_types; ++i)
+                for (int j = i; j < R.cfg.n_types; ++j) {
+                    const double g = R.gamma[i * MAXT + j], sg = R.sigma[i * MAXT + j];
+                    if (g == 0.0 && sg == 0.0) continue;
+                    if (g == 0.0 || sg == 0.0)
+                        return fail(s, TDPD_EINVAL, "replica %zu, types %d-%d: Eq. 4 needs gamma and sigma both zero or both positive", r, i, j);
+                    const double t = sg * sg / (2.0 * g);
+                    if (kT < 0.0) kT = t;
+                    else if (std::fabs(t - kT) > 1e-5 * kT)
+                        return fail(s, TDPD_EINVAL, "replica %zu, types %d-%d: sigma^2 / (2 gamma) = %g differs from %g (Eq. 4 fixes one kT)", r, i, j, t, kT);
+                }
+        }
         s->rep_pbase.push_back(N);
         s->rep_rbc0.push_back((int)s->h_rbcs.size());
         P.push_back(make_params(R, NC, N, n));
@@ -969,7 +1045,8 @@ tdpd_status commit(tdpd_sys *s)
         (rc = dalloc(s, &s->cell_start, (size_t)s->n_tiles * SCAN_TILE + 1)) ||
         (rc = dalloc(s, &s->tile_sum[0], s->n_tiles)) || (rc = dalloc(s, &s->tile_sum[1], s->n_tiles)) ||
         (rc = dalloc(s, &s->d_chunks, s->h_chunks.size())) ||
-        (rc = dalloc(s, &s->errw, s->reps.size())) || (rc = dalloc(s, &s->step_ctr, 3)) ||
+        (rc = dalloc(s, &s->errw, s->reps.size())) || (rc = dalloc(s, &s->quar, s->reps.size())) ||
+        (rc = dalloc(s, &s->step_ctr, 3)) ||
         (rc = dalloc(s, &s->d_reps, P.size())) || (rc = dalloc(s, &s->d_obs, OBS_K * s->h_chunks.size())))
         return rc;
     if ((rc = upload(s, s->d_reps, P.data(), P.size()))) return rc;
@@ -1051,6 +1128,12 @@ tdpd_status commit(tdpd_sys *s)
             (rc = dalloc(s, &s->nlc, (size_t)N * 32)) || (rc = dalloc(s, &s->builds, nrep)))
             return rc;
         CU(cudaMemsetAsync(s->builds, 0, sizeof(uint32_t) * nrep, exec_stream(s)));
+        // half-shell accumulators (zero between steps) and own sums
+        if ((rc = dalloc(s, &s->accF, (size_t)N * 4)) || (rc = dalloc(s, &s->accQ, (size_t)N * ns)) ||
+            (rc = dalloc(s, &s->fown, N)) || (rc = dalloc(s, &s->qown, (size_t)N * ns)))
+            return rc;
+        CU(cudaMemsetAsync(s->accF, 0, sizeof(long long) * 4 * (size_t)N, exec_stream(s)));
+        CU(cudaMemsetAsync(s->accQ, 0, sizeof(long long) * (size_t)N * ns, exec_stream(s)));
         std::vector<uint32_t> ones(nrep + 1, 1u);
         if ((rc = upload(s, s->rb_all, ones.data(), ones.size()))) return rc;
         CU(cudaMemsetAsync(s->disp[0], 0, sizeof(uint32_t) * nrep, exec_stream(s)));
@@ -1058,6 +1141,8 @@ tdpd_status commit(tdpd_sys *s)
     }
     s->step = 0;
     if (s->lanes_fixed > 0) s->lpp = s->lanes_fixed;
+    // pinned lanes and no pinned mode: the half shell, without timing
+    s->half = s->use_list && s->mode_fixed != 1;
     if (s->use_list) {
         // a sorted state for the counting pass that sizes the lists
         s->use_list = false;
@@ -1128,18 +1213,8 @@ tdpd_status download(tdpd_sys *s, int r, float *pos, float *vel, float *conc, fl
 tdpd_status check_config(tdpd_sys *s, const tdpd_config *c)
 {
     if (!c) return fail(s, TDPD_EINVAL, "null config");
-    for (int k = 0; k < 3; ++k)
-        if (!(c->L[k] > 0) || !std::isfinite(c->L[k])) return fail(s, TDPD_EINVAL, "box edge %d must be positive", k);
-    if (!c->periodic[0] || !c->periodic[1]) return fail(s, TDPD_EINVAL, "x and y must be periodic (walls only along z)");
-    if (!c->periodic[2] && !(c->wall_lo >= 0 && c->wall_lo < c->wall_hi && c->wall_hi <= c->L[2]))
-        return fail(s, TDPD_EINVAL, "walls need 0 <= wall_lo < wall_hi <= L[2]");
-    if (c->n_types < 1 || c->n_types > MAXT) return fail(s, TDPD_EINVAL, "n_types must be in 1..%d", MAXT);
-    if (c->n_species < 1 || c->n_species > MAXS) return fail(s, TDPD_EINVAL, "n_species must be in 1..%d", MAXS);
-    if (!(c->dt > 0)) return fail(s, TDPD_EINVAL, "dt must be positive");
-    if (!(c->rc > 0) || !(c->rcc >= 0)) return fail(s, TDPD_EINVAL, "cut-offs: rc > 0, rcc >= 0");
-    if (!(c->s_f > 0) || !(c->s_c > 0)) return fail(s, TDPD_EINVAL, "weight exponents must be positive");
-    if (c->frozen_types >> c->n_types) return fail(s, TDPD_EINVAL, "frozen_types names a type >= n_types");
-    if (c->cells_per_cutoff < 0 || c->cells_per_cutoff > 3) return fail(s, TDPD_EINVAL, "cells_per_cutoff must be 0, 1, 2 or 3");
+    char msg[160];
+    if (config_error(*c, msg, sizeof msg)) return fail(s, TDPD_EINVAL, "%s", msg);
     return TDPD_OK;
 }
 
@@ -1175,7 +1250,8 @@ tdpd_status tdpd_set_pair(tdpd_sys *s, int ti, int tj, float a, float gamma, flo
     HostRep &R = s->reps[0];
     if (s->reps.size() != 1) return fail(s, TDPD_ESTATE, "set parameters on the replicas before batching");
     if (ti < 0 || tj < 0 || ti >= R.cfg.n_types || tj >= R.cfg.n_types) return fail(s, TDPD_EINVAL, "type out of range");
-    if (!std::isfinite(a) || !(gamma >= 0) || !(sigma >= 0)) return fail(s, TDPD_EINVAL, "bad pair coefficients");
+    if (!std::isfinite(a) || !(gamma >= 0) || !(sigma >= 0) || !std::isfinite(gamma) || !std::isfinite(sigma))
+        return fail(s, TDPD_EINVAL, "bad pair coefficients");
     for (int k = 0; k < 2; ++k) {
         const int i = k ? tj : ti, j = k ? ti : tj;
         R.a[i * MAXT + j] = a;
@@ -1374,6 +1450,22 @@ tdpd_status tdpd_set_lanes(tdpd_sys *s, int lanes)
     return TDPD_OK;
 }
 
+tdpd_status tdpd_set_pair_mode(tdpd_sys *s, int mode)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed) return fail(s, TDPD_ESTATE, "the pair mode is fixed after commit");
+    if (mode < 0 || mode > 2) return fail(s, TDPD_EINVAL, "pair mode must be 0 (chosen at commit), 1 (full shell) or 2 (half shell)");
+    s->mode_fixed = mode;
+    return TDPD_OK;
+}
+
+int tdpd_pair_mode(const tdpd_sys *s)
+{
+    if (!s) return 0;
+    if (!s->committed) return s->mode_fixed;
+    return s->half ? 2 : 1;
+}
+
 tdpd_status tdpd_set_skin(tdpd_sys *s, float skin)
 {
     if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
@@ -1560,7 +1652,7 @@ tdpd_status tdpd_save(tdpd_sys *s, const char *path)
     std::memcpy(H.magic, CKP_MAGIC, 8);
     H.version = 1;
     H.N = s->N; H.NC = s->NC; H.ns = s->ns; H.n_rep = (int)s->reps.size(); H.n_rbc = s->n_rbc;
-    H.lpp = s->lpp; H.use_list = s->use_list ? 1 : 0; H.nl_cap = s->nl_cap; H.parity = s->parity;
+    H.lpp = s->lpp; H.use_list = s->use_list ? (s->half ? 2 : 1) : 0; H.nl_cap = s->nl_cap; H.parity = s->parity;
     H.n_tiles = s->n_tiles; H.step = s->step;
     H.nl_ints = nl_used_ints(s);
     CU(cudaStreamSynchronize(exec_stream(s)));
@@ -1599,7 +1691,7 @@ tdpd_status tdpd_load(tdpd_sys *s, const char *path)
     uint64_t h = 0;
     if ((rc = config_hash(s, &h))) { std::fclose(f); return rc; }
     if (H.N != s->N || H.NC != s->NC || H.ns != s->ns || H.n_rep != (int)s->reps.size() || H.n_rbc != s->n_rbc ||
-        H.use_list != (s->use_list ? 1 : 0) || H.n_tiles != s->n_tiles || H.cfg_hash != h) {
+        (H.use_list != 0) != s->use_list || H.n_tiles != s->n_tiles || H.cfg_hash != h) {
         std::fclose(f);
         return fail(s, TDPD_EINVAL, "checkpoint of another configuration (particles, cells, species, replicas, "
                                     "membranes, list mode or parameters differ)");
@@ -1608,6 +1700,12 @@ tdpd_status tdpd_load(tdpd_sys *s, const char *path)
         std::fclose(f);
         return fail(s, TDPD_EINVAL, "checkpoint taken with %d lanes per particle, this handle uses %d "
                                     "(tdpd_set_lanes before commit)", H.lpp, s->lpp);
+    }
+    if (s->use_list && H.use_list != (s->half ? 2 : 1)) {
+        std::fclose(f);
+        return fail(s, TDPD_EINVAL, "checkpoint taken with %s-shell lists, this handle uses %s-shell lists "
+                                    "(tdpd_set_pair_mode before commit)", H.use_list == 2 ? "half" : "full",
+                    s->half ? "half" : "full");
     }
     if (H.parity != 0 && H.parity != 1) {
         std::fclose(f);
@@ -1847,7 +1945,8 @@ int64_t tdpd_current_step(const tdpd_sys *s) { return s ? s->step : -1; }
 int tdpd_launches_per_step(const tdpd_sys *s)
 {
     if (!s) return 0;
-    return (int)step_kernels(s).size();
+    // the half shell's pair entry is two launches (k_pair, k_pair_finish)
+    return (int)step_kernels(s).size() + (s->committed && s->half ? 1 : 0);
 }
 
 const char *tdpd_last_error(const tdpd_sys *s) { return s ? s->err.c_str() : g_err.c_str(); }

@@ -94,7 +94,7 @@ __global__ void k_bin_next(Buffers b, const RepParams *__restrict__ reps, int n,
 }
 
 // One thread per pair lane.
-template <int LPP, int M>
+template <int LPP, int M, bool HALF>
 __global__ void __launch_bounds__(128) k_list_build(ListArgs A)
 {
     pdl_enter();
@@ -105,7 +105,11 @@ __global__ void __launch_bounds__(128) k_list_build(ListArgs A)
     const float4 pi = A.pos[i];
     const int rep = wbits(A.vel[i].w);
     if (!A.rb[rep]) return;
-    build_lane<LPP, M>(A, gt, i, sub, pi, rep);
+    if (A.quar && A.quar[rep]) {                      // quarantined: an empty list
+        A.nlc[gt] = 0;
+        return;
+    }
+    build_lane<LPP, M, HALF>(A, gt, i, sub, pi, rep);
 }
 
 void launch_rebuild_decide(const uint32_t *disp, uint32_t *disp_clear, uint32_t *rb, const RepParams *reps,
@@ -121,29 +125,36 @@ void launch_bin_next(const Buffers &b, const RepParams *reps, int n, int *count,
     launch_pdl(k_bin_next, std::max(1, (n + 255) / 256), 256, st, b, reps, n, count, tile_sum, cellrank, any, d);
 }
 
-void launch_list_build(const ListArgs &a, cudaStream_t st)
+template <bool HALF>
+static void launch_list_build_h(const ListArgs &a, int g, cudaStream_t st)
 {
-    if (a.n <= 0) return;
-    const int g = (int)(((long)a.n * a.lpp + 127) / 128);
     if (a.m2) {
         switch (a.lpp) {
-        case 1: launch_pdl(k_list_build<1, 2>, g, 128, st, a); break;
-        case 2: launch_pdl(k_list_build<2, 2>, g, 128, st, a); break;
-        case 4: launch_pdl(k_list_build<4, 2>, g, 128, st, a); break;
-        case 8: launch_pdl(k_list_build<8, 2>, g, 128, st, a); break;
-        case 16: launch_pdl(k_list_build<16, 2>, g, 128, st, a); break;
-        default: launch_pdl(k_list_build<32, 2>, g, 128, st, a); break;
+        case 1: launch_pdl(k_list_build<1, 2, HALF>, g, 128, st, a); break;
+        case 2: launch_pdl(k_list_build<2, 2, HALF>, g, 128, st, a); break;
+        case 4: launch_pdl(k_list_build<4, 2, HALF>, g, 128, st, a); break;
+        case 8: launch_pdl(k_list_build<8, 2, HALF>, g, 128, st, a); break;
+        case 16: launch_pdl(k_list_build<16, 2, HALF>, g, 128, st, a); break;
+        default: launch_pdl(k_list_build<32, 2, HALF>, g, 128, st, a); break;
         }
         return;
     }
     switch (a.lpp) {
-    case 1: launch_pdl(k_list_build<1, 0>, g, 128, st, a); break;
-    case 2: launch_pdl(k_list_build<2, 0>, g, 128, st, a); break;
-    case 4: launch_pdl(k_list_build<4, 0>, g, 128, st, a); break;
-    case 8: launch_pdl(k_list_build<8, 0>, g, 128, st, a); break;
-    case 16: launch_pdl(k_list_build<16, 0>, g, 128, st, a); break;
-    default: launch_pdl(k_list_build<32, 0>, g, 128, st, a); break;
+    case 1: launch_pdl(k_list_build<1, 0, HALF>, g, 128, st, a); break;
+    case 2: launch_pdl(k_list_build<2, 0, HALF>, g, 128, st, a); break;
+    case 4: launch_pdl(k_list_build<4, 0, HALF>, g, 128, st, a); break;
+    case 8: launch_pdl(k_list_build<8, 0, HALF>, g, 128, st, a); break;
+    case 16: launch_pdl(k_list_build<16, 0, HALF>, g, 128, st, a); break;
+    default: launch_pdl(k_list_build<32, 0, HALF>, g, 128, st, a); break;
     }
+}
+
+void launch_list_build(const ListArgs &a, cudaStream_t st)
+{
+    if (a.n <= 0) return;
+    const int g = (int)(((long)a.n * a.lpp + 127) / 128);
+    if (a.half) launch_list_build_h<true>(a, g, st);
+    else launch_list_build_h<false>(a, g, st);
 }
 
 }  // namespace tdpd

@@ -77,9 +77,12 @@ __device__ __forceinline__ float3 pair_force(const RepParams &P, const LaneInfo 
 }
 
 // Evaluate queue entries [head, head+n) (n <= 32) and add each result to its
-// owner's accumulator in push order.
+// owner's accumulator in push order; HALF: the partner's share (-f) goes to
+// its fixed-point accumulator.
+template <bool HALF>
 __device__ __forceinline__ void drain(WarpSmem &W, int head, int n, const RepParams *__restrict__ reps,
-                                      const float4 *__restrict__ vt, uint32_t step_ctr, int lane)
+                                      const float4 *__restrict__ vt, uint32_t step_ctr, int lane,
+                                      long long *accF, uint32_t *err)
 {
     const bool act = lane < n;
     int owner = 32 + lane;
@@ -89,6 +92,12 @@ __device__ __forceinline__ void drain(WarpSmem &W, int head, int n, const RepPar
         const LaneInfo I = W.li[owner];
         const float3 f = pair_force(reps[I.rep], I, E, vt, step_ctr);
         W.res[lane] = make_float4(f.x, f.y, f.z, 0.f);
+        if (HALF) {
+            long long *a = accF + 4 * (size_t)E.j;
+            acc_add(a, -f.x, ACC_F_SCALE, ACC_F_LIMIT, err + I.rep);
+            acc_add(a + 1, -f.y, ACC_F_SCALE, ACC_F_LIMIT, err + I.rep);
+            acc_add(a + 2, -f.z, ACC_F_SCALE, ACC_F_LIMIT, err + I.rep);
+        }
     }
     const unsigned same = __match_any_sync(0xffffffffu, owner);
     __syncwarp();
@@ -105,11 +114,109 @@ __device__ __forceinline__ void drain(WarpSmem &W, int head, int n, const RepPar
     __syncwarp();
 }
 
+// The epilogue of particle i (slot i, lane 0 of its LPP lanes) once its
+// pair force (fx, fy, fz) and flux q are complete: membrane and body force,
+// reaction source, non-finite check, corrector, the predicted position of
+// the next step (written for membrane vertices), and either its displacement
+// from the list build (LIST) or its next binning (cell mode).
+template <int NS, bool LIST>
+__device__ __forceinline__ void epilogue(const PairArgs &A, const RepParams &P, int i, float4 pi, float4 vi,
+                                         float4 vo, uint32_t wi, int rep, float fx, float fy, float fz,
+                                         float *q, int &cell, float &disp2)
+{
+    const int ns = NS > 0 ? NS : A.ns;
+    const int ti = (int)(wi >> 24);
+    const int bi = wbits(vi.w);
+    const int gi = P.pbase + (int)(wi & ID_MASK);     // load index
+    if (bi >= 0) {
+        const float4 fm = A.fext[gi];
+        fx += fm.x; fy += fm.y; fz += fm.z;
+    }
+    const bool frozen = (P.frozen_mask >> ti) & 1u;
+    if (!frozen) {
+        const float sg = (P.fbody_flip && pi.z >= 0.5f * P.L[2]) ? -1.0f : 1.0f;
+        fx += sg * P.fbody[0];
+        fy += sg * P.fbody[1];
+        fz += sg * P.fbody[2];
+    }
+    if (P.k_react != 0.0f && ((P.react_mask >> ti) & 1u)) {
+        const float rate = P.k_react * A.b.Ct[(size_t)i * ns + P.r_src];
+        for (int s = 0; s < ns; ++s) {
+            if (s == P.r_src) q[s] -= rate;
+            if (s == P.r_dst) q[s] += rate;
+        }
+    }
+    if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(A.err + rep, 1u);
+
+    float4 vn = vo;
+    float *C = A.b.C, *Q = A.b.Q;
+    const float4 fo = A.b.frc[i];
+    if (A.integrate && !frozen) {
+        vn.x = __fmaf_rn(P.hdt, fo.x + fx, vo.x);
+        vn.y = __fmaf_rn(P.hdt, fo.y + fy, vo.y);
+        vn.z = __fmaf_rn(P.hdt, fo.z + fz, vo.z);
+        A.b.vel[i] = vn;
+        for (int s = 0; s < ns; ++s) {
+            const size_t k = (size_t)i * ns + s;
+            C[k] = __fmaf_rn(P.hdt, Q[k] + q[s], C[k]);
+        }
+    }
+    const float4 fn = make_float4(fx, fy, fz, 0.0f);
+    A.b.frc[i] = fn;
+    for (int s = 0; s < ns; ++s) Q[(size_t)i * ns + s] = q[s];
+
+    float3 rn = make_float3(pi.x, pi.y, pi.z);
+    float4 vtn = vn;
+    if (!frozen) {
+        bool flip;
+        rn = predict_pos(P, pi, vn, fn, flip);
+        if (flip) { vtn.x = -vtn.x; vtn.y = -vtn.y; vtn.z = -vtn.z; }
+        vtn.x = __fmaf_rn(P.ldt, fn.x, vtn.x);
+        vtn.y = __fmaf_rn(P.ldt, fn.y, vtn.y);
+        vtn.z = __fmaf_rn(P.ldt, fn.z, vtn.z);
+    }
+    if (bi >= 0) {
+        // the next step's membrane kernels start from these (the same
+        // arithmetic as the predictor of the gather), before the sort
+        A.mx[gi] = make_float4(rn.x, rn.y, rn.z, 0.0f);
+        A.mv[gi] = vtn;
+    }
+    if constexpr (LIST) {
+        // displacement of the next position from the list build
+        const float4 xb = A.xb[i];
+        float ex = rn.x - xb.x, ey = rn.y - xb.y, ez = rn.z - xb.z;
+        ex = __fmaf_rn(-P.L[0], rintf(ex * P.inv_L[0]), ex);
+        ey = __fmaf_rn(-P.L[1], rintf(ey * P.inv_L[1]), ey);
+        ez = __fmaf_rn(-P.L[2], rintf(ez * P.inv_L[2]), ez);
+        disp2 = ex * ex + ey * ey + ez * ez;
+    } else {
+        cell = cell_of(P, rn.x, rn.y, rn.z);
+        const int rank = atomicAdd(A.count + cell, 1);
+        A.cellrank[i] = make_int2(cell, rank);
+    }
+}
+
+// Largest squared displacement per replica (non-negative floats order like
+// their bit patterns); one atomic per warp when the warp holds one replica.
+// Every lane of the warp calls it; mine: this lane reports disp2.
+__device__ __forceinline__ void record_displacement(uint32_t *disp_next, int rep, float disp2, bool mine, int lane)
+{
+    const uint32_t bits = __float_as_uint(disp2);
+    const int rep0 = __shfl_sync(0xffffffffu, rep, 0);
+    if (__all_sync(0xffffffffu, rep == rep0)) {
+        const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
+        if (lane == 0) atomicMax(disp_next + rep0, mx);
+    } else if (mine) {
+        atomicMax(disp_next + rep, bits);
+    }
+}
+
 }  // namespace
 
-template <int NS, int LPP, bool LIST>
+template <int NS, int LPP, bool LIST, bool HALF>
 __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
 {
+    static_assert(LIST || !HALF, "the half shell needs neighbour lists");
     pdl_enter();
     __shared__ WarpSmem smem[4];
     const int ns = NS > 0 ? NS : A.ns;
@@ -131,6 +238,11 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
     const float4 vo = A.b.vel[ic];
     const int rep = wbits(vo.w);
     const RepParams &P = A.reps[rep];
+    // a quarantined replica (a non-finite force or an overflowed list in an
+    // earlier evaluation) is neither evaluated nor moved; its particles keep
+    // their slots and, in cell mode, are binned where they are
+    const bool held = valid && A.quar && A.quar[rep] != 0u;
+    const bool live = valid && !held;
     const uint32_t wi = (uint32_t)wbits(pi.w);
     const int ti = (int)(wi >> 24);
     const int T = P.ntypes;
@@ -171,9 +283,9 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
     int qhead = 0, qcount = 0;
     // one candidate j at separation (dx, dy, dz) from i, with its id/type
     // bits wj and first concentration cj0 loaded
-    auto consider = [&](bool live, int j, float dx, float dy, float dz, uint32_t wj, float cj0) {
+    auto consider = [&](bool in_range, int j, float dx, float dy, float dz, uint32_t wj, float cj0) {
         const float r2 = dx * dx + dy * dy + dz * dz;
-        const bool near = live && r2 > 0.0f;
+        const bool near = in_range && r2 > 0.0f;
         // flux without a branch: the terms of candidates outside r_cc (or of
         // dead lanes) are computed and dropped by the select
         const bool inc = near && r2 < rcc2;
@@ -186,13 +298,20 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
             kap = tj == 1 ? kr[1] : kap;
             kap = tj == 2 ? kr[2] : kap;
             kap = tj == 3 ? kr[3] : kap;
-            const float qn = q[0] - kap * wdc * (ci[0] - cj0);
+            const float qd = kap * wdc * (ci[0] - cj0);
+            const float qn = q[0] - qd;
             q[0] = inc ? qn : q[0];
+            if (HALF && inc) acc_add(A.accQ + j, qd, ACC_Q_SCALE, ACC_Q_LIMIT, A.err + rep);
         } else if (inc) {
             const float *kap = kap_row + tj * ns;
-            q[0] -= kap[0] * wdc * (ci[0] - cj0);
-            for (int s = 1; s < ns; ++s)
-                q[s] -= kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
+            const float qd0 = kap[0] * wdc * (ci[0] - cj0);
+            q[0] -= qd0;
+            if (HALF) acc_add(A.accQ + (size_t)j * ns, qd0, ACC_Q_SCALE, ACC_Q_LIMIT, A.err + rep);
+            for (int s = 1; s < ns; ++s) {
+                const float qd = kap[s] * wdc * (ci[s] - Ct[(size_t)j * ns + s]);
+                q[s] -= qd;
+                if (HALF) acc_add(A.accQ + (size_t)j * ns + s, qd, ACC_Q_SCALE, ACC_Q_LIMIT, A.err + rep);
+            }
             if (NS == 0 && P.qr_coef > 0.0f) {
                 // random flux (Eq. 7): eps w_RC zeta / sqrt(dt), eps^2 =
                 // m_s^2 kappa rho (C_i + C_j), w_RC = w_DC^(1/2) (Eq. 8); one
@@ -205,7 +324,9 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
                     if ((s & 1) == 0)
                         z = normal2(pair_bits(idi, idj, P.seed_lo, P.seed_hi, step_ctr + P.step0, 6u + (uint32_t)(s >> 1)));
                     const float cs = ci[s] + (s == 0 ? cj0 : Ct[(size_t)j * ns + s]);
-                    q[s] += amp * sqrtf(fmaxf(kap[s] * cs, 0.0f)) * ((s & 1) ? z.y : z.x);
+                    const float qr = amp * sqrtf(fmaxf(kap[s] * cs, 0.0f)) * ((s & 1) ? z.y : z.x);
+                    q[s] += qr;
+                    if (HALF) acc_add(A.accQ + (size_t)j * ns + s, -qr, ACC_Q_SCALE, ACC_Q_LIMIT, A.err + rep);
                 }
             }
         }
@@ -220,7 +341,7 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
         qcount += __popc(bal);
         if (qcount >= 32) {
             __syncwarp();
-            drain(W, qhead, 32, A.reps, vt, step_ctr, lane);
+            drain<HALF>(W, qhead, 32, A.reps, vt, step_ctr, lane, A.accF, A.err);
             qhead = (qhead + 32) & (QCAP - 1);
             qcount -= 32;
         }
@@ -233,17 +354,17 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
             // read by the lane that owns them, so no other thread waits);
             // the kernels for more species keep the separate list build
             // (the build's registers would cost them more than the launch)
-            if (A.rb && valid && A.rb[rep]) {
+            if (A.rb && live && A.rb[rep]) {
                 ListArgs L{};
                 L.pos = pos; L.vel = A.b.vel; L.reps = A.reps; L.cell_start = A.cell_start; L.rb = A.rb;
                 L.nl = A.nl_w; L.nlc = A.nlc_w; L.xb = A.xb_w; L.err = A.err; L.n = A.n; L.lpp = LPP; L.cap = A.cap;
-                if (A.m2) build_lane<LPP, 2>(L, gt, i, sub, pi, rep);
-                else build_lane<LPP, 0>(L, gt, i, sub, pi, rep);
+                if (A.m2) build_lane<LPP, 2, HALF>(L, gt, i, sub, pi, rep);
+                else build_lane<LPP, 0, HALF>(L, gt, i, sub, pi, rep);
             }
         }
         // (plain loads: on a rebuild step this thread has just written them)
         const int *nl = A.nl + (size_t)(gt >> 5) * A.cap * 32 + (gt & 31);
-        const int cnt = valid ? A.nlc[gt] : 0;
+        const int cnt = live ? A.nlc[gt] : 0;
         const int nit = __reduce_max_sync(0xffffffffu, cnt);
         const float Lx = P.L[0], Ly = P.L[1], Lz = P.L[2];
         const float iLx = P.inv_L[0], iLy = P.inv_L[1], iLz = P.inv_L[2];
@@ -303,11 +424,11 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
         // rows are split round-robin over the LPP lanes of the particle; the
         // loop trip counts are warp-uniform (maxima over the warp)
         const int kmax = (nrow + LPP - 1) / LPP;
-        const int kw = __reduce_max_sync(0xffffffffu, valid ? kmax : 0);
+        const int kw = __reduce_max_sync(0xffffffffu, live ? kmax : 0);
         for (int k = 0; k < kw; ++k) {
             const int row = sub + k * LPP;
             RowSeg g = {{0, 0}, {0, 0}, 0.f, 0.f, 0.f};
-            if (valid && row < nrow) stencil_row(P, cs, pi, cx, cy, cz, row, oy, oz, eps, rtrim2, g);
+            if (live && row < nrow) stencil_row(P, cs, pi, cx, cy, cz, row, oy, oz, eps, rtrim2, g);
             const float py = pi.y + g.sy, pz = pi.z + g.sz;
 #pragma unroll
             for (int sg = 0; sg < 2; ++sg) {
@@ -342,7 +463,7 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
     }
     if (qcount > 0) {
         __syncwarp();
-        drain(W, qhead, qcount, A.reps, vt, step_ctr, lane);
+        drain<HALF>(W, qhead, qcount, A.reps, vt, step_ctr, lane, A.accF, A.err);
     }
     __syncwarp();
     const float4 fa = W.acc[lane];
@@ -357,107 +478,100 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
     }
     int cell = -1;
     float disp2 = 0.0f;
-    if (valid && sub == 0) {
-        // ---- epilogue: membrane force, sources, corrector, next binning
-        const int bi = wbits(vi.w);
-        const int gi = P.pbase + (int)(wi & ID_MASK);     // load index
-        if (bi >= 0) {
-            const float4 fm = A.fext[gi];
-            fx += fm.x; fy += fm.y; fz += fm.z;
-        }
-        const bool frozen = (P.frozen_mask >> ti) & 1u;
-        if (!frozen) {
-            const float sg = (P.fbody_flip && pi.z >= 0.5f * P.L[2]) ? -1.0f : 1.0f;
-            fx += sg * P.fbody[0];
-            fy += sg * P.fbody[1];
-            fz += sg * P.fbody[2];
-        }
-        if (P.k_react != 0.0f && ((P.react_mask >> ti) & 1u)) {
-            const float rate = P.k_react * Ct[(size_t)i * ns + P.r_src];
-            for (int s = 0; s < ns; ++s) {
-                if (s == P.r_src) q[s] -= rate;
-                if (s == P.r_dst) q[s] += rate;
-            }
-        }
-        if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(A.err + rep, 1u);
-
-        float4 vn = vo;
-        float *C = A.b.C, *Q = A.b.Q;
-        const float4 fo = A.b.frc[i];
-        if (A.integrate && !frozen) {
-            vn.x = __fmaf_rn(P.hdt, fo.x + fx, vo.x);
-            vn.y = __fmaf_rn(P.hdt, fo.y + fy, vo.y);
-            vn.z = __fmaf_rn(P.hdt, fo.z + fz, vo.z);
-            A.b.vel[i] = vn;
-            for (int s = 0; s < ns; ++s) {
-                const size_t k = (size_t)i * ns + s;
-                C[k] = __fmaf_rn(P.hdt, Q[k] + q[s], C[k]);
-            }
-        }
-        const float4 fn = make_float4(fx, fy, fz, 0.0f);
-        A.b.frc[i] = fn;
-        for (int s = 0; s < ns; ++s) Q[(size_t)i * ns + s] = q[s];
-
-        float3 rn = make_float3(pi.x, pi.y, pi.z);
-        float4 vtn = vn;
-        if (!frozen) {
-            bool flip;
-            rn = predict_pos(P, pi, vn, fn, flip);
-            if (flip) { vtn.x = -vtn.x; vtn.y = -vtn.y; vtn.z = -vtn.z; }
-            vtn.x = __fmaf_rn(P.ldt, fn.x, vtn.x);
-            vtn.y = __fmaf_rn(P.ldt, fn.y, vtn.y);
-            vtn.z = __fmaf_rn(P.ldt, fn.z, vtn.z);
-        }
-        if (bi >= 0) {
-            // the next step's membrane kernels start from these (the same
-            // arithmetic as the predictor of the gather), before the sort
-            A.mx[gi] = make_float4(rn.x, rn.y, rn.z, 0.0f);
-            A.mv[gi] = vtn;
-        }
-        if constexpr (LIST) {
-            // displacement of the next position from the list build
-            const float4 xb = A.xb[i];
-            float ex = rn.x - xb.x, ey = rn.y - xb.y, ez = rn.z - xb.z;
-            ex = __fmaf_rn(-P.L[0], rintf(ex * P.inv_L[0]), ex);
-            ey = __fmaf_rn(-P.L[1], rintf(ey * P.inv_L[1]), ey);
-            ez = __fmaf_rn(-P.L[2], rintf(ez * P.inv_L[2]), ez);
-            disp2 = ex * ex + ey * ey + ez * ez;
-        } else {
-            cell = cell_of(P, rn.x, rn.y, rn.z);
+    if constexpr (!LIST) {
+        if (held && sub == 0) {
+            cell = cell_of(P, pi.x, pi.y, pi.z);
             const int rank = atomicAdd(A.count + cell, 1);
             A.cellrank[i] = make_int2(cell, rank);
         }
     }
-    if constexpr (LIST) {
-        // largest squared displacement per replica (non-negative floats order
-        // like their bit patterns); one atomic per warp when it has one replica
-        const uint32_t bits = __float_as_uint(disp2);
-        const int rep0 = __shfl_sync(0xffffffffu, rep, 0);
-        if (__all_sync(0xffffffffu, rep == rep0)) {
-            const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
-            if (lane == 0) atomicMax(A.disp_next + rep0, mx);
-        } else if (valid && sub == 0) {
-            atomicMax(A.disp_next + rep, bits);
+    if (live && sub == 0) {
+        if constexpr (HALF) {
+            // the own sums; k_pair_finish adds the partners' shares and
+            // applies the epilogue
+            A.fown[i] = make_float4(fx, fy, fz, 0.0f);
+            for (int s = 0; s < ns; ++s) A.qown[(size_t)i * ns + s] = q[s];
+        } else {
+            epilogue<NS, LIST>(A, P, i, pi, vi, vo, wi, rep, fx, fy, fz, q, cell, disp2);
         }
+    }
+    if constexpr (HALF) {
+    } else if constexpr (LIST) {
+        record_displacement(A.disp_next, rep, disp2, valid && sub == 0, lane);
     } else {
         add_tile_count(A.tile_sum, cell);
+    }
+}
+
+// Half-shell list mode, after k_pair: each particle's force and flux are its
+// own sums plus the partners' shares from the fixed-point accumulators (exact
+// integer sums, converted once); the accumulators are cleared for the next
+// evaluation and the epilogue follows. One thread per particle.
+template <int NS>
+__global__ void __launch_bounds__(256) k_pair_finish(PairArgs A)
+{
+    pdl_enter();
+    const int ns = NS > 0 ? NS : A.ns;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < A.n;
+    const int ic = valid ? i : 0;
+    const float4 vo = A.b.vel[ic];
+    const int rep = wbits(vo.w);
+    float disp2 = 0.0f;
+    if (valid) {
+        const RepParams &P = A.reps[rep];
+        long long *af = A.accF + 4 * (size_t)i;
+        const longlong2 a01 = *reinterpret_cast<const longlong2 *>(af);
+        const long long a2 = af[2];
+        *reinterpret_cast<longlong2 *>(af) = make_longlong2(0, 0);
+        af[2] = 0;
+        float q[NS > 0 ? NS : MAXS];
+        for (int s = 0; s < ns; ++s) {
+            const size_t k = (size_t)i * ns + s;
+            q[s] = A.qown[k] + __ll2float_rn(A.accQ[k]) * ACC_Q_UNIT;
+            A.accQ[k] = 0;
+        }
+        if (!(A.quar && A.quar[rep] != 0u)) {
+            const float4 fo = A.fown[i];
+            const float fx = fo.x + __ll2float_rn(a01.x) * ACC_F_UNIT;
+            const float fy = fo.y + __ll2float_rn(a01.y) * ACC_F_UNIT;
+            const float fz = fo.z + __ll2float_rn(a2) * ACC_F_UNIT;
+            const float4 pi = A.b.pos[i];
+            int cell = -1;
+            epilogue<NS, true>(A, P, i, pi, A.b.vt[i], vo, (uint32_t)wbits(pi.w), rep, fx, fy, fz, q, cell, disp2);
+        }
+    }
+    record_displacement(A.disp_next, rep, disp2, valid, lane);
+}
+
+template <int NS, bool LIST, bool HALF>
+static void launch_lanes(const PairArgs &a, cudaStream_t st)
+{
+    const int t = 128;
+    const long threads = (long)a.n * a.lpp;
+    const int g = (int)((threads + t - 1) / t);
+    switch (a.lpp) {
+    case 1: launch_pdl(k_pair<NS, 1, LIST, HALF>, g, t, st, a); break;
+    case 2: launch_pdl(k_pair<NS, 2, LIST, HALF>, g, t, st, a); break;
+    case 4: launch_pdl(k_pair<NS, 4, LIST, HALF>, g, t, st, a); break;
+    case 8: launch_pdl(k_pair<NS, 8, LIST, HALF>, g, t, st, a); break;
+    case 16: launch_pdl(k_pair<NS, 16, LIST, HALF>, g, t, st, a); break;
+    default: launch_pdl(k_pair<NS, 32, LIST, HALF>, g, t, st, a); break;
     }
 }
 
 template <int NS, bool LIST>
 static void launch_ns(const PairArgs &a, cudaStream_t st)
 {
-    const int t = 128;
-    const long threads = (long)a.n * a.lpp;
-    const int g = (int)((threads + t - 1) / t);
-    switch (a.lpp) {
-    case 1: launch_pdl(k_pair<NS, 1, LIST>, g, t, st, a); break;
-    case 2: launch_pdl(k_pair<NS, 2, LIST>, g, t, st, a); break;
-    case 4: launch_pdl(k_pair<NS, 4, LIST>, g, t, st, a); break;
-    case 8: launch_pdl(k_pair<NS, 8, LIST>, g, t, st, a); break;
-    case 16: launch_pdl(k_pair<NS, 16, LIST>, g, t, st, a); break;
-    default: launch_pdl(k_pair<NS, 32, LIST>, g, t, st, a); break;
+    if constexpr (LIST) {
+        if (a.half) {
+            launch_lanes<NS, true, true>(a, st);
+            launch_pdl(k_pair_finish<NS>, (a.n + 255) / 256, 256, st, a);
+            return;
+        }
     }
+    launch_lanes<NS, LIST, false>(a, st);
 }
 
 void launch_pair(const PairArgs &a, cudaStream_t st)

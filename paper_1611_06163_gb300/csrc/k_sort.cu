@@ -107,11 +107,16 @@ __global__ void k_rank_gather(Buffers cur, Buffers nxt, const RepParams *__restr
                               const int2 *__restrict__ keys, const int2 *__restrict__ cellrank,
                               const int *__restrict__ cell_start, int *inv, int n, int ns_rt,
                               int predict, const uint32_t *__restrict__ rb, int n_rep, int *tile_zero,
-                              int n_tiles)
+                              int n_tiles, Quarantine Qa)
 {
     pdl_enter();
     const int ns = NS > 0 ? NS : ns_rt;
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    // the quarantine of this step: every replica whose last force evaluation
+    // set its status word (the word does not change before this step's pair
+    // kernel, which reads quar instead)
+    if (Qa.quar)
+        for (int r = d; r < Qa.n_reps; r += gridDim.x * blockDim.x) Qa.quar[r] = Qa.err[r] != 0u ? 1u : 0u;
     const bool any = !rb || rb[n_rep] != 0u;
     if (tile_zero && any)
         for (int t = d; t < n_tiles; t += gridDim.x * blockDim.x) tile_zero[t] = 0;
@@ -145,8 +150,9 @@ __global__ void k_rank_gather(Buffers cur, Buffers nxt, const RepParams *__restr
         const RepParams &P = reps[r];
         const int type = (int)((uint32_t)wbits(p.w) >> 24);
         const bool frozen = (P.frozen_mask >> type) & 1u;
+        const bool held = Qa.err && Qa.err[r] != 0u;     // quarantined: not moved
         float4 vtn = make_float4(v.x, v.y, v.z, vt.w);
-        pred = predict && !frozen;
+        pred = predict && !frozen && !held;
         ldt = P.ldt;
         if (pred) {
             bool flip;
@@ -212,14 +218,14 @@ void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *ce
 void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams *reps,
                         const int2 *keys, const int2 *cellrank, const int *cell_start, int *inv,
                         int n, int ns, int predict, cudaStream_t st, const uint32_t *rb, int n_rep,
-                        int *tile_zero, int n_tiles)
+                        int *tile_zero, int n_tiles, const Quarantine &q)
 {
     if (n <= 0) return;
     const int g = nblk(n, 256);
     switch (ns) {
-    case 1: launch_pdl(k_rank_gather<1>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles); break;
-    case 2: launch_pdl(k_rank_gather<2>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles); break;
-    default: launch_pdl(k_rank_gather<0>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles); break;
+    case 1: launch_pdl(k_rank_gather<1>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles, q); break;
+    case 2: launch_pdl(k_rank_gather<2>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles, q); break;
+    default: launch_pdl(k_rank_gather<0>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles, q); break;
     }
 }
 

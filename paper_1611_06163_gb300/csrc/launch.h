@@ -45,6 +45,7 @@ struct PairArgs {
     int2 *cellrank;              // [N] (cell, rank) of the next binning
     int *tile_sum;               // [n_tiles] particles per scan tile of the next binning
     uint32_t *err;               // [n_rep] status bits
+    const uint32_t *quar;        // [n_rep] nonzero: the replica is quarantined (null: none)
     const uint32_t *step_ctr;    // absolute step of this evaluation
     int n;                       // particles (slots)
     int ns;                      // species (runtime value for the generic path)
@@ -65,6 +66,17 @@ struct PairArgs {
     int *nl_w, *nlc_w;
     float4 *xb_w;
     int m2;
+    // half-shell list mode (half != 0; the lists hold the upper half of the
+    // stencil, every unordered pair once): the pair kernel adds each pair's
+    // share for the partner into fixed-point accumulators and writes each
+    // particle's own sums; k_pair_finish adds the two, applies the epilogue
+    // (membrane and body force, sources, corrector, displacement) and clears
+    // the accumulators
+    int half;
+    long long *accF;             // [n][4] partner forces, units of 2^-32 (zero between steps)
+    long long *accQ;             // [n * ns] partner fluxes, units of 2^-40 (zero between steps)
+    float4 *fown;                // [n] own force sums
+    float *qown;                 // [n * ns] own flux sums
 };
 
 // Neighbour-list build over the cell stencil of radius sqrt(rlist2).
@@ -73,12 +85,14 @@ struct ListArgs {
     const RepParams *reps;
     const int *cell_start;
     const uint32_t *rb;          // [n_rep + 1] rebuild flags, rb[n_rep]: any
+    const uint32_t *quar;        // [n_rep] nonzero: quarantined, no list (null: none)
     int n_rep;
     int *nl, *nlc;
     float4 *xb;
     uint32_t *err;
     int n, lpp, cap;             // cap == 0: count only
     int m2;                      // every replica has the stencil half-width 2
+    int half;                    // upper half of the stencil only (half-shell lists)
 };
 
 struct MemArgs {
@@ -121,10 +135,20 @@ void launch_scan(int *count, int *cell_start, int n_tiles, const int *tile_read,
                  uint32_t *step_ctr, int inc, cudaStream_t st, const uint32_t *any = nullptr);
 void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *cell_start,
                          int2 *keys, int n, cudaStream_t st, const uint32_t *any = nullptr);
+// Quarantine (optional): err [n_reps] is each replica's status word from the
+// last force evaluation; a replica with a nonzero word is not moved (no
+// predictor) and quar[r] = (err[r] != 0) tells the kernels after the gather
+// to skip it.
+struct Quarantine {
+    const uint32_t *err = nullptr;
+    uint32_t *quar = nullptr;
+    int n_reps = 0;
+};
 void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams *reps,
                         const int2 *keys, const int2 *cellrank, const int *cell_start, int *inv,
                         int n, int ns, int predict, cudaStream_t st,
-                        const uint32_t *rb = nullptr, int n_rep = 0, int *tile_zero = nullptr, int n_tiles = 0);
+                        const uint32_t *rb = nullptr, int n_rep = 0, int *tile_zero = nullptr, int n_tiles = 0,
+                        const Quarantine &q = Quarantine{});
 // list mode: rb[n_rep + 1] rebuild flags; without any rebuild every slot keeps
 // its particle, a replica that does not rebuild keeps its slots; tile_zero
 // (n_tiles ints) is cleared after a rebuild
@@ -158,6 +182,9 @@ void launch_observables(const Buffers &b, const RepParams *reps, const int4 *chu
 // (pair_coef [T*T*3] = a, gamma, sigma; kappa [T*T*S]) for a given cell grid.
 RepParams build_rep_params(const tdpd_config &c, const float *pair_coef, const float *kappa,
                            const int nc[3], int m, int cell_base, int pbase, int n);
+// Validity of a replica configuration: false when valid, else true with the
+// reason in msg (the checks of tdpd_create).
+bool config_error(const tdpd_config &c, char *msg, size_t len);
 // Message returned by tdpd_last_error(NULL) on this thread.
 void set_thread_error(const char *msg);
 

@@ -14,7 +14,17 @@ namespace tdpd {
 // 0, the build position xb[i]. M: the stencil half-width when it is known at
 // compile time (2, the default cell size), else 0 (read per replica). Used by
 // k_list_build and, on rebuild steps, by the pair kernel for its own lanes.
-template <int LPP, int M>
+//
+// HALF: only the upper half of the stencil, so that every unordered pair is
+// listed once. A cell's offset (dx, dy, dz) from particle i's cell has one
+// representative in [-m, m]^3 (a periodic axis holds at least 2m + 1 cells),
+// and the pair belongs to the side from which that offset is upper: rows
+// with dz > 0, or dz = 0 and dy > 0 (the rows after the home row), and in
+// the home row the cells with dx > 0 and, in i's own cell, the slots after
+// i. Cells of a row are consecutive slots, so the home row's upper part is
+// the slot range after i up to the row's end, plus the segment that wraps
+// around to the right.
+template <int LPP, int M, bool HALF = false>
 __device__ __forceinline__ void build_lane(const ListArgs &A, int gt, int i, int sub, float4 pi, int rep)
 {
     const RepParams &P = A.reps[rep];
@@ -70,12 +80,21 @@ __device__ __forceinline__ void build_lane(const ListArgs &A, int gt, int i, int
             }
         }
     };
-    for (int row = sub; row < nrow; row += LPP) {
+    for (int row = (HALF ? nrow / 2 : 0) + sub; row < nrow; row += LPP) {
         const int dy = row % width - m, dz = row / width - m;
         RowSeg g = {{0, 0}, {0, 0}, 0.f, 0.f, 0.f};
         if (!stencil_row_d(P, A.cell_start, pi, cx, cy, cz, dy, dz, m, oy, oz, eps, rl2 * 1.0002f, g)) continue;
-        if (dy == 0 && dz == 0) walk(g, std::true_type{});
-        else walk(g, std::false_type{});
+        if (dy == 0 && dz == 0) {
+            if (HALF) {
+                // the home row from the slot after i; a segment that wraps
+                // around to the left (x shift +L) holds only cells with dx < 0
+                g.jb[0] = i + 1;
+                if (g.sx1 > 0.f) g.je[1] = g.jb[1];
+            }
+            walk(g, std::true_type{});
+        } else {
+            walk(g, std::false_type{});
+        }
     }
     A.nlc[gt] = A.cap > 0 ? min(c, A.cap) : c;
     if (A.cap > 0 && c > A.cap) atomicOr(A.err + rep, 2u);

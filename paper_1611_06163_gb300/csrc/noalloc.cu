@@ -11,6 +11,8 @@
 // the GPU can reach host memory, silently use the wrong memory. The device
 // address is obtained once per device with cudaGetSymbolAddress, with that
 // device current, and cached.
+#include <cmath>
+#include <cstdio>
 #include <mutex>
 
 #include "launch.h"
@@ -71,7 +73,14 @@ __global__ void k_na_pack(RepParams P, int n, int ns, const float *__restrict__ 
     for (int c = g0; c <= NA_C; c += stride) S->cell_start[c] = n;
     for (int t = g0; t < 2 * NA_TILES; t += stride) S->tile_sum[t / NA_TILES][t % NA_TILES] = 0;
     for (int k = g0; k < n; k += stride) {
-        const uint32_t w = (uint32_t)k | ((uint32_t)type[k] << 24);
+        // a type outside [0, n_types) is recorded (the outputs become NaN)
+        // and replaced by type 0, so that no table lookup leaves its range
+        int t = type[k];
+        if (t < 0 || t >= P.ntypes) {
+            atomicOr(&S->err[1], 4u);
+            t = 0;
+        }
+        const uint32_t w = (uint32_t)k | ((uint32_t)t << 24);
         S->pos[0][k] = make_float4(pos[3 * k], pos[3 * k + 1], pos[3 * k + 2], __int_as_float((int)w));
         S->vel[0][k] = make_float4(vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], __int_as_float(0));
         S->vt[0][k] = make_float4(vel[3 * k], vel[3 * k + 1], vel[3 * k + 2], __int_as_float(-1));
@@ -85,16 +94,26 @@ __global__ void k_na_pack(RepParams P, int n, int ns, const float *__restrict__ 
     }
 }
 
+// Clear the input check word of this call (before k_na_pack may set it).
+__global__ void k_na_clear(NoAllocLayout *S)
+{
+    S->err[1] = 0u;
+}
+
+// Load-order outputs; every output is NaN when an input type was out of
+// range or some force came out non-finite (the caller checks the outputs).
 __global__ void k_na_unpack(int n, int ns, const NoAllocLayout *S, float *force, float *flux)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    const bool bad = (S->err[0] | S->err[1]) != 0u;
+    const float nan = __int_as_float(0x7fc00000);
     const int slot = S->inv[k];
     const float4 f = S->frc[1][slot];
-    force[3 * k] = f.x;
-    force[3 * k + 1] = f.y;
-    force[3 * k + 2] = f.z;
-    for (int s = 0; s < ns; ++s) flux[(size_t)k * ns + s] = S->Q[1][(size_t)slot * ns + s];
+    force[3 * k] = bad ? nan : f.x;
+    force[3 * k + 1] = bad ? nan : f.y;
+    force[3 * k + 2] = bad ? nan : f.z;
+    for (int s = 0; s < ns; ++s) flux[(size_t)k * ns + s] = bad ? nan : S->Q[1][(size_t)slot * ns + s];
 }
 
 Buffers buffers(NoAllocLayout *S, int b)
@@ -122,19 +141,26 @@ extern "C" tdpd_status tdpd_pair_forces_noalloc(const tdpd_config *cfg, const fl
     if (n < 1 || n > NA_N) return na_fail(TDPD_EINVAL, "noalloc: particle count must be 1..TDPD_NOALLOC_MAX_PARTICLES");
     if (!pos || !vel || !conc || !type || !force || !flux) return na_fail(TDPD_EINVAL, "noalloc: null device array");
     const tdpd_config &c = *cfg;
-    if (c.n_species < 1 || c.n_species > NA_S) return na_fail(TDPD_EINVAL, "noalloc: n_species must be 1..TDPD_NOALLOC_MAX_SPECIES");
-    if (c.n_types < 1 || c.n_types > TDPD_MAX_TYPES) return na_fail(TDPD_EINVAL, "noalloc: n_types out of range");
-    if (!c.periodic[0] || !c.periodic[1] || !c.periodic[2]) return na_fail(TDPD_EINVAL, "noalloc: the box must be periodic on every axis");
-    if (!(c.dt > 0) || !(c.rc > 0) || !(c.rcc >= 0)) return na_fail(TDPD_EINVAL, "noalloc: need dt > 0, rc > 0, rcc >= 0");
+    {
+        // the checks of tdpd_create, then this entry point's own limits
+        char why[200], msg[240];
+        if (config_error(c, why, sizeof why)) {
+            std::snprintf(msg, sizeof msg, "noalloc: %s", why);
+            return na_fail(TDPD_EINVAL, msg);
+        }
+    }
+    if (c.n_species > NA_S) return na_fail(TDPD_EINVAL, "noalloc: n_species must be 1..TDPD_NOALLOC_MAX_SPECIES");
+    if (!c.periodic[2]) return na_fail(TDPD_EINVAL, "noalloc: the box must be periodic on every axis");
     const int m = c.cells_per_cutoff > 0 ? c.cells_per_cutoff : 2;
-    if (m > 3) return na_fail(TDPD_EINVAL, "noalloc: cells_per_cutoff must be 0..3");
     const float rcut = c.rc > c.rcc ? c.rc : c.rcc;
     int nc[3];
     long ncell = 1;
     for (int k = 0; k < 3; ++k) {
         if (!(c.L[k] > 0) || (double)c.L[k] < 3.0 * rcut * 1.0001)
             return na_fail(TDPD_EINVAL, "noalloc: every box edge must hold three cut-offs");
-        nc[k] = (int)((double)c.L[k] * m / ((double)rcut * 1.0001));
+        const double ncd = std::floor((double)c.L[k] * m / ((double)rcut * 1.0001));
+        if (ncd > NA_C) return na_fail(TDPD_EINVAL, "noalloc: the box needs more than TDPD_NOALLOC_MAX_CELLS cells");
+        nc[k] = (int)ncd;
         if (nc[k] < 2 * m + 1) return na_fail(TDPD_EINVAL, "noalloc: too few cells");
         ncell *= nc[k];
     }
@@ -158,6 +184,7 @@ extern "C" tdpd_status tdpd_pair_forces_noalloc(const tdpd_config *cfg, const fl
     const int ns = c.n_species;
     const RepParams P = build_rep_params(c, pair_coef, kappa, nc, m, 0, 0, n);
     cudaStream_t st = (cudaStream_t)stream;
+    k_na_clear<<<1, 1, 0, st>>>(S);
     k_na_pack<<<64, 256, 0, st>>>(P, n, ns, pos, vel, conc, type, step, S);
     const Buffers b0 = buffers(S, 0), b1 = buffers(S, 1);
     const RepParams *dP = &S->params;

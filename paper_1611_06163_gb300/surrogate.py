@@ -12,6 +12,9 @@ to which the Fickian diffusivity of Eq. 9 is proportional).
 Point -> outcomes: mean release rate of species 0 from the membranes
 (fraction of the initial membrane amount per unit time, 0 without
 membranes) and the final mean concentration of the solvent.
+
+A point set carries its box side per point ('L', the batched ensemble's
+cubic boxes of side 8..16) or, without it, the 10^3 box of the quick sweep.
 """
 
 from __future__ import annotations
@@ -21,7 +24,7 @@ import functools
 import numpy as np
 
 import workloads as W
-from workloads.surrogate import init_params, sample_points
+from workloads.surrogate import ensemble_points, init_params, sample_points
 
 from . import binding as bd
 
@@ -34,9 +37,15 @@ def _mesh(diameter):
     return W.biconcave_mesh(500, diameter)
 
 
-def replica(point, k, L=BOX):
-    """Workload of point k: a periodic box of side L at density 3 with the
-    point's number of membranes, permeability, body force and solvent kappa."""
+def _side(point, k):
+    return float(point['L'][k]) if 'L' in point else BOX
+
+
+def replica(point, k):
+    """Workload of point k: a periodic box of the point's side at density 3
+    with its number of membranes (clamped to the box's slots), permeability,
+    body force and solvent kappa."""
+    L = _side(point, k)
     rng = np.random.default_rng(np.random.SeedSequence(int(point['seeds'][k])))
     d = W._base('sweep', (L, L, L), (1, 1, 1), 2, 1, int(point['seeds'][k]), 3.0, dt=W.MEMBRANE_DT)
     d['particles'] = W.fluid_particles(rng, d['L'], 3.0, 1)
@@ -63,9 +72,10 @@ def rbc_volume():
     return float(np.einsum('ij,ij->i', a, np.cross(b, c)).sum() / 6.0)
 
 
-def features(point, idx=None, L=BOX):
+def features(point, idx=None):
     idx = np.arange(len(point['permeability'])) if idx is None else np.asarray(idx)
-    n_rbc = np.minimum(point['n_rbc'][idx], _slots(L))
+    L = np.array([_side(point, int(k)) for k in idx])
+    n_rbc = np.minimum(point['n_rbc'][idx], [_slots(x) for x in L])
     hct = n_rbc * rbc_volume() / L ** 3
     return np.stack([point['permeability'][idx], point['body_force'][idx], hct, point['kappa'][idx]],
                     1).astype(np.float32)
@@ -80,7 +90,7 @@ def _slots(L=BOX):
 def simulate(point, idx, steps, stream_ptr=None):
     """Run the points idx as one batch for `steps` steps; returns outcomes
     (n, 2): release rate, final solvent concentration (NaN for a replica whose
-    status reports a non-finite force)."""
+    status reports a fault: it was quarantined and its outcome is not kept)."""
     idx = np.asarray(idx)
     descs = [replica(point, int(k)) for k in idx]
     hs = [bd.create_from(d) for d in descs]
@@ -90,6 +100,11 @@ def simulate(point, idx, steps, stream_ptr=None):
     try:
         if stream_ptr:
             bd.tdpd_set_stream(batch, stream_ptr)
+        # one lane per particle and the half shell, pinned: a replica then gives
+        # the same bits in any batch, so a point simulated again (a fallback)
+        # reproduces its recorded outcome exactly
+        bd.tdpd_set_lanes(batch, 1)
+        bd.tdpd_set_pair_mode(batch, 2)
         bd.tdpd_commit(batch)
         before = [bd.tdpd_read_observables(batch, r) for r in range(len(descs))]
         bd.tdpd_step(batch, steps)
@@ -143,4 +158,5 @@ def predict_with_fallback(model, point, idx, steps, threshold=0.05):
     return vals, fell
 
 
-__all__ = ['sample_points', 'replica', 'features', 'simulate', 'Surrogate', 'predict_with_fallback']
+__all__ = ['sample_points', 'ensemble_points', 'replica', 'features', 'simulate', 'Surrogate',
+           'predict_with_fallback']

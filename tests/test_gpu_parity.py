@@ -10,7 +10,7 @@ import pytest
 import oracle
 import workloads as W
 from gpu_common import (B, make, normwise, elementwise, wrap_diff, forces_vs_oracle, run_vs_oracle,
-                        TOL_FORCE, TOL_TRAJ)
+                        check_step, check_traj, TOL_FORCE, TOL_EW_STEP)
 from helpers import custom, membrane_only, small_sphere
 
 pytestmark = pytest.mark.gpu
@@ -49,9 +49,7 @@ def test_pair_forces_small_box(ns):
     the last block) against the O(n^2) oracle."""
     d = W.fluid_box(L=6.0, rho=4.0, n_species=ns, seed=11)
     F, Q, Fo, Qo = forces_vs_oracle(d, mode=0)
-    assert normwise(F, Fo) < TOL_FORCE
-    assert normwise(Q, Qo) < TOL_FORCE
-    assert elementwise(F, Fo) < 5e-4
+    check_step(F, Q, Fo, Qo)
 
 
 def test_pair_forces_two_types_and_exponents():
@@ -68,8 +66,7 @@ def test_pair_forces_two_types_and_exponents():
     d['kappa'][0, 1, :] = d['kappa'][1, 0, :] = [0.1, 0.5]
     d['kappa'][1, 1, :] = [2.0, 0.0]
     F, Q, Fo, Qo = forces_vs_oracle(d, mode=0)
-    assert normwise(F, Fo) < TOL_FORCE
-    assert normwise(Q, Qo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
 
 
 def test_fluid_4k_forces_and_trajectory():
@@ -77,11 +74,9 @@ def test_fluid_4k_forces_and_trajectory():
     state after 10 velocity-Verlet steps."""
     d = W.fluid_box()
     F, Q, Fo, Qo = forces_vs_oracle(d, mode=1)
-    assert normwise(F, Fo) < TOL_FORCE
-    assert normwise(Q, Qo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
     err, obs, o, _ = run_vs_oracle(d, 10)
-    for k, v in err.items():
-        assert v < TOL_TRAJ, (k, v, err)
+    check_traj(err, d)
     ob = o.observables()
     assert obs['kT'] == pytest.approx(ob['kT'], rel=1e-4)
     assert np.allclose(obs['momentum'], ob['momentum'], atol=1e-3)
@@ -93,13 +88,11 @@ def test_single_rbc_forces_trajectory_and_fp64_reductions():
     steps, and the FP64 area/volume against the oracle."""
     d = W.single_rbc()
     F, Q, Fo, Qo = forces_vs_oracle(d, mode=1)
-    assert normwise(F, Fo) < TOL_FORCE
-    assert normwise(Q, Qo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
     mem = slice(d['particles']['pos'].shape[0], None)
-    assert normwise(F[mem], Fo[mem]) < TOL_FORCE
+    check_step(F[mem], Q[mem], Fo[mem], Qo[mem], 'membrane vertices')
     err, obs, o, (A, V) = run_vs_oracle(d, 10)
-    for k, v in err.items():
-        assert v < TOL_TRAJ, (k, v, err)
+    check_traj(err, d)
     ob = o.observables()
     assert abs(A[0] - ob['area'][0]) / ob['area'][0] < 1e-6
     assert abs(V[0] - ob['volume'][0]) / ob['volume'][0] < 1e-6
@@ -119,13 +112,13 @@ def test_membrane_forces_alone(theta0):
     d['sigma'][:] = 0.0
     d['kappa'][:] = 0.0
     F, Q, Fo, Qo = forces_vs_oracle(d, mode=1)
-    assert normwise(F, Fo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
     # conservative part alone (kT = 0 removes the random force; velocity zero)
     d2 = membrane_only(u, t, L=20.0, rest=v, kT=0.0, theta0=theta0)
     for k in ('a', 'gamma', 'sigma', 'kappa'):
         d2[k][:] = 0.0
-    F2, _, Fo2, _ = forces_vs_oracle(d2, mode=1)
-    assert normwise(F2, Fo2) < TOL_FORCE
+    F2, Q2, Fo2, Qo2 = forces_vs_oracle(d2, mode=1)
+    check_step(F2, Q2, Fo2, Qo2)
     assert np.abs(F2.astype(np.float64).sum(0)).max() < 1e-4 * np.abs(Fo2).max()
 
 
@@ -143,7 +136,7 @@ def test_membrane_straddling_periodic_boundary():
         x = x - np.floor(x / L) * L
         r[key] = np.minimum(x.astype(np.float32), np.nextafter(L.astype(np.float32), 0))
     F, Q, Fo, Qo = forces_vs_oracle(d, mode=1)
-    assert normwise(F, Fo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
 
 
 def test_edge_positions_and_single_particle():
@@ -161,8 +154,7 @@ def test_edge_positions_and_single_particle():
     pos[120:160, 0] += np.arange(40) * 0.01
     d = custom(pos, rng.normal(0, 1, (n, 3)), rng.random((n, 1)), L=(L, L, L))
     F, Q, Fo, Qo = forces_vs_oracle(d, mode=0)
-    assert normwise(F, Fo) < TOL_FORCE
-    assert normwise(Q, Qo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
     d1 = custom([[1.0, 2.0, 3.0]], [[0.1, 0.2, 0.3]], L=(5.0, 5.0, 5.0), body_force=(0.05, 0.0, -0.01))
     F1, _, Fo1, _ = forces_vs_oracle(d1, mode=0)
     assert np.allclose(F1, Fo1, atol=1e-7)
@@ -202,8 +194,7 @@ def test_deterministic_and_set_state():
             F1, Q1 = bd.tdpd_read_forces(h, 0, 1)
             o = oracle.Oracle(d, mode=1)
             o.set_state(p, v, c, step=7)
-            assert normwise(F1, o.F) < TOL_FORCE
-            assert normwise(Q1, o.Q) < TOL_FORCE
+            check_step(F1, Q1, o.F, o.Q)
             p2, v2, c2 = bd.tdpd_read_state(h, 0, 1)
             assert np.array_equal(p, p2) and np.array_equal(v, v2) and np.array_equal(c, c2)
         bd.tdpd_destroy(h)
@@ -211,18 +202,22 @@ def test_deterministic_and_set_state():
         assert np.array_equal(a, b)
 
 
-def test_batch_equals_replicas_alone():
+@pytest.mark.parametrize('mode', [1, 2])
+def test_batch_equals_replicas_alone(mode):
     """Replicas of uneven size stepped together in one batch give the
-    same bits as each stepped alone."""
+    same bits as each stepped alone (full and half shell)."""
     bd = B()
     reps = W.replica_ensemble(n_rep=5, seed=77, side_lo=8, side_hi=11)
     hs = [bd.create_from(r) for r in reps]
     batch = bd.tdpd_batch_create(hs)
     bd.tdpd_set_lanes(batch, 8)
+    bd.tdpd_set_pair_mode(batch, mode)
     bd.tdpd_step(batch, 6)
+    assert bd.tdpd_pair_mode(batch) == mode
     for k, r in enumerate(reps):
         alone = bd.create_from(r)
         bd.tdpd_set_lanes(alone, 8)
+        bd.tdpd_set_pair_mode(alone, mode)
         bd.tdpd_step(alone, 6)
         a = bd.tdpd_read_state(alone, 0, 1) + bd.tdpd_read_forces(alone, 0, 1)
         b = bd.tdpd_read_state(batch, k, 1) + bd.tdpd_read_forces(batch, k, 1)
@@ -241,8 +236,7 @@ def test_replica_ensemble_matches_oracle():
     reps = W.replica_ensemble(n_rep=3, seed=5, side_lo=10, side_hi=12)
     for r in reps:
         F, Q, Fo, Qo = forces_vs_oracle(r, mode=1)
-        assert normwise(F, Fo) < TOL_FORCE
-        assert normwise(Q, Qo) < TOL_FORCE
+        check_step(F, Q, Fo, Qo)
 
 
 def test_channel_walls_reaction_full_size():
@@ -251,11 +245,9 @@ def test_channel_walls_reaction_full_size():
     force): forces at step 0 and 10 steps against the oracle."""
     d = W.rbc_channel()
     F, Q, Fo, Qo = forces_vs_oracle(d, mode=1)
-    assert normwise(F, Fo) < TOL_FORCE
-    assert normwise(Q, Qo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
     err, obs, o, (A, V) = run_vs_oracle(d, 10)
-    for k, v in err.items():
-        assert v < TOL_TRAJ, (k, v, err)
+    check_traj(err, d)
     ob = o.observables()
     assert np.allclose(A, ob['area'], rtol=1e-6)
     assert np.allclose(V, ob['volume'], rtol=1e-6)
@@ -281,8 +273,7 @@ def test_ensemble_512_sampled_against_oracle():
         for k in sorted(pick):
             F, Q = bd.tdpd_read_forces(batch, k, 1)
             o = oracle.Oracle(reps[k], mode=1)
-            assert normwise(F, o.F) < TOL_FORCE, k
-            assert normwise(Q, o.Q) < TOL_FORCE, k
+            check_step(F, Q, o.F, o.Q, k)
         bd.tdpd_step(batch, 3)
         bd.tdpd_sync(batch)
         assert (bd.tdpd_replica_status(batch) == 0).all()
@@ -290,10 +281,12 @@ def test_ensemble_512_sampled_against_oracle():
         bd.tdpd_destroy(batch)
 
 
-def test_every_lane_count_matches_oracle():
+@pytest.mark.parametrize('mode', [1, 2])
+def test_every_lane_count_matches_oracle(mode):
     """The pair kernel at 1..32 lanes per particle (rows split over the lanes,
-    partial sums combined by a butterfly) gives F(0), Q(0) within the per-step
-    tolerance of the oracle; invalid lane counts are refused."""
+    partial sums combined by a butterfly), with full-shell and with half-shell
+    lists, gives F(0), Q(0) within the per-step tolerance of the oracle;
+    invalid lane counts and pair modes are refused."""
     bd = B()
     d = W.single_rbc(L=10.0, diameter=5.0, seed=31)
     o = oracle.Oracle(d, mode=1)
@@ -302,20 +295,26 @@ def test_every_lane_count_matches_oracle():
         with pytest.raises(bd.TdpdError) as e:
             bd.tdpd_set_lanes(h, bad)
         assert e.value.status == 1 and 'lanes' in str(e.value)
+    for bad in (-1, 3):
+        with pytest.raises(bd.TdpdError) as e:
+            bd.tdpd_set_pair_mode(h, bad)
+        assert e.value.status == 1 and 'pair mode' in str(e.value)
     bd.tdpd_destroy(h)
     for lanes in (1, 2, 4, 8, 16, 32):
         h = bd.create_from(d)
         bd.tdpd_set_lanes(h, lanes)
+        bd.tdpd_set_pair_mode(h, mode)
         bd.tdpd_commit(h)
+        assert bd.tdpd_pair_mode(h) == mode
         F, Q = bd.tdpd_read_forces(h, 0, 1)
         with pytest.raises(bd.TdpdError):
             bd.tdpd_set_lanes(h, 4)                # fixed after commit
         bd.tdpd_destroy(h)
-        assert normwise(F, o.F) < TOL_FORCE, lanes
-        assert normwise(Q, o.Q) < TOL_FORCE, lanes
+        check_step(F, Q, o.F, o.Q, lanes)
 
 
-def test_neighbour_lists_match_cell_mode_and_oracle():
+@pytest.mark.parametrize('mode', [1, 2])
+def test_neighbour_lists_match_cell_mode_and_oracle(mode):
     """Verlet lists (default skin, rebuilt when a particle of the replica has
     moved half the skin) against the cell stencil walked every step (skin 0):
     both match the oracle on F(0), Q(0) and over 40 steps, during which the
@@ -331,10 +330,10 @@ def test_neighbour_lists_match_cell_mode_and_oracle():
     bd.tdpd_destroy(h)
     res = {}
     for skin in (0.0, 0.3):
-        h = bd.create_from(dict(d, skin=skin))
+        h = bd.create_from(dict(d, skin=skin, pair_mode=mode))
         bd.tdpd_commit(h)
         F, Q = bd.tdpd_read_forces(h, 0, 1)
-        assert normwise(F, o.F) < TOL_FORCE and normwise(Q, o.Q) < TOL_FORCE, skin
+        check_step(F, Q, o.F, o.Q, skin)
         with pytest.raises(bd.TdpdError):
             bd.tdpd_set_skin(h, 0.2)                # fixed after commit
         bd.tdpd_step(h, 40)
@@ -363,10 +362,9 @@ def test_lagged_area_volume_matches_oracle():
     d = W.single_rbc(L=10.0, diameter=5.0, seed=51)
     d['membrane']['lagged_av'] = 1
     F, Q, Fo, Qo = forces_vs_oracle(d)
-    assert normwise(F, Fo) < TOL_FORCE and normwise(Q, Qo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
     err, obs, o, (A, V) = run_vs_oracle(d, 10)
-    for k, v in err.items():
-        assert v < TOL_TRAJ, (k, v, err)
+    check_traj(err, d)
     ob = o.observables()
     assert abs(A[0] - ob['area'][0]) / ob['area'][0] < 1e-6
     assert abs(V[0] - ob['volume'][0]) / ob['volume'][0] < 1e-6
@@ -375,37 +373,38 @@ def test_lagged_area_volume_matches_oracle():
     assert abs(A[0] - As[0]) / As[0] < 5e-3 and abs(V[0] - Vs[0]) / Vs[0] < 5e-3
 
 
-def test_ten_species_and_random_flux_match_oracle():
+@pytest.mark.parametrize('mode', [1, 2])
+def test_ten_species_and_random_flux_match_oracle(mode):
     """N_s = 10 with distinct kappa per species (the general kernel), then
     with the random flux of Eq. 7 on: F(0), Q(0) and 10 steps against the
-    oracle; species totals conserved by the random flux on the device."""
+    oracle; species totals conserved by the random flux on the device. Full
+    and half shell."""
     d = W.fluid_box(L=8.0, rho=3.0, n_species=10, seed=61)
+    d['pair_mode'] = mode
     d['kappa'][...] = np.linspace(0.5, 2.0, 10, dtype=np.float32)
     F, Q, Fo, Qo = forces_vs_oracle(d)
-    assert normwise(F, Fo) < TOL_FORCE and normwise(Q, Qo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
     d['random_flux'] = dict(m_s=0.05, rho=3.0)
     F, Q, Fo, Qo = forces_vs_oracle(d)
-    assert normwise(F, Fo) < TOL_FORCE and normwise(Q, Qo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
     Q64 = Q.astype(np.float64)
     assert np.abs(Q64.sum(axis=0)).max() < 1e-5 * np.abs(Q64).sum(axis=0).max()
     err, obs, o, _ = run_vs_oracle(d, 10)
-    for k, v in err.items():
-        assert v < TOL_TRAJ, (k, v, err)
+    check_traj(err, d)
     ob = o.observables()
     assert np.allclose(obs['mass'], ob['mass'], rtol=1e-6)
 
 
 def test_cylinder_wall_matches_oracle():
-    """The Dirichlet cylinder of Sec. 4.1 at small size (R = 3, 1582
+    """The Dirichlet cylinder of Sec. 4.2 at small size (R = 3, 1582
     particles): frozen reservoir shell at C = 1, bounce-back at the cylinder.
     Forces at step 0 and 10 steps against the oracle; after 200 steps on the
     device the fluid is inside R and the shell still holds C = 1."""
     d = W.cylinder_diffusion(R=3.0, Lx=6.0, seed=33)
     F, Q, Fo, Qo = forces_vs_oracle(d)
-    assert normwise(F, Fo) < TOL_FORCE and normwise(Q, Qo) < TOL_FORCE
+    check_step(F, Q, Fo, Qo)
     err, obs, o, _ = run_vs_oracle(d, 10)
-    for k, v in err.items():
-        assert v < TOL_TRAJ, (k, v, err)
+    check_traj(err, d)
     bd = B()
     h = bd.create_from(d)
     bd.tdpd_commit(h)
@@ -540,13 +539,20 @@ def test_checkpoint_restart_is_bitwise(tmp_path):
     assert np.array_equal(ra, rb_)
     for h in (a, b):
         bd.tdpd_destroy(h)
-    # another configuration: a different lane count, then a different box
+    # another configuration: a different lane count, the other pair mode,
+    # then a different box
     d2 = dict(d, lanes=8)
     h = bd.create_from(d2)
     bd.tdpd_commit(h)
     with pytest.raises(bd.TdpdError) as e:
         bd.tdpd_load(h, path)
     assert e.value.status == 1 and 'lanes' in str(e.value)
+    bd.tdpd_destroy(h)
+    h = bd.create_from(dict(d, pair_mode=1))
+    bd.tdpd_commit(h)
+    with pytest.raises(bd.TdpdError) as e:
+        bd.tdpd_load(h, path)
+    assert e.value.status == 1 and 'shell' in str(e.value)
     bd.tdpd_destroy(h)
     h = bd.create_from(W.fluid_box(L=10.0, seed=3))
     bd.tdpd_commit(h)
@@ -626,3 +632,28 @@ def test_device_pointer_state_io():
             assert np.array_equal(u, w)
     for h in [b1, b2] + hs1 + hs2:
         bd.tdpd_destroy(h)
+
+
+def test_double_poiseuille_forcing_matches_oracle():
+    """The flow validation's fluid (Sec. 4.1): a = 18.75, gamma = 4.5, rc =
+    rcc = 1.58, w_R exponent s_f = 0.41, rho = 4, with the body force +f below
+    z = L_z/2 and -f above (tdpd_set_body_force_profile(1)). F(0), Q(0) and 10
+    steps against the oracle; on the device, the forces with the profile
+    differ from those with the uniform body force by exactly -2f on the
+    particles at z >= L_z/2 and by nothing below."""
+    d = W.double_poiseuille(L=12.0, rho=4.0, f=0.2, seed=7)
+    assert float(d['s_f']) == pytest.approx(0.41) and float(d['rc']) == pytest.approx(1.58)
+    F, Q, Fo, Qo = forces_vs_oracle(d)
+    check_step(F, Q, Fo, Qo)
+    d_uniform = dict(d, body_force_flip=0)
+    F1, _, _, _ = forces_vs_oracle(d_uniform)
+    top = d['particles']['pos'][:, 2] >= 0.5 * d['L'][2]
+    assert 0 < top.sum() < len(top)
+    diff = F.astype(np.float64) - F1.astype(np.float64)
+    f = float(d['body_force'][0])
+    scale = np.abs(F1).max() * 2.0 ** -22
+    assert np.abs(diff[top, 0] + 2 * f).max() < scale
+    assert np.abs(diff[~top, 0]).max() < scale
+    assert np.abs(diff[:, 1:]).max() < scale
+    err, obs, o, _ = run_vs_oracle(d, 10)
+    check_traj(err, d)

@@ -92,7 +92,7 @@ def test_double_poiseuille_transient_follows_stokes_series():
 
 
 def test_cylinder_dirichlet_diffusion_follows_bessel_series():
-    """Transport validation of Sec. 4.1 at the paper's size: R = 20, length 80,
+    """Transport validation of Sec. 4.2 at the paper's size: R = 20, length 80,
     rho = 4 (402,000 fluid particles), kappa = 5, the fluid at C0 = 0 and a
     frozen reservoir shell beyond R at CD = 1. The radially binned
     concentration at t = 2, 5, 10 and 20 follows the series of Eq. 17 with

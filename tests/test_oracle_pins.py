@@ -564,7 +564,7 @@ def test_membrane_relaxes_to_its_area_and_volume_targets():
 
 
 def test_cylinder_wall_reflects_radially():
-    """Bounce-back at the cylinder of the transport validation (Sec. 4.1,
+    """Bounce-back at the cylinder of the transport validation (Sec. 4.2,
     Eq. 17): a free particle whose predicted position lies outside radius R
     of the axis lands on the same radial line at distance 2R - d, with x
     untouched and its velocity reversed; one that stays inside moves freely."""

@@ -134,7 +134,7 @@ def _annulus(rng, n, r0, r1, L, cy, cz):
 
 
 def cylinder_diffusion(R=20.0, Lx=80.0, rho=4.0, kappa=5.0, c0=0.0, cd=1.0, seed=1006):
-    """The transport validation setup of Sec. 4.1 (Eq. 17): tDPD fluid filling
+    """The transport validation setup of Sec. 4.2 (Eq. 17): tDPD fluid filling
     a cylinder of radius R along x (R = 20 and length 80 at rho = 4: about
     402,000 particles), a = 18.75, gamma = 4.5, r_c = r_cc = 1.58, w_R
     exponent s = 0.41, flux exponent 2, kappa = 5. The fluid starts at
