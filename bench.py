@@ -44,7 +44,8 @@ METRIC = 'tDPD particle-steps/s on 1 GB300 (% HBM roofline); batched vs plain at
 UNIT = 'particle-steps/s'
 # DRAM bytes (read + write) of one k_pair launch from an ncu capture of the
 # current kernel build (summaries under profiles/), keyed by workload, skin,
-# lane count and replica count (0: not an ensemble); the capture is
+# stencil width, lane count, pair mode and replica count (0: not an
+# ensemble); the capture is
 # cold-cache and the bench step follows an L2 flush, so the two see the same
 # misses. A workload without an entry reports traffic null.
 PAIR_TRAFFIC = {}
@@ -298,6 +299,7 @@ def run_native(args):
     while bd.tdpd_kernel_name(h, len(names)) is not None:
         names.append(bd.tdpd_kernel_name(h, len(names)))
     pair_mode = bd.tdpd_pair_mode(h)
+    shape_skin, shape_m, shape_ms = bd.tdpd_list_shape(h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device='cuda')
 
     def barrier():
@@ -374,7 +376,7 @@ def run_native(args):
         # one TEA-8 draw + Box-Muller per two species, and ~8 operations per
         # species, for every pair inside the flux cut-off
         ops_pp += n_flux * (110 * ((ns + 1) // 2) + 8 * ns)
-    skin = 0.2 if args.skin is None else args.skin
+    skin = shape_skin
     rcut = max(float(d0['rc']), float(d0['rcc']))
     n_list = rho * 4.0 / 3.0 * math.pi * (rcut + skin) ** 3 if skin > 0 else 0.0
     compulsory_pp = 48 + 8 * ns
@@ -392,7 +394,8 @@ def run_native(args):
     gbs = compulsory_pp * n_all / (pair_ms * 1e-3) / 1e9
     lanes_now = bd.tdpd_lanes(h)
     traffic = None
-    key = (args.workload, skin, lanes_now, args.replicas if args.workload == 'ensemble' else 0)
+    key = (args.workload, round(skin, 3), shape_m, lanes_now, pair_mode,
+           args.replicas if args.workload == 'ensemble' else 0)
     if not args.random_flux and not args.cells_per_cutoff and key in PAIR_TRAFFIC:
         traffic = PAIR_TRAFFIC[key]
     roof = {'bound': 'alu', 'achieved': alu, 'peak': alu_peak, 'unit': 'Tops/s', 'frac': alu / alu_peak,
@@ -492,7 +495,11 @@ def run_native(args):
                        'pair_mode': {1: 'full shell', 2: 'half shell (fixed-point partner sums)'}.get(pair_mode),
                        'neighbour_list': ({'skin': skin, 'rebuilds_per_replica_step': rebuild_rate} if skin > 0
                                           else 'off (cell stencil every step)'),
-                       'cells_per_cutoff': args.cells_per_cutoff or 'library default (2)'},
+                       'cells_per_cutoff': shape_m,
+                       'shape': ('timed at commit: ms per 16 steps for skins 0.2, 0.15, 0.25, 0.3, 0.4 at m = 2'
+                                 '%s' % (', then at m = 3' if len(shape_ms) > 5 else '')) if len(shape_ms) else
+                                'not timed (pinned)',
+                       'shape_ms': [round(float(x), 4) for x in shape_ms]},
             'roofline': roof,
             'cpu_baseline': cpu,
             'e2e': e2e,

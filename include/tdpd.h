@@ -72,8 +72,10 @@ typedef struct {
     float body_force[3];        /* added to every non-frozen particle */
     uint32_t frozen_types;      /* bit t: particles of type t are not moved */
     int32_t exclude_same_body;  /* 1: no Eq. 3 forces within one membrane */
-    int32_t cells_per_cutoff;   /* cell-list stencil: cells of edge >= max(rc, rcc)/m,
-                                 * m = 2 or 3; 0 selects 2 */
+    int32_t cells_per_cutoff;   /* cell-list stencil: cells of edge >= max(rc, rcc)/m
+                                 * (plus the skin with lists), m = 1, 2 or 3; 0
+                                 * selects 2, or the width commit finds fastest
+                                 * when it times the list shape (tdpd_list_shape) */
 } tdpd_config;
 
 /* Membrane constants (Sec. 2.2). Bond l_m = l0/x0 and k_p are set per bond
@@ -213,6 +215,20 @@ tdpd_status tdpd_set_pair_mode(tdpd_sys *s, int mode);
  * reports 1); before commit the value tdpd_set_pair_mode set. */
 int tdpd_pair_mode(const tdpd_sys *s);
 
+/* The neighbour-list shape in use (commits the handle if needed): the skin
+ * (0 in cell mode; a replica whose box is too small for it uses a smaller
+ * one) and the stencil width m of the first replica (cells of edge >= (rcut
+ * + skin)/m). When the lanes are not pinned (tdpd_set_lanes) and the skin is
+ * not set (tdpd_set_skin), commit times whole steps (16, list rebuilds
+ * included) for the skins 0.2, 0.15, 0.25, 0.3 and 0.4, each with m = 2 and
+ * m = 3 unless a replica sets cells_per_cutoff, and keeps the first within
+ * 3 % of the fastest in that order; tuning_ms (may be NULL) receives up to
+ * max_tuning of those times, in that order, and *n_tuning their count (0
+ * when nothing was timed). No counterpart in the paper (it rebuilds its list
+ * every few steps at a fixed radius). */
+tdpd_status tdpd_list_shape(tdpd_sys *s, float *skin, int *cells_per_cutoff, float *tuning_ms, int max_tuning,
+                            int *n_tuning);
+
 /* Skin of the Verlet neighbour lists of the pair kernel (length units): each
  * particle keeps the partners within max(rc, rcc) + skin found at a list
  * build; a replica rebuilds its lists (and re-sorts its cells) in the step
@@ -220,7 +236,8 @@ int tdpd_pair_mode(const tdpd_sys *s);
  * the last build, which keeps every pair inside the cut-off in the lists
  * (Sec. 3.1 rebuilds the list every few steps). 0 selects cell mode: no
  * lists, the cell stencil is walked and the particles re-sorted every step.
- * Default (not called): 0.2. A replica whose box is too small for the skin
+ * Default (not called): 0.2, or, when the lanes are not pinned, the skin
+ * commit finds fastest (see tdpd_list_shape). A replica whose box is too small for the skin
  * (rcut + 2 skin must not exceed half a periodic edge, and the cells of edge
  * (rcut + skin)/m must fit 2m+1 times) gets a smaller one. The skin changes
  * the order in which pair terms are summed, so results agree to rounding,

@@ -72,6 +72,7 @@ def _load():
         'tdpd_set_skin': ([P, C.c_float], I),
         'tdpd_lanes': ([P], I),
         'tdpd_set_pair_mode': ([P, I], I),
+        'tdpd_list_shape': ([P, C.POINTER(C.c_float), C.POINTER(I), P, I, C.POINTER(I)], I),
         'tdpd_pair_mode': ([P], I),
         'tdpd_set_random_flux': ([P, C.c_float, C.c_float], I),
         'tdpd_set_body_force_profile': ([P, I], I),
@@ -203,6 +204,14 @@ def tdpd_set_pair_mode(h, mode):
 
 def tdpd_pair_mode(h):
     return int(lib.tdpd_pair_mode(h))
+
+
+def tdpd_list_shape(h):
+    """(skin, cells_per_cutoff, commit's step times of the candidate shapes in ms)."""
+    sk, m, n = C.c_float(0), C.c_int(0), C.c_int(0)
+    t = np.zeros(16, np.float32)
+    _chk(h, lib.tdpd_list_shape(h, C.byref(sk), C.byref(m), _ptr(t), 16, C.byref(n)))
+    return float(sk.value), int(m.value), t[:min(n.value, 16)].copy()
 
 
 def tdpd_set_skin(h, skin):

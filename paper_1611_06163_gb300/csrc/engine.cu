@@ -70,6 +70,12 @@ struct tdpd_sys {
     int lpp = 1;
     int lanes_fixed = 0;   // 0: timed at commit
     int mode_fixed = 0;    // pair mode: 0 chosen at commit, 1 full shell, 2 half shell
+    std::vector<float> shape_ms;   // commit's timing of the candidate list shapes (ms per 16 steps)
+    int shape_win = -1;            // the shape chosen (-1: not timed)
+    struct {
+        float skin;
+        int m;
+    } shape = {0.0f, 0};           // the list shape in use (m 0: each replica's configured width)
     bool half = false;     // list mode with half-shell lists (each unordered pair once)
     long long *accF = nullptr, *accQ = nullptr;   // half shell: partners' fixed-point shares
     float4 *fown = nullptr;                       // half shell: own force sums
@@ -884,6 +890,128 @@ tdpd_status capture_graphs(tdpd_sys *s)
     return TDPD_OK;
 }
 
+// Cell grids of every replica for a neighbour-list skin and a stencil width
+// m_force (0: each replica's configured cells_per_cutoff, 2 by default):
+// cells of edge >= (rcut + skin)/m; a periodic axis needs 2m+1 distinct
+// cells, and a list partner must stay the nearest image (rcut + 2 skin <=
+// L/2), so small boxes get a smaller skin. Sets each replica's m, skin and
+// nc and returns the replica tables and the total cell count.
+tdpd_status layout(tdpd_sys *s, float skin, int m_force, std::vector<RepParams> &P, int &NC)
+{
+    P.clear();
+    long total = 0;
+    for (size_t r = 0; r < s->reps.size(); ++r) {
+        HostRep &R = s->reps[r];
+        const float rcut = std::max(R.cfg.rc, R.cfg.rcc);
+        R.m = m_force > 0 ? m_force : (R.cfg.cells_per_cutoff > 0 ? R.cfg.cells_per_cutoff : 2);
+        float sk = s->use_list ? skin : 0.0f;
+        for (int c = 0; c < 3; ++c) {
+            const double L = R.cfg.L[c];
+            if (R.cfg.periodic[c]) sk = std::min(sk, (float)(0.999 * (0.5 * L - rcut) / 2));
+            sk = std::min(sk, (float)(0.999 * (L * R.m / ((2 * R.m + 1) * 1.0001) - rcut)));
+        }
+        R.skin = std::max(sk, 0.0f);
+        for (int c = 0; c < 3; ++c) {
+            R.nc[c] = (int)std::floor((double)R.cfg.L[c] * R.m / ((double)(rcut + R.skin) * 1.0001));
+            if (R.nc[c] < 2 * R.m + 1) return fail(s, TDPD_EINVAL, "replica %zu: too few cells", r);
+        }
+        const long ncells = (long)R.nc[0] * R.nc[1] * R.nc[2];
+        if (total + ncells > (1L << 30)) return fail(s, TDPD_EOVERFLOW, "too many cells");
+        P.push_back(make_params(R, (int)total, s->rep_pbase[r], (int)R.type.size()));
+        total += ncells;
+    }
+    NC = (int)total;
+    return TDPD_OK;
+}
+
+// A list shape the commit may time: neighbour-list skin and stencil width.
+struct Shape {
+    float skin;
+    int m;
+};
+
+// The shapes timed at commit, the default first: with neighbour lists, lanes
+// that are not pinned and no skin set, the skins 0.15-0.4; with no replica
+// pinning its cells_per_cutoff, the widths 2 and 3. Empty: nothing to time.
+std::vector<Shape> shape_candidates(const tdpd_sys *s)
+{
+    std::vector<Shape> v;
+    if (!s->use_list || s->lanes_fixed > 0) return v;
+    bool tune_m = true;
+    for (const HostRep &R : s->reps)
+        if (R.cfg.cells_per_cutoff > 0) tune_m = false;
+    const bool tune_skin = s->skin < 0.0f;
+    if (!tune_m && !tune_skin) return v;
+    const float skins_all[] = {DEFAULT_SKIN, 0.15f, 0.25f, 0.3f, 0.4f};
+    std::vector<float> skins = tune_skin ? std::vector<float>(std::begin(skins_all), std::end(skins_all))
+                                         : std::vector<float>{s->skin};
+    std::vector<int> ms = tune_m ? std::vector<int>{2, 3} : std::vector<int>{0};
+    for (int m : ms)
+        for (float sk : skins) v.push_back({sk, m});
+    return v;
+}
+
+// Make shape (skin, m) current: replica tables, cell count, lists sized and
+// built for the state the host holds, forces evaluated.
+tdpd_status apply_shape(tdpd_sys *s, const Shape &sh)
+{
+    std::vector<RepParams> P;
+    int NC = 0;
+    tdpd_status rc = layout(s, sh.skin, sh.m, P, NC);
+    if (rc) return rc;
+    if (NC > s->n_tiles * SCAN_TILE) return fail(s, TDPD_ESTATE, "cell arrays too small for a tuned shape");
+    s->NC = NC;
+    if ((rc = upload(s, s->d_reps, P.data(), P.size()))) return rc;
+    // a sorted state for the counting pass that sizes the lists
+    s->use_list = false;
+    rc = init_state(s);
+    s->use_list = true;
+    if (rc || (rc = prepare_list(s))) return rc;
+    return init_state(s);
+}
+
+// Time the candidate shapes over a few whole steps each (the list rebuilds
+// they cause included) with the default lanes and pair mode, keep the first
+// within 3 % of the fastest (the default first), and leave it applied at
+// step 0 with the host's state loaded.
+tdpd_status tune_shape(tdpd_sys *s, const std::vector<Shape> &shapes)
+{
+    constexpr int STEPS = 16;
+    cudaStream_t st = exec_stream(s);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    std::vector<float> t(shapes.size(), 1e30f);
+    tdpd_status rc = TDPD_OK;
+    for (size_t k = 0; k < shapes.size() && !rc; ++k) {
+        if ((rc = apply_shape(s, shapes[k]))) break;
+        int p = s->parity;
+        enqueue_step(s, p, st);                   // warm-up
+        p ^= 1;
+        cudaEventRecord(e0, st);
+        for (int it = 0; it < STEPS; ++it, p ^= 1) enqueue_step(s, p, st);
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t[k], e0, e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) rc = fail(s, TDPD_ECUDA, "shape tuning: %s", cudaGetErrorString(e));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    const float best = *std::min_element(t.begin(), t.end());
+    size_t win = 0;
+    while (t[win] > 1.03f * best) ++win;
+    s->shape_ms.assign(t.begin(), t.end());
+    s->shape_win = (int)win;
+    s->shape.skin = shapes[win].skin;
+    s->shape.m = shapes[win].m;
+    s->step = 0;
+    if ((rc = apply_shape(s, shapes[win]))) return rc;
+    if (s->builds) CU(cudaMemsetAsync(s->builds, 0, sizeof(uint32_t) * s->reps.size(), st));
+    return TDPD_OK;
+}
+
 tdpd_status commit(tdpd_sys *s)
 {
     if (s->committed) return TDPD_OK;
@@ -909,23 +1037,6 @@ tdpd_status commit(tdpd_sys *s)
         for (int c = 0; c < 3; ++c)
             if ((double)R.cfg.L[c] < 3.0 * rcut * 1.0001)
                 return fail(s, TDPD_EINVAL, "replica %zu: box edge %g is shorter than 3 cut-offs (%g)", r, R.cfg.L[c], rcut);
-        // cells of edge >= (rcut + skin)/m; a periodic axis needs 2m+1
-        // distinct cells, and a list partner must stay the nearest image
-        // (rcut + 2 skin <= L/2), so small boxes get a smaller skin
-        R.m = R.cfg.cells_per_cutoff > 0 ? R.cfg.cells_per_cutoff : 2;
-        float sk = s->use_list ? skin : 0.0f;
-        for (int c = 0; c < 3; ++c) {
-            const double L = R.cfg.L[c];
-            if (R.cfg.periodic[c]) sk = std::min(sk, (float)(0.999 * (0.5 * L - rcut) / 2));
-            sk = std::min(sk, (float)(0.999 * (L * R.m / ((2 * R.m + 1) * 1.0001) - rcut)));
-        }
-        R.skin = std::max(sk, 0.0f);
-        for (int c = 0; c < 3; ++c) {
-            R.nc[c] = (int)std::floor((double)R.cfg.L[c] * R.m / ((double)(rcut + R.skin) * 1.0001));
-            if (R.nc[c] < 2 * R.m + 1) return fail(s, TDPD_EINVAL, "replica %zu: too few cells", r);
-        }
-        const long ncells = (long)R.nc[0] * R.nc[1] * R.nc[2];
-        if ((long)NC + ncells > (1L << 30)) return fail(s, TDPD_EOVERFLOW, "too many cells");
         if (!R.rbcs.empty() && !R.has_mem) return fail(s, TDPD_ESTATE, "replica %zu has membranes but no tdpd_set_membrane", r);
         {
             // Eq. 4: sigma^2 = 2 kT gamma with one temperature for every type
@@ -945,7 +1056,6 @@ tdpd_status commit(tdpd_sys *s)
         }
         s->rep_pbase.push_back(N);
         s->rep_rbc0.push_back((int)s->h_rbcs.size());
-        P.push_back(make_params(R, NC, N, n));
         // membranes
         int first = R.n_free;
         for (size_t b = 0; b < R.rbcs.size(); ++b) {
@@ -1008,11 +1118,25 @@ tdpd_status commit(tdpd_sys *s)
             first += H.nv;
         }
         N += n;
-        NC += (int)ncells;
     }
     s->N = N;
+    // the cell grids of the default shape; with the shape tuned at commit the
+    // cell arrays are sized for the candidate with the most cells
+    tdpd_status lrc = layout(s, skin, 0, P, NC);
+    if (lrc) return lrc;
     s->NC = NC;
-    s->n_tiles = (NC + SCAN_TILE - 1) / SCAN_TILE;
+    s->shape.skin = s->use_list ? skin : 0.0f;
+    s->shape.m = 0;
+    const std::vector<Shape> shapes = shape_candidates(s);
+    int NC_alloc = NC;
+    for (const Shape &sh : shapes) {
+        std::vector<RepParams> Q;
+        int nc2 = 0;
+        if ((lrc = layout(s, sh.skin, sh.m, Q, nc2))) return lrc;
+        NC_alloc = std::max(NC_alloc, nc2);
+    }
+    if (!shapes.empty() && (lrc = layout(s, skin, 0, P, NC))) return lrc;
+    s->n_tiles = (NC_alloc + SCAN_TILE - 1) / SCAN_TILE;
     s->h_chunks.clear();
     for (size_t r = 0; r < s->reps.size(); ++r) {
         const int b0 = s->rep_pbase[r], n = (int)s->reps[r].type.size();
@@ -1151,14 +1275,15 @@ tdpd_status commit(tdpd_sys *s)
         if (rc || (rc = prepare_list(s))) return rc;
     }
     if ((rc = init_state(s))) return rc;
-    if (s->lanes_fixed == 0 && (rc = autotune(s))) return rc;
-    const int nk = (int)step_kernels(s).size();
-    for (int k = 0; k <= nk; ++k) CU(cudaEventCreate(&s->ev[k]));
-    s->n_ev = nk + 1;
     CU(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&s->gathered, cudaEventDisableTiming));
+    if (!shapes.empty() && (rc = tune_shape(s, shapes))) return rc;
+    if (s->lanes_fixed == 0 && (rc = autotune(s))) return rc;
+    const int nk = (int)step_kernels(s).size();
+    for (int k = 0; k <= nk; ++k) CU(cudaEventCreate(&s->ev[k]));
+    s->n_ev = nk + 1;
     if ((rc = capture_graphs(s))) return rc;
     CU(cudaStreamSynchronize(exec_stream(s)));
     s->committed = true;
@@ -1447,6 +1572,19 @@ tdpd_status tdpd_set_lanes(tdpd_sys *s, int lanes)
     if (lanes < 0 || lanes > 32 || (lanes & (lanes - 1)))
         return fail(s, TDPD_EINVAL, "lanes must be 0 (timed) or 1, 2, 4, 8, 16, 32");
     s->lanes_fixed = lanes;
+    return TDPD_OK;
+}
+
+tdpd_status tdpd_list_shape(tdpd_sys *s, float *skin, int *cells_per_cutoff, float *tuning_ms, int max_tuning,
+                            int *n_tuning)
+{
+    tdpd_status rc = ensure(s);
+    if (rc) return rc;
+    if (skin) *skin = s->shape.skin;
+    if (cells_per_cutoff) *cells_per_cutoff = s->reps[0].m;
+    const int n = (int)s->shape_ms.size();
+    for (int k = 0; k < n && k < max_tuning && tuning_ms; ++k) tuning_ms[k] = s->shape_ms[k];
+    if (n_tuning) *n_tuning = n;
     return TDPD_OK;
 }
 

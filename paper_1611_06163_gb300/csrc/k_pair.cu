@@ -128,10 +128,19 @@ __device__ __forceinline__ void epilogue(const PairArgs &A, const RepParams &P, 
     const int ti = (int)(wi >> 24);
     const int bi = wbits(vi.w);
     const int gi = P.pbase + (int)(wi & ID_MASK);     // load index
-    if (bi >= 0) {
-        const float4 fm = A.fext[gi];
-        fx += fm.x; fy += fm.y; fz += fm.z;
+    float *C = A.b.C, *Q = A.b.Q;
+    // every load before the first store, so that they are in flight together
+    const float4 fm = bi >= 0 ? A.fext[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 fo = A.b.frc[i];
+    const float4 xb = LIST ? A.xb[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool reacts = P.k_react != 0.0f && ((P.react_mask >> ti) & 1u);
+    const float c_src = reacts ? A.b.Ct[(size_t)i * ns + P.r_src] : 0.0f;
+    float c_old[NS > 0 ? NS : MAXS], q_old[NS > 0 ? NS : MAXS];
+    for (int s = 0; s < ns; ++s) {
+        c_old[s] = C[(size_t)i * ns + s];
+        q_old[s] = Q[(size_t)i * ns + s];
     }
+    fx += fm.x; fy += fm.y; fz += fm.z;
     const bool frozen = (P.frozen_mask >> ti) & 1u;
     if (!frozen) {
         const float sg = (P.fbody_flip && pi.z >= 0.5f * P.L[2]) ? -1.0f : 1.0f;
@@ -139,8 +148,8 @@ __device__ __forceinline__ void epilogue(const PairArgs &A, const RepParams &P, 
         fy += sg * P.fbody[1];
         fz += sg * P.fbody[2];
     }
-    if (P.k_react != 0.0f && ((P.react_mask >> ti) & 1u)) {
-        const float rate = P.k_react * A.b.Ct[(size_t)i * ns + P.r_src];
+    if (reacts) {
+        const float rate = P.k_react * c_src;
         for (int s = 0; s < ns; ++s) {
             if (s == P.r_src) q[s] -= rate;
             if (s == P.r_dst) q[s] += rate;
@@ -149,17 +158,12 @@ __device__ __forceinline__ void epilogue(const PairArgs &A, const RepParams &P, 
     if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(A.err + rep, 1u);
 
     float4 vn = vo;
-    float *C = A.b.C, *Q = A.b.Q;
-    const float4 fo = A.b.frc[i];
     if (A.integrate && !frozen) {
         vn.x = __fmaf_rn(P.hdt, fo.x + fx, vo.x);
         vn.y = __fmaf_rn(P.hdt, fo.y + fy, vo.y);
         vn.z = __fmaf_rn(P.hdt, fo.z + fz, vo.z);
         A.b.vel[i] = vn;
-        for (int s = 0; s < ns; ++s) {
-            const size_t k = (size_t)i * ns + s;
-            C[k] = __fmaf_rn(P.hdt, Q[k] + q[s], C[k]);
-        }
+        for (int s = 0; s < ns; ++s) C[(size_t)i * ns + s] = __fmaf_rn(P.hdt, q_old[s] + q[s], c_old[s]);
     }
     const float4 fn = make_float4(fx, fy, fz, 0.0f);
     A.b.frc[i] = fn;
@@ -183,7 +187,6 @@ __device__ __forceinline__ void epilogue(const PairArgs &A, const RepParams &P, 
     }
     if constexpr (LIST) {
         // displacement of the next position from the list build
-        const float4 xb = A.xb[i];
         float ex = rn.x - xb.x, ey = rn.y - xb.y, ez = rn.z - xb.z;
         ex = __fmaf_rn(-P.L[0], rintf(ex * P.inv_L[0]), ex);
         ey = __fmaf_rn(-P.L[1], rintf(ey * P.inv_L[1]), ey);
@@ -516,31 +519,36 @@ __global__ void __launch_bounds__(256) k_pair_finish(PairArgs A)
     const int lane = threadIdx.x & 31;
     const bool valid = i < A.n;
     const int ic = valid ? i : 0;
+    // the particle's inputs first (independent loads, all in flight together)
     const float4 vo = A.b.vel[ic];
+    const float4 pi = A.b.pos[ic];
+    const float4 vi = A.b.vt[ic];
+    const float4 fo = A.fown[ic];
+    long long *af = A.accF + 4 * (size_t)ic;
+    const longlong2 a01 = *reinterpret_cast<const longlong2 *>(af);
+    const long long a2 = af[2];
+    float q[NS > 0 ? NS : MAXS];
+    long long aq[NS > 0 ? NS : MAXS];
+    for (int s = 0; s < ns; ++s) {
+        q[s] = A.qown[(size_t)ic * ns + s];
+        aq[s] = A.accQ[(size_t)ic * ns + s];
+    }
     const int rep = wbits(vo.w);
     float disp2 = 0.0f;
     if (valid) {
         const RepParams &P = A.reps[rep];
-        long long *af = A.accF + 4 * (size_t)i;
-        const longlong2 a01 = *reinterpret_cast<const longlong2 *>(af);
-        const long long a2 = af[2];
-        *reinterpret_cast<longlong2 *>(af) = make_longlong2(0, 0);
-        af[2] = 0;
-        float q[NS > 0 ? NS : MAXS];
-        for (int s = 0; s < ns; ++s) {
-            const size_t k = (size_t)i * ns + s;
-            q[s] = A.qown[k] + __ll2float_rn(A.accQ[k]) * ACC_Q_UNIT;
-            A.accQ[k] = 0;
-        }
+        for (int s = 0; s < ns; ++s) q[s] += __ll2float_rn(aq[s]) * ACC_Q_UNIT;
         if (!(A.quar && A.quar[rep] != 0u)) {
-            const float4 fo = A.fown[i];
             const float fx = fo.x + __ll2float_rn(a01.x) * ACC_F_UNIT;
             const float fy = fo.y + __ll2float_rn(a01.y) * ACC_F_UNIT;
             const float fz = fo.z + __ll2float_rn(a2) * ACC_F_UNIT;
-            const float4 pi = A.b.pos[i];
             int cell = -1;
-            epilogue<NS, true>(A, P, i, pi, A.b.vt[i], vo, (uint32_t)wbits(pi.w), rep, fx, fy, fz, q, cell, disp2);
+            epilogue<NS, true>(A, P, i, pi, vi, vo, (uint32_t)wbits(pi.w), rep, fx, fy, fz, q, cell, disp2);
         }
+        // cleared for the next evaluation
+        *reinterpret_cast<longlong2 *>(af) = make_longlong2(0, 0);
+        af[2] = 0;
+        for (int s = 0; s < ns; ++s) A.accQ[(size_t)i * ns + s] = 0;
     }
     record_displacement(A.disp_next, rep, disp2, valid, lane);
 }

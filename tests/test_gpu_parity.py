@@ -657,3 +657,48 @@ def test_double_poiseuille_forcing_matches_oracle():
     assert np.abs(diff[:, 1:]).max() < scale
     err, obs, o, _ = run_vs_oracle(d, 10)
     check_traj(err, d)
+
+
+@pytest.mark.parametrize('m', [1, 3])
+@pytest.mark.parametrize('skin', [0.0, 0.25])
+def test_stencil_widths_match_oracle(m, skin):
+    """Cells of edge >= (rcut + skin)/m for m = 1 and 3 (the default is 2):
+    the stencil walk (skin 0) and the half-shell lists built over it give
+    F(0), Q(0) and 10 steps within tolerance of the oracle."""
+    d = W.single_rbc(L=10.0, diameter=5.0, seed=43)
+    d.update(cells_per_cutoff=m, skin=skin, lanes=2)
+    F, Q, Fo, Qo = forces_vs_oracle(d)
+    check_step(F, Q, Fo, Qo, (m, skin))
+    err, obs, o, _ = run_vs_oracle(d, 10)
+    check_traj(err, d)
+
+
+def test_list_shape_timed_at_commit():
+    """With the lanes not pinned and no skin set, commit times ten list
+    shapes (skins 0.2, 0.15, 0.25, 0.3, 0.4 at stencil widths 2 and 3) and
+    keeps one of them; the forces of the shape it keeps match the oracle.
+    With the lanes pinned nothing is timed and the default shape is used."""
+    bd = B()
+    d = W.single_rbc(L=12.0, diameter=5.0, seed=45)
+    o = oracle.Oracle(d, mode=1)
+    h = make(d)
+    try:
+        skin, m, ms = bd.tdpd_list_shape(h)
+        assert len(ms) == 10 and np.all(ms > 0), ms
+        assert m in (2, 3)
+        assert any(abs(skin - c) < 1e-6 for c in (0.2, 0.15, 0.25, 0.3, 0.4)), skin
+        k = [0.2, 0.15, 0.25, 0.3, 0.4].index(min((0.2, 0.15, 0.25, 0.3, 0.4), key=lambda c: abs(c - skin)))
+        chosen = ms[(m - 2) * 5 + k]
+        assert chosen <= 1.03 * ms.min() + 1e-9
+        F, Q = bd.tdpd_read_forces(h, 0, 1)
+        check_step(F, Q, o.F, o.Q)
+        bd.tdpd_step(h, 20)
+        assert (bd.tdpd_replica_status(h) == 0).all()
+    finally:
+        bd.tdpd_destroy(h)
+    h = make(dict(d, lanes=2))
+    try:
+        skin, m, ms = bd.tdpd_list_shape(h)
+        assert len(ms) == 0 and abs(skin - 0.2) < 1e-6 and m == 2
+    finally:
+        bd.tdpd_destroy(h)
