@@ -18,11 +18,14 @@
 //   - the flux (about a quarter of the candidates) is summed inline by the
 //     lane that found it; the force pairs (a few per cent of the candidates,
 //     each needing a TEA draw) are pushed to a per-warp queue and evaluated
-//     32 at a time with every lane busy. Each owner adds its pairs' forces
-//     one by one in push order (that is, candidate order), so the sums do
-//     not depend on how particles are grouped into warps.
-// Every unordered pair is evaluated from both sides; the random number is
-// keyed on (min id, max id, step), so both sides draw the same xi_ij.
+//     32 at a time with every lane busy. Each owner adds its
+//     pairs' forces one by one in push order (that is, candidate order), so
+//     the sums do not depend on how particles are grouped into warps.
+// In cell mode and with full-shell lists every unordered pair is evaluated
+// from both sides; the random number is keyed on (min id, max id, step), so
+// both sides draw the same xi_ij. With half-shell lists each pair is
+// evaluated once and the partner's share goes to fixed-point accumulators
+// (k_pair_finish completes the sums).
 #include "launch.h"
 #include "list_lane.cuh"
 
@@ -30,7 +33,13 @@ namespace tdpd {
 
 namespace {
 
-constexpr int QCAP = 64;   // queue ring per warp (a push adds at most 32)
+// The force pairs are queued per warp and evaluated DRAIN_W x 32 at a time,
+// DRAIN_W per lane (two per lane, which interleaves two TEA chains, measured
+// 1 % slower on the ensemble and the 786k fluid: the dependent latency of one
+// chain is already hidden by the other warps). The ring holds one drain plus
+// a push (32).
+constexpr int DRAIN_W = 1;
+constexpr int QCAP = 64;
 constexpr int UNR = 2;       // candidates loaded per trip of a stencil row (cell mode)
 constexpr int UNR_LIST = 2;  // list entries per trip (list mode; fetched a trip ahead)
 
@@ -48,9 +57,11 @@ struct LaneInfo {
     int rep;
 };
 
+static_assert(QCAP >= 32 * DRAIN_W + 32 && (QCAP & (QCAP - 1)) == 0, "queue ring");
+
 struct WarpSmem {
     QEntry q[QCAP];
-    float4 res[32];
+    float4 res[32 * DRAIN_W];
     float4 acc[32];
     LaneInfo li[32];
 };
@@ -76,42 +87,51 @@ __device__ __forceinline__ float3 pair_force(const RepParams &P, const LaneInfo 
     return make_float3(f * ex, f * ey, f * ez);
 }
 
-// Evaluate queue entries [head, head+n) (n <= 32) and add each result to its
-// owner's accumulator in push order; HALF: the partner's share (-f) goes to
-// its fixed-point accumulator.
+// Evaluate queue entries [head, head+n) (n <= 32 DRAIN_W; lane l takes the
+// entries l, l + 32, ...) and add each result to its owner's accumulator in
+// push order; HALF: the partner's share (-f) goes to its fixed-point
+// accumulator.
 template <bool HALF>
 __device__ __forceinline__ void drain(WarpSmem &W, int head, int n, const RepParams *__restrict__ reps,
                                       const float4 *__restrict__ vt, uint32_t step_ctr, int lane,
                                       long long *accF, uint32_t *err)
 {
-    const bool act = lane < n;
-    int owner = 32 + lane;
-    if (act) {
-        const QEntry E = W.q[(head + lane) & (QCAP - 1)];
-        owner = E.owner;
-        const LaneInfo I = W.li[owner];
-        const float3 f = pair_force(reps[I.rep], I, E, vt, step_ctr);
-        W.res[lane] = make_float4(f.x, f.y, f.z, 0.f);
-        if (HALF) {
-            long long *a = accF + 4 * (size_t)E.j;
-            acc_add(a, -f.x, ACC_F_SCALE, ACC_F_LIMIT, err + I.rep);
-            acc_add(a + 1, -f.y, ACC_F_SCALE, ACC_F_LIMIT, err + I.rep);
-            acc_add(a + 2, -f.z, ACC_F_SCALE, ACC_F_LIMIT, err + I.rep);
+    int owner[DRAIN_W];
+#pragma unroll
+    for (int u = 0; u < DRAIN_W; ++u) {
+        const int e = 32 * u + lane;
+        owner[u] = 32 + lane;
+        if (e < n) {
+            const QEntry E = W.q[(head + e) & (QCAP - 1)];
+            owner[u] = E.owner;
+            const LaneInfo I = W.li[E.owner];
+            const float3 f = pair_force(reps[I.rep], I, E, vt, step_ctr);
+            W.res[e] = make_float4(f.x, f.y, f.z, 0.f);
+            if (HALF) {
+                long long *a = accF + 4 * (size_t)E.j;
+                acc_add(a, -f.x, ACC_F_SCALE, ACC_F_LIMIT, err + I.rep);
+                acc_add(a + 1, -f.y, ACC_F_SCALE, ACC_F_LIMIT, err + I.rep);
+                acc_add(a + 2, -f.z, ACC_F_SCALE, ACC_F_LIMIT, err + I.rep);
+            }
         }
     }
-    const unsigned same = __match_any_sync(0xffffffffu, owner);
     __syncwarp();
-    if (act && lane == __ffs(same) - 1) {
-        float4 a = W.acc[owner];
-        for (unsigned m = same; m; m &= m - 1) {
-            const float4 r = W.res[__ffs(m) - 1];
-            a.x += r.x;
-            a.y += r.y;
-            a.z += r.z;
+#pragma unroll
+    for (int u = 0; u < DRAIN_W; ++u) {
+        const int e = 32 * u + lane;
+        const unsigned same = __match_any_sync(0xffffffffu, owner[u]);
+        if (e < n && lane == __ffs(same) - 1) {
+            float4 a = W.acc[owner[u]];
+            for (unsigned m = same; m; m &= m - 1) {
+                const float4 r = W.res[32 * u + __ffs(m) - 1];
+                a.x += r.x;
+                a.y += r.y;
+                a.z += r.z;
+            }
+            W.acc[owner[u]] = a;
         }
-        W.acc[owner] = a;
+        __syncwarp();
     }
-    __syncwarp();
 }
 
 // The epilogue of particle i (slot i, lane 0 of its LPP lanes) once its
@@ -342,11 +362,11 @@ __global__ void __launch_bounds__(128, 6) k_pair(PairArgs A)
             e[1] = make_int4(__float_as_int(dx), __float_as_int(dy), __float_as_int(dz), __float_as_int(r2));
         }
         qcount += __popc(bal);
-        if (qcount >= 32) {
+        if (qcount >= 32 * DRAIN_W) {
             __syncwarp();
-            drain<HALF>(W, qhead, 32, A.reps, vt, step_ctr, lane, A.accF, A.err);
-            qhead = (qhead + 32) & (QCAP - 1);
-            qcount -= 32;
+            drain<HALF>(W, qhead, 32 * DRAIN_W, A.reps, vt, step_ctr, lane, A.accF, A.err);
+            qhead = (qhead + 32 * DRAIN_W) & (QCAP - 1);
+            qcount -= 32 * DRAIN_W;
         }
     };
     if constexpr (LIST) {

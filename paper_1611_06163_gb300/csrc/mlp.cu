@@ -42,100 +42,135 @@ __device__ void load_weights(float *w, const float *params)
     __syncthreads();
 }
 
-// Forward pass of one sample per thread. With TRAIN, keeps the pre- and
-// post-activations, the output error signal dL/dy and per-block loss sums.
-template <bool TRAIN>
+// Forward pass (prediction) of one sample per thread.
 __global__ void __launch_bounds__(TPB) k_mlp_fwd(const float *__restrict__ params, const float *__restrict__ X,
-                                                 const float *__restrict__ T, int n, float *Z1, float *H1,
-                                                 float *Z2, float *H2, float *D3, float *Y, float *loss_part)
-{
-    __shared__ float w[NP];
-    __shared__ float red[TPB / 32];
-    const int mbr = blockIdx.y;
-    load_weights(w, params + (size_t)mbr * NP);
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    float err2 = 0.0f;
-    if (s < n) {
-        float x[IN];
-#pragma unroll
-        for (int i = 0; i < IN; ++i) x[i] = X[(size_t)s * IN + i];
-        const size_t base = ((size_t)mbr * n + s) * HID;
-        float h1[HID];
-#pragma unroll
-        for (int o = 0; o < HID; ++o) {
-            float z = w[OB1 + o];
-#pragma unroll
-            for (int i = 0; i < IN; ++i) z = fmaf(w[OW1 + o * IN + i], x[i], z);
-            h1[o] = gelu(z);
-            if (TRAIN) {
-                Z1[base + o] = z;
-                H1[base + o] = h1[o];
-            }
-        }
-        float y0 = w[OB3], y1 = w[OB3 + 1];
-        // four outputs at a time: four independent multiply-add chains
-        for (int o0 = 0; o0 < HID; o0 += 4) {
-            float z[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) z[q] = w[OB2 + o0 + q];
-#pragma unroll
-            for (int i = 0; i < HID; ++i)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) z[q] = fmaf(w[OW2 + (o0 + q) * HID + i], h1[i], z[q]);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int o = o0 + q;
-                const float h = gelu(z[q]);
-                if (TRAIN) {
-                    Z2[base + o] = z[q];
-                    H2[base + o] = h;
-                }
-                y0 = fmaf(w[OW3 + o], h, y0);
-                y1 = fmaf(w[OW3 + HID + o], h, y1);
-            }
-        }
-        const size_t yo = ((size_t)mbr * n + s) * OUT;
-        Y[yo] = y0;
-        Y[yo + 1] = y1;
-        if (TRAIN) {
-            const float e0 = y0 - T[(size_t)s * OUT], e1 = y1 - T[(size_t)s * OUT + 1];
-            const float sc = 2.0f / (float)(n * OUT);
-            D3[yo] = sc * e0;
-            D3[yo + 1] = sc * e1;
-            err2 = e0 * e0 + e1 * e1;
-        }
-    }
-    if (TRAIN) {
-        for (int o = 16; o > 0; o >>= 1) err2 += __shfl_down_sync(0xffffffffu, err2, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = err2;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float t = 0.0f;
-            for (int k = 0; k < TPB / 32; ++k) t += red[k];
-            loss_part[(size_t)mbr * gridDim.x + blockIdx.x] = t;
-        }
-    }
-}
-
-// Back-propagated error signals of the two hidden layers, one sample per thread.
-__global__ void __launch_bounds__(TPB) k_mlp_delta(const float *__restrict__ params, const float *__restrict__ Z1,
-                                                   const float *__restrict__ Z2, const float *__restrict__ D3,
-                                                   int n, float *D2, float *D1)
+                                                 int n, float *Y)
 {
     __shared__ float w[NP];
     const int mbr = blockIdx.y;
     load_weights(w, params + (size_t)mbr * NP);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const size_t base = ((size_t)mbr * n + s) * HID;
+    float x[IN];
+#pragma unroll
+    for (int i = 0; i < IN; ++i) x[i] = X[(size_t)s * IN + i];
+    float h1[HID];
+#pragma unroll
+    for (int o = 0; o < HID; ++o) {
+        float z = w[OB1 + o];
+#pragma unroll
+        for (int i = 0; i < IN; ++i) z = fmaf(w[OW1 + o * IN + i], x[i], z);
+        h1[o] = gelu(z);
+    }
+    float y0 = w[OB3], y1 = w[OB3 + 1];
+    // four outputs at a time: four independent multiply-add chains
+    for (int o0 = 0; o0 < HID; o0 += 4) {
+        float z[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) z[q] = w[OB2 + o0 + q];
+#pragma unroll
+        for (int i = 0; i < HID; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) z[q] = fmaf(w[OW2 + (o0 + q) * HID + i], h1[i], z[q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float h = gelu(z[q]);
+            y0 = fmaf(w[OW3 + o0 + q], h, y0);
+            y1 = fmaf(w[OW3 + HID + o0 + q], h, y1);
+        }
+    }
     const size_t yo = ((size_t)mbr * n + s) * OUT;
-    const float d30 = D3[yo], d31 = D3[yo + 1];
+    Y[yo] = y0;
+    Y[yo + 1] = y1;
+}
+
+// One training pass over a chunk of CH samples (one per thread) of one
+// member: forward, back-propagation, and the chunk's share of every
+// parameter's gradient, in one launch. The chunk's activations and error
+// signals stay in shared memory, feature-major with rows padded to CH + 1 so
+// that the per-sample writes and the per-parameter reads are free of bank
+// conflicts. Each gradient entry is the chunk's samples summed in sample
+// order; k_mlp_reduce adds the chunks in chunk order (float-float), so the
+// gradient is deterministic.
+constexpr int CH = 128;
+constexpr int LD = CH + 1;
+
+struct ChunkSmem {
+    float w[NP];
+    float X[IN][LD];
+    float H1[HID][LD], A1[HID][LD];   // A1: z1, then the error signal d1
+    float H2[HID][LD], A2[HID][LD];   // A2: z2, then the error signal d2
+    float D3[OUT][LD];
+    float red[CH / 32];
+};
+
+__global__ void __launch_bounds__(CH) k_mlp_chunk(const float *__restrict__ params, const float *__restrict__ X,
+                                                 const float *__restrict__ T, int n, float *part, float *loss_part)
+{
+    extern __shared__ float4 smem_raw[];
+    ChunkSmem &S = *reinterpret_cast<ChunkSmem *>(smem_raw);
+    const int mbr = blockIdx.y, c = blockIdx.x, nch = gridDim.x;
+    const int t = threadIdx.x;
+    const int smp = c * CH + t;
+    const bool valid = smp < n;
+    for (int k = t; k < NP; k += CH) S.w[k] = bf16r(params[(size_t)mbr * NP + k]);
+    __syncthreads();
+    const float *w = S.w;
+
+    // ---- forward
+    float x[IN];
+#pragma unroll
+    for (int i = 0; i < IN; ++i) {
+        x[i] = valid ? X[(size_t)smp * IN + i] : 0.0f;
+        S.X[i][t] = x[i];
+    }
+    float h1[HID];
+#pragma unroll
+    for (int o = 0; o < HID; ++o) {
+        float z = w[OB1 + o];
+#pragma unroll
+        for (int i = 0; i < IN; ++i) z = fmaf(w[OW1 + o * IN + i], x[i], z);
+        h1[o] = valid ? gelu(z) : 0.0f;
+        S.A1[o][t] = z;
+        S.H1[o][t] = h1[o];
+    }
+    float y0 = w[OB3], y1 = w[OB3 + 1];
+    for (int o0 = 0; o0 < HID; o0 += 4) {
+        float z[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) z[q] = w[OB2 + o0 + q];
+#pragma unroll
+        for (int i = 0; i < HID; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) z[q] = fmaf(w[OW2 + (o0 + q) * HID + i], h1[i], z[q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int o = o0 + q;
+            const float h = valid ? gelu(z[q]) : 0.0f;
+            S.A2[o][t] = z[q];
+            S.H2[o][t] = h;
+            y0 = fmaf(w[OW3 + o], h, y0);
+            y1 = fmaf(w[OW3 + HID + o], h, y1);
+        }
+    }
+    float d30 = 0.0f, d31 = 0.0f, err2 = 0.0f;
+    if (valid) {
+        const float e0 = y0 - T[(size_t)smp * OUT], e1 = y1 - T[(size_t)smp * OUT + 1];
+        const float sc = 2.0f / (float)(n * OUT);
+        d30 = sc * e0;
+        d31 = sc * e1;
+        err2 = e0 * e0 + e1 * e1;
+    }
+    S.D3[0][t] = d30;
+    S.D3[1][t] = d31;
+
+    // ---- back-propagation (this thread's sample)
     float d2[HID];
 #pragma unroll
     for (int o = 0; o < HID; ++o) {
         const float g = fmaf(d30, w[OW3 + o], d31 * w[OW3 + HID + o]);
-        d2[o] = g * gelu_grad(Z2[base + o]);
-        D2[base + o] = d2[o];
+        d2[o] = g * gelu_grad(S.A2[o][t]);
+        S.A2[o][t] = d2[o];
     }
     for (int i0 = 0; i0 < HID; i0 += 4) {
         float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -144,73 +179,96 @@ __global__ void __launch_bounds__(TPB) k_mlp_delta(const float *__restrict__ par
 #pragma unroll
             for (int q = 0; q < 4; ++q) a[q] = fmaf(d2[o], w[OW2 + o * HID + i0 + q], a[q]);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) D1[base + i0 + q] = a[q] * gelu_grad(Z1[base + i0 + q]);
+        for (int q = 0; q < 4; ++q) S.A1[i0 + q][t] = a[q] * gelu_grad(S.A1[i0 + q][t]);
     }
-}
+    for (int o = 16; o > 0; o >>= 1) err2 += __shfl_down_sync(0xffffffffu, err2, o);
+    if ((t & 31) == 0) S.red[t >> 5] = err2;
+    __syncthreads();
 
-// Gradient of one parameter per thread, in two passes: each CTA row c sums
-// the samples [c GCH, (c+1) GCH) in sample order (float-float compensated,
-// the loads of several samples in flight), then k_mlp_grad_sum adds the
-// chunks' partial sums in chunk order. The order is fixed, so the gradient
-// is deterministic.
-constexpr int GCH = 128;
-
-__global__ void __launch_bounds__(TPB) k_mlp_grad_part(const float *__restrict__ X, const float *__restrict__ H1,
-                                                       const float *__restrict__ H2, const float *__restrict__ D1,
-                                                       const float *__restrict__ D2, const float *__restrict__ D3,
-                                                       int n, float2 *part)
-{
-    const int mbr = blockIdx.z, c = blockIdx.y;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= NP) return;
-    const float *A = nullptr, *Bv = nullptr;   // gradient = sum_s A[s][ra] * Bv[s][rb] (Bv null: 1)
-    int ra = 0, rb = 0, wa = HID, wb = HID;
-    size_t oa = (size_t)mbr * n * HID, ob = (size_t)mbr * n * HID;
-    if (p < OB1) { A = D1; ra = (p - OW1) / IN; Bv = X; rb = (p - OW1) % IN; wb = IN; ob = 0; }
-    else if (p < OW2) { A = D1; ra = p - OB1; }
-    else if (p < OB2) { A = D2; ra = (p - OW2) / HID; Bv = H1; rb = (p - OW2) % HID; }
-    else if (p < OW3) { A = D2; ra = p - OB2; }
-    else if (p < OB3) { A = D3; wa = OUT; oa = (size_t)mbr * n * OUT; ra = (p - OW3) / HID; Bv = H2; rb = (p - OW3) % HID; }
-    else { A = D3; wa = OUT; oa = (size_t)mbr * n * OUT; ra = p - OB3; }
-    const int s0 = c * GCH, s1 = min(n, s0 + GCH);
-    FF acc{0.0f, 0.0f};
-    if (Bv) {
-#pragma unroll 8
-        for (int s = s0; s < s1; ++s)
-            acc = ff_add(acc, A[oa + (size_t)s * wa + ra] * Bv[ob + (size_t)s * wb + rb]);
+    // ---- the chunk's gradient: sums over its samples in sample order
+    float *out = part + ((size_t)mbr * nch + c) * NP;
+    {
+        // dW2[o][i] = sum_s d2[o][s] h1[i][s]: a 4 x 8 tile per thread
+        const int o0 = 4 * (t >> 3), i0 = 8 * (t & 7);
+        float acc[4][8];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+        for (int k = 0; k < CH; ++k) {
+            float da[4], hb[8];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) da[a] = S.A2[o0 + a][k];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) hb[b] = S.H1[i0 + b][k];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(da[a], hb[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) out[OW2 + (o0 + a) * HID + i0 + b] = acc[a][b];
+    }
+    if (t < HID) {
+        // row o of dW1, db1 and db2
+        const int o = t;
+        float g1[IN] = {0.0f, 0.0f, 0.0f, 0.0f}, gb1 = 0.0f, gb2 = 0.0f;
+        for (int k = 0; k < CH; ++k) {
+            const float d1 = S.A1[o][k];
+#pragma unroll
+            for (int i = 0; i < IN; ++i) g1[i] = fmaf(d1, S.X[i][k], g1[i]);
+            gb1 += d1;
+            gb2 += S.A2[o][k];
+        }
+#pragma unroll
+        for (int i = 0; i < IN; ++i) out[OW1 + o * IN + i] = g1[i];
+        out[OB1 + o] = gb1;
+        out[OB2 + o] = gb2;
     } else {
-#pragma unroll 8
-        for (int s = s0; s < s1; ++s) acc = ff_add(acc, A[oa + (size_t)s * wa + ra]);
+        // column i of dW3, and db3
+        const int i = t - HID;
+        float g0 = 0.0f, g1 = 0.0f, gb = 0.0f;
+        for (int k = 0; k < CH; ++k) {
+            const float h = S.H2[i][k];
+            g0 = fmaf(S.D3[0][k], h, g0);
+            g1 = fmaf(S.D3[1][k], h, g1);
+            if (i < OUT) gb += S.D3[i][k];
+        }
+        out[OW3 + i] = g0;
+        out[OW3 + HID + i] = g1;
+        if (i < OUT) out[OB3 + i] = gb;
     }
-    part[((size_t)mbr * gridDim.y + c) * NP + p] = make_float2(acc.hi, acc.lo);
+    if (t == 0) {
+        float l = 0.0f;
+        for (int k = 0; k < CH / 32; ++k) l += S.red[k];
+        loss_part[(size_t)mbr * nch + c] = l;
+    }
 }
 
-__global__ void __launch_bounds__(TPB) k_mlp_grad_sum(const float2 *__restrict__ part, int nch, float *grad)
-{
-    const int mbr = blockIdx.y;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= NP) return;
-    FF acc{0.0f, 0.0f};
-    for (int c = 0; c < nch; ++c) {
-        const float2 q = part[((size_t)mbr * nch + c) * NP + p];
-        acc = ff_add(acc, FF{q.x, q.y});
-    }
-    grad[(size_t)mbr * NP + p] = acc.hi + acc.lo;
-}
-
-// Adam (Kingma & Ba) on the float master weights; bc1, bc2 are the bias
-// corrections 1 - beta^t.
-__global__ void k_mlp_adam(float *params, const float *__restrict__ grad, float *m, float *v, int total, float lr,
-                           float beta1, float beta2, float eps, float bc1, float bc2)
+// Each parameter's gradient: its chunks' sums added in chunk order
+// (float-float); with adam, the Adam step (Kingma & Ba) on the float master
+// weights, bc1 and bc2 being the bias corrections 1 - beta^t.
+__global__ void __launch_bounds__(TPB) k_mlp_reduce(const float *__restrict__ part, int nch, int total,
+                                                    float *grad, int adam, float *params, float *m, float *v,
+                                                    float lr, float beta1, float beta2, float eps, float bc1,
+                                                    float bc2)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= total) return;
-    const float g = grad[k];
-    const float mk = fmaf(beta1, m[k], (1.0f - beta1) * g);
-    const float vk = fmaf(beta2, v[k], (1.0f - beta2) * g * g);
-    m[k] = mk;
-    v[k] = vk;
-    params[k] -= lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+    const int mbr = k / NP, p = k - mbr * NP;
+    FF acc{0.0f, 0.0f};
+    for (int c = 0; c < nch; ++c) acc = ff_add(acc, part[((size_t)mbr * nch + c) * NP + p]);
+    const float g = acc.hi + acc.lo;
+    grad[k] = g;
+    if (adam) {
+        const float mk = fmaf(beta1, m[k], (1.0f - beta1) * g);
+        const float vk = fmaf(beta2, v[k], (1.0f - beta2) * g * g);
+        m[k] = mk;
+        v[k] = vk;
+        params[k] -= lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+    }
 }
 
 }  // namespace
@@ -219,9 +277,8 @@ struct tdpd_mlp {
     int members = 0, n = 0, cap = 0;
     int64_t t = 0;
     float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
-    float *X = nullptr, *T = nullptr, *Z1 = nullptr, *H1 = nullptr, *Z2 = nullptr, *H2 = nullptr;
-    float *D1 = nullptr, *D2 = nullptr, *D3 = nullptr, *Y = nullptr, *loss_part = nullptr;
-    float *gpart = nullptr;     // [members][chunks][NP] float-float partial gradients
+    float *X = nullptr, *T = nullptr, *loss_part = nullptr;
+    float *gpart = nullptr;     // [members][chunks][NP] per-chunk gradient sums
     double mx[IN] = {}, sx[IN] = {}, my[OUT] = {}, sy[OUT] = {};
     bool have_data = false;
     cudaStream_t st = nullptr;
@@ -254,13 +311,10 @@ tdpd_status alloc_data(tdpd_mlp *m, int n)
     if (n <= m->cap) return TDPD_OK;
     cudaStreamSynchronize(m->st);
     free_data(m);
-    const size_t M = m->members;
-    float **bufs[] = {&m->X, &m->T, &m->Z1, &m->H1, &m->Z2, &m->H2, &m->D1, &m->D2, &m->D3, &m->Y, &m->loss_part,
-                      &m->gpart};
-    const size_t sizes[] = {(size_t)n * IN, (size_t)n * OUT, M * n * HID, M * n * HID, M * n * HID, M * n * HID,
-                            M * n * HID, M * n * HID, M * n * OUT, M * n * OUT, M * ((n + TPB - 1) / TPB),
-                            2 * M * ((n + GCH - 1) / GCH) * NP};
-    for (int k = 0; k < 12; ++k) {
+    const size_t M = m->members, nch = (size_t)(n + CH - 1) / CH;
+    float **bufs[] = {&m->X, &m->T, &m->loss_part, &m->gpart};
+    const size_t sizes[] = {(size_t)n * IN, (size_t)n * OUT, M * nch, M * nch * NP};
+    for (int k = 0; k < 4; ++k) {
         void *p = nullptr;
         if (cudaMalloc(&p, sizes[k] * sizeof(float)) != cudaSuccess) {
             free_data(m);
@@ -273,27 +327,37 @@ tdpd_status alloc_data(tdpd_mlp *m, int n)
     return TDPD_OK;
 }
 
-tdpd_status forward_backward(tdpd_mlp *m, double *loss)
+// One pass over the data: the chunks' gradients, then their sums (and, with
+// lr > 0, one Adam step); loss (may be NULL) receives each member's loss.
+tdpd_status pass(tdpd_mlp *m, float lr, double *loss)
 {
-    const dim3 gs((m->n + TPB - 1) / TPB, m->members);
-    k_mlp_fwd<true><<<gs, TPB, 0, m->st>>>(m->params, m->X, m->T, m->n, m->Z1, m->H1, m->Z2, m->H2, m->D3, m->Y,
-                                           m->loss_part);
-    k_mlp_delta<<<gs, TPB, 0, m->st>>>(m->params, m->Z1, m->Z2, m->D3, m->n, m->D2, m->D1);
-    const int nch = (m->n + GCH - 1) / GCH;
-    k_mlp_grad_part<<<dim3((NP + TPB - 1) / TPB, nch, m->members), TPB, 0, m->st>>>(
-        m->X, m->H1, m->H2, m->D1, m->D2, m->D3, m->n, reinterpret_cast<float2 *>(m->gpart));
-    k_mlp_grad_sum<<<dim3((NP + TPB - 1) / TPB, m->members), TPB, 0, m->st>>>(
-        reinterpret_cast<const float2 *>(m->gpart), nch, m->grad);
+    static bool attr = false;
+    if (!attr) {
+        MCU(cudaFuncSetAttribute(k_mlp_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChunkSmem)));
+        attr = true;
+    }
+    const int nch = (m->n + CH - 1) / CH;
+    k_mlp_chunk<<<dim3(nch, m->members), CH, sizeof(ChunkSmem), m->st>>>(m->params, m->X, m->T, m->n, m->gpart,
+                                                                          m->loss_part);
+    const int total = m->members * NP;
+    float bc1 = 1.0f, bc2 = 1.0f;
+    if (lr > 0.0f) {
+        ++m->t;
+        bc1 = (float)(1.0 - std::pow(0.9, (double)m->t));
+        bc2 = (float)(1.0 - std::pow(0.999, (double)m->t));
+    }
+    k_mlp_reduce<<<(total + TPB - 1) / TPB, TPB, 0, m->st>>>(m->gpart, nch, total, m->grad, lr > 0.0f ? 1 : 0,
+                                                             m->params, m->m, m->v, lr, 0.9f, 0.999f, 1e-8f, bc1,
+                                                             bc2);
     MCU(cudaGetLastError());
     if (loss) {
-        const int nb = (m->n + TPB - 1) / TPB;
-        std::vector<float> part((size_t)m->members * nb);
+        std::vector<float> part((size_t)m->members * nch);
         MCU(cudaMemcpyAsync(part.data(), m->loss_part, part.size() * sizeof(float), cudaMemcpyDeviceToHost, m->st));
         MCU(cudaStreamSynchronize(m->st));
         for (int k = 0; k < m->members; ++k) {
-            double s = 0.0;
-            for (int b = 0; b < nb; ++b) s += part[(size_t)k * nb + b];
-            loss[k] = s / ((double)m->n * OUT);
+            double sum = 0.0;
+            for (int c = 0; c < nch; ++c) sum += part[(size_t)k * nch + c];
+            loss[k] = sum / ((double)m->n * OUT);
         }
     }
     return TDPD_OK;
@@ -389,7 +453,7 @@ tdpd_status tdpd_mlp_set_data(tdpd_mlp *m, int n, const float *X, const float *Y
 tdpd_status tdpd_mlp_loss_grad(tdpd_mlp *m, double *loss, float *grad)
 {
     if (!m || !m->have_data) return mfail(TDPD_ESTATE, "tdpd_mlp_loss_grad: no data set");
-    tdpd_status rc = forward_backward(m, loss);
+    tdpd_status rc = pass(m, 0.0f, loss);
     if (rc) return rc;
     if (grad) {
         MCU(cudaMemcpyAsync(grad, m->grad, (size_t)m->members * NP * sizeof(float), cudaMemcpyDeviceToHost, m->st));
@@ -402,19 +466,11 @@ tdpd_status tdpd_mlp_train(tdpd_mlp *m, int steps, float lr, double *loss)
 {
     if (!m || !m->have_data) return mfail(TDPD_ESTATE, "tdpd_mlp_train: no data set");
     if (steps < 0 || !(lr > 0)) return mfail(TDPD_EINVAL, "tdpd_mlp_train: steps >= 0, lr > 0");
-    const float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
-    const int total = m->members * NP;
     for (int k = 0; k < steps; ++k) {
-        tdpd_status rc = forward_backward(m, nullptr);
+        tdpd_status rc = pass(m, lr, nullptr);
         if (rc) return rc;
-        ++m->t;
-        const float bc1 = (float)(1.0 - std::pow(0.9, (double)m->t));
-        const float bc2 = (float)(1.0 - std::pow(0.999, (double)m->t));
-        k_mlp_adam<<<(total + 255) / 256, 256, 0, m->st>>>(m->params, m->grad, m->m, m->v, total, lr, beta1, beta2,
-                                                           eps, bc1, bc2);
     }
-    MCU(cudaGetLastError());
-    if (loss) return forward_backward(m, loss);
+    if (loss) return pass(m, 0.0f, loss);
     MCU(cudaStreamSynchronize(m->st));
     return TDPD_OK;
 }
@@ -431,8 +487,7 @@ tdpd_status tdpd_mlp_predict(tdpd_mlp *m, int n, const float *X, float *mean, fl
     for (int i = 0; i < n; ++i)
         for (int c = 0; c < IN; ++c) xs[(size_t)i * IN + c] = (float)((X[(size_t)i * IN + c] - m->mx[c]) / m->sx[c]);
     MCU(cudaMemcpyAsync(dX, xs.data(), xs.size() * sizeof(float), cudaMemcpyHostToDevice, m->st));
-    k_mlp_fwd<false><<<dim3((n + TPB - 1) / TPB, m->members), TPB, 0, m->st>>>(
-        m->params, dX, nullptr, n, nullptr, nullptr, nullptr, nullptr, nullptr, dY, nullptr);
+    k_mlp_fwd<<<dim3((n + TPB - 1) / TPB, m->members), TPB, 0, m->st>>>(m->params, dX, n, dY);
     MCU(cudaGetLastError());
     MCU(cudaMemcpyAsync(ys.data(), dY, ys.size() * sizeof(float), cudaMemcpyDeviceToHost, m->st));
     MCU(cudaFreeAsync(dX, m->st));
