@@ -48,7 +48,12 @@ UNIT = 'particle-steps/s'
 # ensemble); the capture is
 # cold-cache and the bench step follows an L2 flush, so the two see the same
 # misses. A workload without an entry reports traffic null.
-PAIR_TRAFFIC = {}
+PAIR_TRAFFIC = {
+    # k_pair + k_pair_finish, half shell, one lane, skin 0.2, m = 2: 375.4 MB +
+    # 145.0 MB per launch on the first 128 replicas (841,109 particles; two
+    # launches averaged), scaled by particles to the 512 (3,496,044)
+    ('ensemble', 0.2, 2, 1, 2, 512): 2.1631e9,
+}
 
 
 def _ns10(d):
@@ -382,9 +387,15 @@ def run_native(args):
     compulsory_pp = 48 + 8 * ns
     impl = {'corrector': 48 + 12 * ns}
     if skin > 0:
-        ops_pp += rebuild_rate * 9 * n_list
-        impl['lists'] = 4 * n_list + 16
-        impl['list_rebuilds'] = rebuild_rate * (4 * n_list + 16)
+        # half shell: each pair listed once (half the entries), and the
+        # finishing pass reads and clears the fixed-point accumulators (32 +
+        # 8 ns B) and reads back the own sums (16 + 4 ns B) written before
+        n_entries = n_list / 2 if pair_mode == 2 else n_list
+        ops_pp += rebuild_rate * 9 * n_entries
+        impl['lists'] = 4 * n_entries + 16
+        impl['list_rebuilds'] = rebuild_rate * (4 * n_entries + 16)
+        if pair_mode == 2:
+            impl['half_shell_sums'] = 2 * (32 + 8 * ns) + 2 * (16 + 4 * ns)
     else:
         impl['next_binning'] = 8
     hbm, src = peaks()

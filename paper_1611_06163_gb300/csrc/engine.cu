@@ -578,17 +578,17 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         const uint32_t *any = s->rb + nrep;
         if (inline_decide(s)) {
             const DecideArgs d{s->disp[p], s->disp[1 - p], s->rb, s->step_ctr, s->builds, nrep};
-            launch_bin_next(cur, s->d_reps, s->N, s->count, s->tile_sum[0], s->cellrank, any, st, d);
+            launch_bin_next(cur, s->d_reps, s->N, s->count, s->tile_sum[0], s->cellrank, s->rb, any, st, d);
             mark();
         } else {
             launch_rebuild_decide(s->disp[p], s->disp[1 - p], s->rb, s->d_reps, nrep, 0, s->step_ctr, s->builds, st);
             mark();
-            launch_bin_next(cur, s->d_reps, s->N, s->count, s->tile_sum[0], s->cellrank, any, st);
+            launch_bin_next(cur, s->d_reps, s->N, s->count, s->tile_sum[0], s->cellrank, s->rb, any, st);
             mark();
         }
         launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[0], s->tile_sum[1], s->step_ctr, 0, st, any);
         mark();
-        launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st, any);
+        launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st, any, s->rb);
         mark();
         launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st,
                            s->rb, nrep, s->tile_sum[0], s->n_tiles, quarantine(s));

@@ -45,13 +45,16 @@ __global__ void k_rebuild_decide(const uint32_t *__restrict__ disp, uint32_t *di
     }
 }
 
-// Cell and rank of the position each particle will have at the next force
-// evaluation (the predictor of the gather), for the sort of a rebuild step.
+// Cell and rank of the position each particle of a rebuilding replica will
+// have at the next force evaluation (the predictor of the gather), for the
+// sort of a rebuild step. A replica that keeps its list keeps its slots: its
+// particles are not binned, and its whole count goes to its first cell, so
+// that the scan still gives every replica its own slot range.
 // With D.disp set (few replicas) the rebuild decision is taken here instead
 // of in k_rebuild_decide: every CTA reads the replicas' maxima itself, and
-// CTA 0 records the decision as k_rebuild_decide would.
+// CTA 0 records the decision as k_rebuild_decide would; otherwise rb holds it.
 __global__ void k_bin_next(Buffers b, const RepParams *__restrict__ reps, int n, int *count, int *tile_sum,
-                           int2 *cellrank, const uint32_t *any, DecideArgs D)
+                           int2 *cellrank, const uint32_t *any, const uint32_t *__restrict__ rb, DecideArgs D)
 {
     pdl_enter();
     if (D.disp) {
@@ -77,18 +80,25 @@ __global__ void k_bin_next(Buffers b, const RepParams *__restrict__ reps, int n,
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     int c = -1;
     if (k < n) {
-        const float4 p = b.pos[k];
         const float4 v = b.vel[k];
-        const RepParams &P = reps[wbits(v.w)];
-        const int type = (int)((uint32_t)wbits(p.w) >> 24);
-        float3 rn = make_float3(p.x, p.y, p.z);
-        if (!((P.frozen_mask >> type) & 1u)) {
-            bool flip;
-            rn = predict_pos(P, p, v, b.frc[k], flip);
+        const int r = wbits(v.w);
+        const RepParams &P = reps[r];
+        const bool rebuild = D.disp ? __uint_as_float(D.disp[r]) > P.half_skin2 : rb[r] != 0u;
+        if (rebuild) {
+            const float4 p = b.pos[k];
+            const int type = (int)((uint32_t)wbits(p.w) >> 24);
+            float3 rn = make_float3(p.x, p.y, p.z);
+            if (!((P.frozen_mask >> type) & 1u)) {
+                bool flip;
+                rn = predict_pos(P, p, v, b.frc[k], flip);
+            }
+            c = cell_of(P, rn.x, rn.y, rn.z);
+            const int rank = atomicAdd(count + c, 1);
+            cellrank[k] = make_int2(c, rank);
+        } else if (k == P.pbase) {
+            atomicAdd(count + P.cell_base, P.n);
+            atomicAdd(tile_sum + (P.cell_base >> SCAN_TILE_LOG2), P.n);
         }
-        c = cell_of(P, rn.x, rn.y, rn.z);
-        const int rank = atomicAdd(count + c, 1);
-        cellrank[k] = make_int2(c, rank);
     }
     add_tile_count(tile_sum, c);
 }
@@ -119,10 +129,10 @@ void launch_rebuild_decide(const uint32_t *disp, uint32_t *disp_clear, uint32_t 
 }
 
 void launch_bin_next(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum, int2 *cellrank,
-                     const uint32_t *any, cudaStream_t st, const DecideArgs &d)
+                     const uint32_t *rb, const uint32_t *any, cudaStream_t st, const DecideArgs &d)
 {
     if (n <= 0 && !d.disp) return;
-    launch_pdl(k_bin_next, std::max(1, (n + 255) / 256), 256, st, b, reps, n, count, tile_sum, cellrank, any, d);
+    launch_pdl(k_bin_next, std::max(1, (n + 255) / 256), 256, st, b, reps, n, count, tile_sum, cellrank, any, rb, d);
 }
 
 template <bool HALF>

@@ -88,12 +88,14 @@ __global__ void __launch_bounds__(1024) k_scan(int *count, int *cell_start, cons
     if (tid == 0) tile_clear[t] = 0;
 }
 
-__global__ void k_scatter_keys(const float4 *__restrict__ pos, const int2 *__restrict__ cellrank,
-                               const int *__restrict__ cell_start, int2 *keys, int n, const uint32_t *any)
+__global__ void k_scatter_keys(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
+                               const int2 *__restrict__ cellrank, const int *__restrict__ cell_start, int2 *keys,
+                               int n, const uint32_t *any, const uint32_t *__restrict__ rb)
 {
     pdl_enter();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || (any && !*any)) return;
+    if (rb && !rb[wbits(vel[k].w)]) return;          // a replica that keeps its slots
     int2 cr = cellrank[k];
     int id = wbits(pos[k].w) & ID_MASK;
     keys[cell_start[cr.x] + cr.y] = make_int2(id, k);
@@ -125,7 +127,10 @@ __global__ void k_rank_gather(Buffers cur, Buffers nxt, const RepParams *__restr
     bool pred = false;          // the species rows get the predictor
     float ldt = 0.0f;
     if (valid) {
-        if (any) {
+        // a replica that keeps its list keeps its slots (replicas own fixed
+        // slot ranges, so slot d's replica is that of the particle there)
+        const bool keep = !any || (rb && rb[wbits(cur.vel[d].w)] == 0u);
+        if (!keep) {
             const int2 key = keys[d];
             id = key.x;
             src = key.y;
@@ -134,9 +139,6 @@ __global__ void k_rank_gather(Buffers cur, Buffers nxt, const RepParams *__restr
             int rank = 0;
             for (int e = lo; e < hi; ++e) rank += (keys[e].x < id);
             dst = lo + rank;
-            // a replica that keeps its list keeps its slots (its cells map
-            // onto its own slot range, so this is a permutation of that range)
-            if (rb && rb[wbits(cur.vel[src].w)] == 0u) dst = src;
         } else {
             src = dst = d;
             id = wbits(cur.pos[d].w) & ID_MASK;
@@ -209,10 +211,10 @@ void launch_scan(int *count, int *cell_start, int n_tiles, const int *tile_read,
 }
 
 void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *cell_start,
-                         int2 *keys, int n, cudaStream_t st, const uint32_t *any)
+                         int2 *keys, int n, cudaStream_t st, const uint32_t *any, const uint32_t *rb)
 {
     if (n <= 0) return;
-    launch_pdl(k_scatter_keys, nblk(n, 256), 256, st, cur.pos, cellrank, cell_start, keys, n, any);
+    launch_pdl(k_scatter_keys, nblk(n, 256), 256, st, cur.pos, cur.vel, cellrank, cell_start, keys, n, any, rb);
 }
 
 void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams *reps,

@@ -133,8 +133,11 @@ void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count,
 // any (optional): skip all but the step counter when *any == 0
 void launch_scan(int *count, int *cell_start, int n_tiles, const int *tile_read, int *tile_clear,
                  uint32_t *step_ctr, int inc, cudaStream_t st, const uint32_t *any = nullptr);
+// rb (optional): only the particles of replicas with rb[r] set (their slots
+// are the only ones re-sorted); any = rb + n_rep skips everything when none
 void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *cell_start,
-                         int2 *keys, int n, cudaStream_t st, const uint32_t *any = nullptr);
+                         int2 *keys, int n, cudaStream_t st, const uint32_t *any = nullptr,
+                         const uint32_t *rb = nullptr);
 // Quarantine (optional): err [n_reps] is each replica's status word from the
 // last force evaluation; a replica with a nonzero word is not moved (no
 // predictor) and quar[r] = (err[r] != 0) tells the kernels after the gather
@@ -165,10 +168,12 @@ struct DecideArgs {
     uint32_t *disp_clear, *rb, *step_ctr, *builds;
     int n_rep;
 };
-// cell and rank of each particle's next predicted position (list mode, when
-// any replica rebuilds)
+// cell and rank of the next predicted position of each particle of a
+// rebuilding replica (list mode, when any replica rebuilds; rb[r]: replica r
+// rebuilds, unless d.disp is set and the decision is taken here); a replica
+// that keeps its slots adds its particle count to its first cell
 void launch_bin_next(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum, int2 *cellrank,
-                     const uint32_t *any, cudaStream_t st, const DecideArgs &d = DecideArgs{});
+                     const uint32_t *rb, const uint32_t *any, cudaStream_t st, const DecideArgs &d = DecideArgs{});
 void launch_list_build(const ListArgs &a, cudaStream_t st);
 // pdl: launched as a programmatic dependent of the previous kernel on st
 void launch_mem_gather(const MemArgs &a, cudaStream_t st, bool pdl);
