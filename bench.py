@@ -48,12 +48,7 @@ UNIT = 'particle-steps/s'
 # ensemble); the capture is
 # cold-cache and the bench step follows an L2 flush, so the two see the same
 # misses. A workload without an entry reports traffic null.
-PAIR_TRAFFIC = {
-    # k_pair + k_pair_finish, half shell, one lane, skin 0.2, m = 2: 375.4 MB +
-    # 145.0 MB per launch on the first 128 replicas (841,109 particles; two
-    # launches averaged), scaled by particles to the 512 (3,496,044)
-    ('ensemble', 0.2, 2, 1, 2, 512): 2.1631e9,
-}
+PAIR_TRAFFIC = {}
 
 
 def _ns10(d):
@@ -121,7 +116,7 @@ class Clocks:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(['nvidia-smi', '-i', str(self.index), '--query-gpu=' + self.Q,
-                                       '--format=csv,noheader,nounits', '-lms', '100'],
+                                       '--format=csv,noheader,nounits', '-lms', '20'],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None

@@ -469,6 +469,7 @@ PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum, 
     for (const HostRep &R : s->reps)
         if (R.qr_ms > 0.0f) a.qr = 1;
     if (s->use_list) {
+        a.pre = b.pos == s->buf[0].pos ? s->buf[1] : s->buf[0];
         a.nl = s->nl; a.nlc = s->nlc; a.cap = s->nl_cap; a.xb = s->xb; a.disp_next = disp_next;
         a.half = s->half ? 1 : 0;
         a.accF = s->accF; a.accQ = s->accQ; a.fown = s->fown; a.qown = s->qown;
@@ -1757,6 +1758,16 @@ std::vector<std::pair<void *, size_t>> ckp_arrays(tdpd_sys *s, int parity, size_
         {s->tile_sum[0], 4 * (size_t)s->n_tiles}, {s->tile_sum[1], 4 * (size_t)s->n_tiles},
         {s->cellrank, 8 * N}, {s->errw, 4 * nr}, {s->step_ctr, 12}};
     if (s->use_list) {
+        // the other buffer holds the next step's predicted state (written by
+        // the pair epilogue), which a step without a rebuild uses as it is
+        const Buffers &O = s->buf[1 - parity];
+        v.push_back({O.pos, 16 * N});
+        v.push_back({O.vt, 16 * N});
+        v.push_back({O.vel, 16 * N});
+        v.push_back({O.frc, 16 * N});
+        v.push_back({O.C, 4 * N * ns});
+        v.push_back({O.Ct, 4 * N * ns});
+        v.push_back({O.Q, 4 * N * ns});
         v.push_back({s->disp[0], 4 * nr});
         v.push_back({s->disp[1], 4 * nr});
         v.push_back({s->builds, 4 * nr});
@@ -1788,7 +1799,7 @@ tdpd_status tdpd_save(tdpd_sys *s, const char *path)
     if (!path) return fail(s, TDPD_EINVAL, "null path");
     CkpHeader H{};
     std::memcpy(H.magic, CKP_MAGIC, 8);
-    H.version = 1;
+    H.version = 2;     // 2: list mode also saves the other buffer
     H.N = s->N; H.NC = s->NC; H.ns = s->ns; H.n_rep = (int)s->reps.size(); H.n_rbc = s->n_rbc;
     H.lpp = s->lpp; H.use_list = s->use_list ? (s->half ? 2 : 1) : 0; H.nl_cap = s->nl_cap; H.parity = s->parity;
     H.n_tiles = s->n_tiles; H.step = s->step;
@@ -1822,7 +1833,7 @@ tdpd_status tdpd_load(tdpd_sys *s, const char *path)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(s, TDPD_EINVAL, "cannot open %s", path);
     CkpHeader H{};
-    if (std::fread(&H, sizeof H, 1, f) != 1 || std::memcmp(H.magic, CKP_MAGIC, 8) != 0 || H.version != 1) {
+    if (std::fread(&H, sizeof H, 1, f) != 1 || std::memcmp(H.magic, CKP_MAGIC, 8) != 0 || H.version != 2) {
         std::fclose(f);
         return fail(s, TDPD_EINVAL, "%s is not a checkpoint of this library", path);
     }

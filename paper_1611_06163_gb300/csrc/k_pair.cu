@@ -178,12 +178,16 @@ __device__ __forceinline__ void epilogue(const PairArgs &A, const RepParams &P, 
     if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(A.err + rep, 1u);
 
     float4 vn = vo;
-    if (A.integrate && !frozen) {
+    const bool moves = A.integrate && !frozen;
+    if (moves) {
         vn.x = __fmaf_rn(P.hdt, fo.x + fx, vo.x);
         vn.y = __fmaf_rn(P.hdt, fo.y + fy, vo.y);
         vn.z = __fmaf_rn(P.hdt, fo.z + fz, vo.z);
         A.b.vel[i] = vn;
-        for (int s = 0; s < ns; ++s) C[(size_t)i * ns + s] = __fmaf_rn(P.hdt, q_old[s] + q[s], c_old[s]);
+        for (int s = 0; s < ns; ++s) {
+            c_old[s] = __fmaf_rn(P.hdt, q_old[s] + q[s], c_old[s]);    // now C_{k+1}
+            C[(size_t)i * ns + s] = c_old[s];
+        }
     }
     const float4 fn = make_float4(fx, fy, fz, 0.0f);
     A.b.frc[i] = fn;
@@ -191,13 +195,32 @@ __device__ __forceinline__ void epilogue(const PairArgs &A, const RepParams &P, 
 
     float3 rn = make_float3(pi.x, pi.y, pi.z);
     float4 vtn = vn;
+    bool flip = false;
     if (!frozen) {
-        bool flip;
         rn = predict_pos(P, pi, vn, fn, flip);
         if (flip) { vtn.x = -vtn.x; vtn.y = -vtn.y; vtn.z = -vtn.z; }
         vtn.x = __fmaf_rn(P.ldt, fn.x, vtn.x);
         vtn.y = __fmaf_rn(P.ldt, fn.y, vtn.y);
         vtn.z = __fmaf_rn(P.ldt, fn.z, vtn.z);
+    }
+    if constexpr (LIST) {
+        if (A.pre.pos) {
+            // the next step's predicted state at this slot, in the other
+            // buffer: the same values the gather's predictor would write (a
+            // wall bounce reverses the stored velocity too)
+            const Buffers &O = A.pre;
+            const float sv = flip ? -1.0f : 1.0f;
+            O.pos[i] = make_float4(rn.x, rn.y, rn.z, pi.w);
+            O.vel[i] = make_float4(sv * vn.x, sv * vn.y, sv * vn.z, vo.w);
+            O.frc[i] = fn;
+            O.vt[i] = make_float4(vtn.x, vtn.y, vtn.z, vi.w);
+            for (int s = 0; s < ns; ++s) {
+                const size_t k = (size_t)i * ns + s;
+                O.C[k] = c_old[s];
+                O.Q[k] = q[s];
+                O.Ct[k] = frozen ? c_old[s] : __fmaf_rn(P.ldt, q[s], c_old[s]);
+            }
+        }
     }
     if (bi >= 0) {
         // the next step's membrane kernels start from these (the same

@@ -122,13 +122,20 @@ __global__ void k_rank_gather(Buffers cur, Buffers nxt, const RepParams *__restr
     const bool any = !rb || rb[n_rep] != 0u;
     if (tile_zero && any)
         for (int t = d; t < n_tiles; t += gridDim.x * blockDim.x) tile_zero[t] = 0;
-    const bool valid = d < n;
+    bool valid = d < n;
     int id = 0, src = 0, dst = 0;
     bool pred = false;          // the species rows get the predictor
     float ldt = 0.0f;
+    if (valid && rb) {
+        // list mode: a replica that keeps its list keeps its slots (replicas
+        // own fixed slot ranges, so slot d's replica is that of the particle
+        // there), and the last pair epilogue already wrote its predicted
+        // state into nxt at those slots; only a quarantined replica, which
+        // that epilogue skipped, is copied here
+        const int r = wbits(cur.vel[d].w);
+        if ((!any || rb[r] == 0u) && !(Qa.err && Qa.err[r] != 0u)) valid = false;
+    }
     if (valid) {
-        // a replica that keeps its list keeps its slots (replicas own fixed
-        // slot ranges, so slot d's replica is that of the particle there)
         const bool keep = !any || (rb && rb[wbits(cur.vel[d].w)] == 0u);
         if (!keep) {
             const int2 key = keys[d];

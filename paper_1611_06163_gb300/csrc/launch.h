@@ -37,6 +37,11 @@ struct Buffers {
 
 struct PairArgs {
     Buffers b;
+    // neighbour-list mode: the other buffer, which receives each particle's
+    // predicted state for the next step at its slot (what the next gather
+    // would write for a replica that keeps its slots, bit for bit); pre.pos
+    // null: not written (cell mode)
+    Buffers pre;
     const float4 *fext;          // membrane force by load index (membrane particles only)
     float4 *mx, *mv;             // out: next predicted position and v~ of membrane particles
     const RepParams *reps;
@@ -142,6 +147,9 @@ void launch_scatter_keys(const Buffers &cur, const int2 *cellrank, const int *ce
 // last force evaluation; a replica with a nonzero word is not moved (no
 // predictor) and quar[r] = (err[r] != 0) tells the kernels after the gather
 // to skip it.
+// In list mode (rb set) a replica that keeps its slots is not gathered at
+// all: the last pair epilogue wrote its predicted state into nxt already;
+// only a quarantined one is copied (without the predictor).
 struct Quarantine {
     const uint32_t *err = nullptr;
     uint32_t *quar = nullptr;
