@@ -42,13 +42,17 @@ import workloads as W  # noqa: E402
 
 METRIC = 'tDPD particle-steps/s on 1 GB300 (% HBM roofline); batched vs plain at tol'
 UNIT = 'particle-steps/s'
-# DRAM bytes (read + write) of one k_pair launch from an ncu capture of the
-# current kernel build (summaries under profiles/), keyed by workload, skin,
-# stencil width, lane count, pair mode and replica count (0: not an
-# ensemble); the capture is
-# cold-cache and the bench step follows an L2 flush, so the two see the same
-# misses. A workload without an entry reports traffic null.
-PAIR_TRAFFIC = {}
+# DRAM bytes (read + write) of one pair step (k_pair, plus k_pair_finish in
+# half-shell mode) from an ncu capture of the current kernel build (summaries
+# under profiles/), keyed by workload, skin, stencil width, lane count, pair
+# mode and replica count (0: not an ensemble). The ensemble's figure is the
+# mean of two steps captured on its first 128 replicas (841,109 particles),
+# scaled by particles to all 512 (3,496,044). The capture is cold-cache and
+# the bench step follows an L2 flush, so the two see the same misses. A
+# workload without an entry reports traffic null.
+PAIR_TRAFFIC = {
+    ('ensemble', 0.2, 2, 1, 2, 512): 2.393e9,
+}
 
 
 def _ns10(d):
@@ -405,7 +409,7 @@ def run_native(args):
     if not args.random_flux and not args.cells_per_cutoff and key in PAIR_TRAFFIC:
         traffic = PAIR_TRAFFIC[key]
     roof = {'bound': 'alu', 'achieved': alu, 'peak': alu_peak, 'unit': 'Tops/s', 'frac': alu / alu_peak,
-            'traffic': traffic, 'traffic_unit': 'bytes per k_pair launch (ncu DRAM read + write)',
+            'traffic': traffic, 'traffic_unit': 'bytes per pair step (ncu DRAM read + write)',
             'peak_source': 'derived: %d SMs (this device) x 128 FP32 lanes x %.0f MHz (measured max clock)' % (
                 n_sm, sm_max_mhz()),
             'kernel': 'k_pair' + (' + k_pair_finish' if pair_mode == 2 else ''),

@@ -548,12 +548,15 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
     auto mark = [&]() {
         if (ev && e < s->n_ev) cudaEventRecordWithFlags(ev[e++], st, cudaEventRecordExternal);
     };
-    // The membrane kernels read the predicted vertices the last pair kernel
+    // The membrane kernels read the predicted vertices the last pair epilogue
     // wrote in load order, so they need not wait for the sort: in a plain
-    // step they run on a side stream beside scan, scatter and gather, and the
-    // pair kernel joins both. When every membrane's constraints are lagged,
-    // K-Apply goes first and the pair kernel waits for it alone; K-Gather
-    // (for the next step) overlaps the pair kernel. The timed step keeps one
+    // step they run on a side stream from the step's start. Their forces are
+    // needed only by the epilogue, which also writes the vertices' next
+    // positions they read, so the branch joins just before the epilogue:
+    // before k_pair_finish with the half shell (the branch then overlaps the
+    // sort and the pair walk), before the pair kernel otherwise. When every
+    // membrane's constraints are lagged, K-Apply goes first and K-Gather (for
+    // the next step) follows it on the branch. The timed step keeps one
     // stream, so that the events bracket one kernel each.
     const bool branch = s->n_rbc && !ev;
     if (branch) {
@@ -614,11 +617,18 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         launch_mem_forces(m, st);
         mark();
     }
-    if (branch) cudaStreamWaitEvent(st, s->join, 0);
-    launch_pair(pair_args(s, nxt, 1, s->tile_sum[1 - p], s->disp[1 - p], pair_builds_lists(s) ? s->rb : nullptr),
-                st);
+    const PairArgs pa = pair_args(s, nxt, 1, s->tile_sum[1 - p], s->disp[1 - p],
+                                  pair_builds_lists(s) ? s->rb : nullptr);
+    auto join = [&]() {
+        if (!branch) return;
+        cudaStreamWaitEvent(st, s->join, 0);
+        if (s->all_lagged) cudaStreamWaitEvent(st, s->gathered, 0);
+    };
+    if (!s->half) join();
+    launch_pair(pa, st, PAIR_WALK);
+    if (s->half) join();
+    launch_pair(pa, st, PAIR_FINISH);
     mark();
-    if (branch && s->all_lagged) cudaStreamWaitEvent(st, s->gathered, 0);
 }
 
 constexpr size_t OBS_STAGE = (sizeof(double) * OBS_K + 15) / 16 * 16;
@@ -702,8 +712,11 @@ void enqueue_init(tdpd_sys *s, cudaStream_t st, bool branch)
         launch_mem_gather(m, st, true);
         launch_mem_forces(m, st);
     }
-    if (branch) cudaStreamWaitEvent(st, s->join, 0);
-    launch_pair(pair_args(s, s->buf[1], 0, s->tile_sum[1], s->disp[1]), st);
+    const PairArgs pa = pair_args(s, s->buf[1], 0, s->tile_sum[1], s->disp[1]);
+    if (branch && !s->half) cudaStreamWaitEvent(st, s->join, 0);
+    launch_pair(pa, st, PAIR_WALK);
+    if (branch && s->half) cudaStreamWaitEvent(st, s->join, 0);
+    launch_pair(pa, st, PAIR_FINISH);
 }
 
 // Device part of loading a state whose reference points are staged and whose

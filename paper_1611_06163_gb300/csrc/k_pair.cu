@@ -613,37 +613,37 @@ static void launch_lanes(const PairArgs &a, cudaStream_t st)
 }
 
 template <int NS, bool LIST>
-static void launch_ns(const PairArgs &a, cudaStream_t st)
+static void launch_ns(const PairArgs &a, cudaStream_t st, int part)
 {
     if constexpr (LIST) {
         if (a.half) {
-            launch_lanes<NS, true, true>(a, st);
-            launch_pdl(k_pair_finish<NS>, (a.n + 255) / 256, 256, st, a);
+            if (part & PAIR_WALK) launch_lanes<NS, true, true>(a, st);
+            if (part & PAIR_FINISH) launch_pdl(k_pair_finish<NS>, (a.n + 255) / 256, 256, st, a);
             return;
         }
     }
-    launch_lanes<NS, LIST, false>(a, st);
+    if (part & PAIR_WALK) launch_lanes<NS, LIST, false>(a, st);
 }
 
-void launch_pair(const PairArgs &a, cudaStream_t st)
+void launch_pair(const PairArgs &a, cudaStream_t st, int part)
 {
     if (a.n <= 0) return;
     if (a.qr) {
         // the random flux lives in the general kernel only
-        if (a.nl) launch_ns<0, true>(a, st);
-        else launch_ns<0, false>(a, st);
+        if (a.nl) launch_ns<0, true>(a, st, part);
+        else launch_ns<0, false>(a, st, part);
     } else if (a.nl) {
         switch (a.ns) {
-        case 1: launch_ns<1, true>(a, st); break;
-        case 2: launch_ns<2, true>(a, st); break;
-        case 10: launch_ns<10, true>(a, st); break;     // the paper's ten-species case
-        default: launch_ns<0, true>(a, st); break;
+        case 1: launch_ns<1, true>(a, st, part); break;
+        case 2: launch_ns<2, true>(a, st, part); break;
+        case 10: launch_ns<10, true>(a, st, part); break;     // the paper's ten-species case
+        default: launch_ns<0, true>(a, st, part); break;
         }
     } else {
         switch (a.ns) {
-        case 1: launch_ns<1, false>(a, st); break;
-        case 2: launch_ns<2, false>(a, st); break;
-        default: launch_ns<0, false>(a, st); break;
+        case 1: launch_ns<1, false>(a, st, part); break;
+        case 2: launch_ns<2, false>(a, st, part); break;
+        default: launch_ns<0, false>(a, st, part); break;
         }
     }
 }

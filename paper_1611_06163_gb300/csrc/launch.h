@@ -163,7 +163,10 @@ void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams 
 // list mode: rb[n_rep + 1] rebuild flags; without any rebuild every slot keeps
 // its particle, a replica that does not rebuild keeps its slots; tile_zero
 // (n_tiles ints) is cleared after a rebuild
-void launch_pair(const PairArgs &a, cudaStream_t st);
+// part: PAIR_WALK the pair kernel, PAIR_FINISH the half shell's finishing
+// pass (nothing in full-shell and cell mode), or both
+constexpr int PAIR_WALK = 1, PAIR_FINISH = 2, PAIR_ALL = 3;
+void launch_pair(const PairArgs &a, cudaStream_t st, int part = PAIR_ALL);
 // rb[r] = the displacement of replica r exceeds half its skin (or force);
 // rb[n_rep] = any; disp_clear zeroed for the next evaluation; advances the
 // step counter and counts each replica's rebuilds in builds
