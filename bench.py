@@ -295,6 +295,8 @@ def run_native(args):
             bd.tdpd_set_lanes(h, args.lanes)
     if args.pair_mode:
         bd.tdpd_set_pair_mode(h, args.pair_mode)
+    if args.sort_mode:
+        bd.tdpd_set_sort_mode(h, args.sort_mode)
     bd.tdpd_commit(h)
     nk = bd.tdpd_launches_per_step(h)
     # timed entries: one per launch, except that the half shell's pair entry
@@ -303,6 +305,7 @@ def run_native(args):
     while bd.tdpd_kernel_name(h, len(names)) is not None:
         names.append(bd.tdpd_kernel_name(h, len(names)))
     pair_mode = bd.tdpd_pair_mode(h)
+    sort_mode, sort_ms = bd.tdpd_sort_mode(h)
     shape_skin, shape_m, shape_ms = bd.tdpd_list_shape(h)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device='cuda')
 
@@ -509,7 +512,11 @@ def run_native(args):
                        'shape': ('timed at commit: ms per 16 steps for skins 0.2, 0.15, 0.25, 0.3, 0.4 at m = 2'
                                  '%s' % (', then at m = 3' if len(shape_ms) > 5 else '')) if len(shape_ms) else
                                 'not timed (pinned)',
-                       'shape_ms': [round(float(x), 4) for x in shape_ms]},
+                       'shape_ms': [round(float(x), 4) for x in shape_ms],
+                       'sort': ({1: 'kernel chain', 2: 'one thread-block cluster'}.get(sort_mode) if skin > 0
+                                else 'kernel chain (cell mode)'),
+                       'sort_ms': ([round(float(x), 4) for x in sort_ms] if (sort_ms > 0).all() else
+                                   'not timed')},
             'roofline': roof,
             'cpu_baseline': cpu,
             'e2e': e2e,
@@ -547,6 +554,8 @@ def main():
                     help='lanes per particle of the pair kernel (0: timed at commit)')
     ap.add_argument('--pair-mode', type=int, default=0, choices=[0, 1, 2],
                     help='pair kernel with lists: 1 full shell, 2 half shell, 0 chosen at commit')
+    ap.add_argument('--sort-mode', type=int, default=0, choices=[0, 1, 2],
+                    help='list-mode sort: 1 kernel chain, 2 one thread-block cluster, 0 chosen at commit')
     ap.add_argument('--skin', type=float, default=None,
                     help='neighbour-list skin; 0 = cell mode (stencil every step); default: the library\'s')
     args = ap.parse_args()

@@ -229,6 +229,26 @@ int tdpd_pair_mode(const tdpd_sys *s);
 tdpd_status tdpd_list_shape(tdpd_sys *s, float *skin, int *cells_per_cutoff, float *tuning_ms, int max_tuning,
                             int *n_tuning);
 
+/* How a neighbour-list step sorts the replicas that rebuild their lists
+ * (the reorder of Sec. 3.1): 0 (default) chosen at commit, 1 a chain of
+ * kernels over the whole GPU (binning, scan, scatter, gather), 2 one launch
+ * of one thread-block cluster (8 or 16 CTAs) doing all four, its phases
+ * separated by the cluster barrier -- for systems of at most 262,144
+ * particles and 1,048,576 cells, where the chain's launches cost more than
+ * its work. Both give the same sorted order and the same bits. With 0,
+ * commit times 16 steps of each (one graph replay each) where the cluster
+ * sort fits, and keeps it unless the chain is more than 3 % faster. Before
+ * tdpd_commit; TDPD_EINVAL for another value, TDPD_ESTATE after commit;
+ * commit fails with TDPD_EINVAL when 2 is set and the cluster sort does not
+ * fit (cell mode: the setting is ignored). */
+tdpd_status tdpd_set_sort_mode(tdpd_sys *s, int mode);
+
+/* The sort in use after commit (1 kernel chain, 2 one cluster; cell mode
+ * reports 1); before commit the value tdpd_set_sort_mode set. tuning_ms (may
+ * be NULL, 2 floats): the times commit took for 16 steps with the cluster
+ * and with the chain, -1 when it did not time them. */
+int tdpd_sort_mode(const tdpd_sys *s, float *tuning_ms);
+
 /* Skin of the Verlet neighbour lists of the pair kernel (length units): each
  * particle keeps the partners within max(rc, rcc) + skin found at a list
  * build; a replica rebuilds its lists (and re-sorts its cells) in the step

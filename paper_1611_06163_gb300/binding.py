@@ -74,6 +74,8 @@ def _load():
         'tdpd_set_pair_mode': ([P, I], I),
         'tdpd_list_shape': ([P, C.POINTER(C.c_float), C.POINTER(I), P, I, C.POINTER(I)], I),
         'tdpd_pair_mode': ([P], I),
+        'tdpd_set_sort_mode': ([P, I], I),
+        'tdpd_sort_mode': ([P, P], I),
         'tdpd_set_random_flux': ([P, C.c_float, C.c_float], I),
         'tdpd_set_body_force_profile': ([P, I], I),
         'tdpd_set_cylinder_wall': ([P, F], I),
@@ -204,6 +206,18 @@ def tdpd_set_pair_mode(h, mode):
 
 def tdpd_pair_mode(h):
     return int(lib.tdpd_pair_mode(h))
+
+
+def tdpd_set_sort_mode(h, mode):
+    _chk(h, lib.tdpd_set_sort_mode(h, int(mode)))
+
+
+def tdpd_sort_mode(h):
+    """(sort in use: 1 kernel chain, 2 one cluster; commit's times of 16 steps
+    with the cluster and with the chain in ms, -1 when not timed)."""
+    t = np.full(2, -1.0, np.float32)
+    m = int(lib.tdpd_sort_mode(h, _ptr(t)))
+    return m, t.copy()
 
 
 def tdpd_list_shape(h):
@@ -488,6 +502,8 @@ def create_from(desc, stream_ptr=None):
             tdpd_set_lanes(h, desc['lanes'])
         if desc.get('pair_mode') is not None:
             tdpd_set_pair_mode(h, desc['pair_mode'])
+        if desc.get('sort_mode') is not None:
+            tdpd_set_sort_mode(h, desc['sort_mode'])
         if stream_ptr:
             tdpd_set_stream(h, stream_ptr)
     except Exception:

@@ -70,6 +70,9 @@ struct tdpd_sys {
     int lpp = 1;
     int lanes_fixed = 0;   // 0: timed at commit
     int mode_fixed = 0;    // pair mode: 0 chosen at commit, 1 full shell, 2 half shell
+    int sort_fixed = 0;    // list-mode sort: 0 chosen at commit, 1 kernel chain, 2 one cluster
+    int sort_ctas = 0;     // CTAs of the one-cluster sort in use (0: the kernel chain)
+    std::vector<float> sort_ms;    // commit's timing of the two sorts (ms per 16 steps: cluster, chain)
     std::vector<float> shape_ms;   // commit's timing of the candidate list shapes (ms per 16 steps)
     int shape_win = -1;            // the shape chosen (-1: not timed)
     struct {
@@ -434,7 +437,7 @@ tdpd_status free_device(tdpd_sys *s)
 }
 
 const char *const KERNEL_NAMES[] = {"scan",       "scatter_keys", "rank_gather", "mem_gather", "mem_forces",
-                                    "pair",       "decide",       "bin",         "list_build"};
+                                    "pair",       "decide",       "bin",         "list_build", "sort"};
 
 // ref_in: which reference point buffer this evaluation reads; its K-Gather
 // writes the other one and the (A, V) buffer of the same index. inc: a step
@@ -523,12 +526,38 @@ bool pair_builds_lists(const tdpd_sys *s)
     return true;
 }
 
+// The one-cluster sort of step p (reading buffer p): its decision reads the
+// maxima of the last epilogue, like k_bin_next's inline decision.
+SortSmallArgs sort_small_args(tdpd_sys *s, int p)
+{
+    SortSmallArgs a;
+    a.cur = s->buf[p];
+    a.nxt = s->buf[1 - p];
+    a.reps = s->d_reps;
+    a.n = s->N;
+    a.ns_rt = s->ns;
+    a.nc = s->NC;
+    a.count = s->count;
+    a.cell_start = s->cell_start;
+    a.inv = s->inv;
+    a.cellrank = s->cellrank;
+    a.keys = s->keys;
+    a.D = DecideArgs{s->disp[p], s->disp[1 - p], s->rb, s->step_ctr, s->builds, (int)s->reps.size()};
+    a.Qa = quarantine(s);
+    return a;
+}
+
+// Cells the one-cluster sort may scan (its particle limit depends on the
+// cluster size: SORT_SMALL_ITEMS per thread).
+constexpr int SORT_SMALL_MAX_NC = 1 << 20;
+
 // Kernel kinds one step launches, in order (indices into KERNEL_NAMES).
 std::vector<int> step_kernels(const tdpd_sys *s)
 {
     std::vector<int> k;
     if (s->use_list) {
-        if (inline_decide(s)) k = {7, 0, 1, 2};
+        if (s->sort_ctas) k = {9};
+        else if (inline_decide(s)) k = {7, 0, 1, 2};
         else k = {6, 7, 0, 1, 2};
         if (!pair_builds_lists(s)) k.push_back(8);
     } else {
@@ -580,7 +609,10 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
         // rebuild the lists of the replicas whose particles moved more than
         // half their skin; the others keep their lists and their slots
         const uint32_t *any = s->rb + nrep;
-        if (inline_decide(s)) {
+        if (s->sort_ctas) {
+            launch_sort_small(sort_small_args(s, p), s->sort_ctas, st);
+            mark();
+        } else if (inline_decide(s)) {
             const DecideArgs d{s->disp[p], s->disp[1 - p], s->rb, s->step_ctr, s->builds, nrep};
             launch_bin_next(cur, s->d_reps, s->N, s->count, s->tile_sum[0], s->cellrank, s->rb, any, st, d);
             mark();
@@ -590,13 +622,16 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
             launch_bin_next(cur, s->d_reps, s->N, s->count, s->tile_sum[0], s->cellrank, s->rb, any, st);
             mark();
         }
-        launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[0], s->tile_sum[1], s->step_ctr, 0, st, any);
-        mark();
-        launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st, any, s->rb);
-        mark();
-        launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st,
-                           s->rb, nrep, s->tile_sum[0], s->n_tiles, quarantine(s));
-        mark();
+        if (!s->sort_ctas) {
+            launch_scan(s->count, s->cell_start, s->n_tiles, s->tile_sum[0], s->tile_sum[1], s->step_ctr, 0, st,
+                        any);
+            mark();
+            launch_scatter_keys(cur, s->cellrank, s->cell_start, s->keys, s->N, st, any, s->rb);
+            mark();
+            launch_rank_gather(cur, nxt, s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, s->N, s->ns, 1, st,
+                               s->rb, nrep, s->tile_sum[0], s->n_tiles, quarantine(s));
+            mark();
+        }
         if (!pair_builds_lists(s)) {
             launch_list_build(list_args(s, nxt, s->rb, s->nl_cap), st);
             mark();
@@ -1026,6 +1061,58 @@ tdpd_status tune_shape(tdpd_sys *s, const std::vector<Shape> &shapes)
     return TDPD_OK;
 }
 
+// List mode: the sort of a step as one cluster launch or as the kernel chain.
+// Both give the same bits; unless the caller pinned one, time 16 steps of
+// each as one graph replay (after one warm-up replay) and keep the cluster
+// unless the chain is more than 3 % faster; then reload the host's state.
+tdpd_status tune_sort(tdpd_sys *s)
+{
+    s->sort_ctas = 0;
+    s->sort_ms.clear();
+    if (!s->use_list || s->sort_fixed == 1) return TDPD_OK;
+    int ctas = s->NC <= SORT_SMALL_MAX_NC ? sort_small_ctas(s->ns) : 0;
+    const int max_n = ctas * SORT_SMALL_THREADS * SORT_SMALL_ITEMS;
+    if (s->N > max_n) ctas = 0;
+    if (s->sort_fixed == 2) {
+        if (!ctas)
+            return fail(s, TDPD_EINVAL, "the one-cluster sort needs at most %d particles and %d cells (here %d, %d) "
+                        "and a resident cluster of 8 or 16 CTAs", 16 * SORT_SMALL_THREADS * SORT_SMALL_ITEMS,
+                        SORT_SMALL_MAX_NC, s->N, s->NC);
+        s->sort_ctas = ctas;
+        return TDPD_OK;
+    }
+    if (!ctas) return TDPD_OK;
+    constexpr int STEPS = 16;
+    cudaStream_t st = exec_stream(s);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float t[2] = {1e30f, 1e30f};
+    tdpd_status rc = TDPD_OK;
+    for (int k = 0; k < 2 && !rc; ++k) {
+        s->sort_ctas = k == 0 ? ctas : 0;
+        cudaGraphExec_t g = nullptr;
+        if ((rc = capture(s, s->parity, STEPS, &g))) break;
+        cudaError_t e = cudaGraphLaunch(g, st);            // warm-up (an even count: same parity after)
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(g, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t[k], e0, e1);
+        cudaGraphExecDestroy(g);
+        if (e != cudaSuccess) rc = fail(s, TDPD_ECUDA, "sort tuning: %s", cudaGetErrorString(e));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    s->sort_ms.assign(t, t + 2);
+    s->sort_ctas = t[0] <= 1.03f * t[1] ? ctas : 0;
+    s->step = 0;
+    if ((rc = init_state(s))) return rc;
+    if (s->builds) CU(cudaMemsetAsync(s->builds, 0, sizeof(uint32_t) * s->reps.size(), st));
+    return TDPD_OK;
+}
+
 tdpd_status commit(tdpd_sys *s)
 {
     if (s->committed) return TDPD_OK;
@@ -1295,6 +1382,7 @@ tdpd_status commit(tdpd_sys *s)
     CU(cudaEventCreateWithFlags(&s->gathered, cudaEventDisableTiming));
     if (!shapes.empty() && (rc = tune_shape(s, shapes))) return rc;
     if (s->lanes_fixed == 0 && (rc = autotune(s))) return rc;
+    if ((rc = tune_sort(s))) return rc;
     const int nk = (int)step_kernels(s).size();
     for (int k = 0; k <= nk; ++k) CU(cudaEventCreate(&s->ev[k]));
     s->n_ev = nk + 1;
@@ -1616,6 +1704,27 @@ int tdpd_pair_mode(const tdpd_sys *s)
     if (!s) return 0;
     if (!s->committed) return s->mode_fixed;
     return s->half ? 2 : 1;
+}
+
+tdpd_status tdpd_set_sort_mode(tdpd_sys *s, int mode)
+{
+    if (!s) return fail(nullptr, TDPD_EINVAL, "null handle");
+    if (s->committed) return fail(s, TDPD_ESTATE, "the sort is fixed after commit");
+    if (mode < 0 || mode > 2)
+        return fail(s, TDPD_EINVAL, "sort mode must be 0 (chosen at commit), 1 (kernel chain) or 2 (one cluster)");
+    s->sort_fixed = mode;
+    return TDPD_OK;
+}
+
+int tdpd_sort_mode(const tdpd_sys *s, float *tuning_ms)
+{
+    if (!s) return 0;
+    if (!s->committed) return s->sort_fixed;
+    if (tuning_ms) {
+        tuning_ms[0] = s->sort_ms.size() == 2 ? s->sort_ms[0] : -1.0f;
+        tuning_ms[1] = s->sort_ms.size() == 2 ? s->sort_ms[1] : -1.0f;
+    }
+    return s->sort_ctas ? 2 : 1;
 }
 
 tdpd_status tdpd_set_skin(tdpd_sys *s, float skin)

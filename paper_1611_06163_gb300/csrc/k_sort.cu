@@ -6,6 +6,8 @@
 // Order within a cell is by particle id, so the sorted layout -- and with it
 // every floating-point summation order -- depends only on the state, not on
 // the order in which atomics happened to land.
+#include <cooperative_groups.h>
+
 #include "launch.h"
 
 namespace tdpd {
@@ -201,6 +203,224 @@ __global__ void k_rank_gather(Buffers cur, Buffers nxt, const RepParams *__restr
     }
 }
 
+// The sort of a list-mode step for a small system in one launch. The grid is
+// one thread-block cluster, whose CTAs are resident together, so the phases
+// are separated by the cluster's hardware barrier (no flag is polled). Each
+// thread owns up to ITEMS particles (slots g, g + G, ...) and keeps their
+// state in registers from the binning to the final write:
+//   decision   every CTA reads each replica's largest displacement (the last
+//              pair epilogue's) and takes the rebuild decision itself; CTA 0
+//              records it, clears the next maxima, counts the builds,
+//              advances the step counter and sets the quarantine;
+//   binning    (some replica rebuilds) cell and arrival rank of each owned
+//              particle's predicted position, a kept replica's count to its
+//              first cell; a quarantined replica that keeps its slots is
+//              copied as it stands;
+//   scan       each CTA scans a contiguous range of cells, its offset the sum
+//              of the lower CTAs' totals read from their shared memory;
+//   scatter    each owned particle's (id, old slot) key into its cell's range;
+//   placement  each owned particle's slot: its cell's start plus the number
+//              of keys of the cell with a smaller id; the predicted state
+//              (velocity-Verlet predictor, as in k_rank_gather) is written
+//              there.
+// The order (cell, then id) is unique, so the result is that of k_bin_next,
+// k_scan, k_scatter_keys and k_rank_gather, bit for bit.
+template <int NS, int ITEMS>
+__global__ void __launch_bounds__(SORT_SMALL_THREADS, 1) k_sort_small(SortSmallArgs A)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ int wsum[SORT_SMALL_THREADS / 32];
+    __shared__ int cta_total;
+    pdl_enter();
+    const int ns = NS > 0 ? NS : A.ns_rt;
+    const int nct = gridDim.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int G = nct * SORT_SMALL_THREADS;
+    const int g = blockIdx.x * SORT_SMALL_THREADS + tid;
+    const DecideArgs &D = A.D;
+    const uint32_t *err = A.Qa.err;
+
+    int a = 0, h = 0;
+    for (int r = tid; r < D.n_rep; r += SORT_SMALL_THREADS) {
+        const bool rebuild = __uint_as_float(D.disp[r]) > A.reps[r].half_skin2;
+        const bool held = err[r] != 0u;
+        a |= rebuild;
+        h |= held;
+        if (blockIdx.x == 0) {
+            D.rb[r] = rebuild ? 1u : 0u;
+            D.disp_clear[r] = 0u;
+            if (rebuild) D.builds[r] += 1u;
+            A.Qa.quar[r] = held ? 1u : 0u;
+        }
+    }
+    const bool any = __syncthreads_or(a) != 0;
+    const bool any_held = __syncthreads_or(h) != 0;
+    if (blockIdx.x == 0 && tid == 0) {
+        D.rb[D.n_rep] = any ? 1u : 0u;
+        *D.step_ctr += 1u;
+    }
+    // no rebuild and no quarantined replica (the common step): every slot
+    // keeps its particle, whose predicted state the last epilogue wrote
+    if (!any && !any_held) return;
+
+    // binning of the owned particles (a rebuilding replica's: kept in
+    // registers; a quarantined replica that keeps its slots: copied now)
+    float4 p[ITEMS], v[ITEMS], f[ITEMS];
+    float vtw[ITEMS];
+    int cell[ITEMS], rank[ITEMS];
+    bool mine[ITEMS], pred[ITEMS];
+    float cs_[ITEMS][NS > 0 ? NS : 1], qs_[ITEMS][NS > 0 ? NS : 1];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int k = g + i * G;
+        mine[i] = false;
+        pred[i] = false;
+        cell[i] = rank[i] = 0;
+        if (k >= A.n) continue;
+        v[i] = A.cur.vel[k];
+        const int r = wbits(v[i].w);
+        const RepParams &P = A.reps[r];
+        const bool rebuild = __uint_as_float(D.disp[r]) > P.half_skin2;
+        const bool held = err[r] != 0u;
+        if (rebuild) {
+            p[i] = A.cur.pos[k];
+            f[i] = A.cur.frc[k];
+            vtw[i] = A.cur.vt[k].w;
+            if constexpr (NS > 0) {
+#pragma unroll
+                for (int sp = 0; sp < NS; ++sp) {
+                    cs_[i][sp] = A.cur.C[(size_t)k * NS + sp];
+                    qs_[i][sp] = A.cur.Q[(size_t)k * NS + sp];
+                }
+            }
+            const int type = (int)((uint32_t)wbits(p[i].w) >> 24);
+            const bool frozen = (P.frozen_mask >> type) & 1u;
+            float3 rn = make_float3(p[i].x, p[i].y, p[i].z);
+            bool flip = false;
+            if (!frozen) rn = predict_pos(P, p[i], v[i], f[i], flip);
+            cell[i] = cell_of(P, rn.x, rn.y, rn.z);
+            rank[i] = atomicAdd(A.count + cell[i], 1);
+            mine[i] = true;
+            pred[i] = !frozen && !held;
+            if (pred[i]) {
+                p[i].x = rn.x; p[i].y = rn.y; p[i].z = rn.z;
+                if (flip) { v[i].x = -v[i].x; v[i].y = -v[i].y; v[i].z = -v[i].z; }
+            }
+        } else {
+            if (k == P.pbase && any) atomicAdd(A.count + P.cell_base, P.n);
+            if (held) {
+                // as the gather copies a quarantined replica: no predictor
+                const float4 q = A.cur.vel[k];
+                A.nxt.pos[k] = A.cur.pos[k];
+                A.nxt.vel[k] = q;
+                A.nxt.frc[k] = A.cur.frc[k];
+                A.nxt.vt[k] = make_float4(q.x, q.y, q.z, A.cur.vt[k].w);
+                for (int sp = 0; sp < ns; ++sp) {
+                    const float c = A.cur.C[(size_t)k * ns + sp];
+                    A.nxt.C[(size_t)k * ns + sp] = c;
+                    A.nxt.Q[(size_t)k * ns + sp] = A.cur.Q[(size_t)k * ns + sp];
+                    A.nxt.Ct[(size_t)k * ns + sp] = c;
+                }
+                A.inv[P.pbase + (wbits(A.cur.pos[k].w) & ID_MASK)] = k;
+            }
+        }
+    }
+    if (!any) return;              // uniform over the cluster: no barrier follows
+    __threadfence();
+    cl.sync();
+
+    // scan: CTA b owns cells [c0, c1), each thread a run of `per` of them
+    {
+        const int chunk = (A.nc + nct - 1) / nct;
+        const int c0 = min(blockIdx.x * chunk, A.nc), c1 = min(c0 + chunk, A.nc);
+        const int per = (chunk + SORT_SMALL_THREADS - 1) / SORT_SMALL_THREADS;
+        const int lo = min(c0 + tid * per, c1), hi = min(lo + per, c1);
+        int s = 0;
+        for (int c = lo; c < hi; ++c) s += __ldcg(A.count + c);
+        int x = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int t = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t;
+            if (lane == 31) cta_total = t;
+        }
+        cl.sync();                                   // every CTA's total in its shared memory
+        // the lower CTAs' totals, one per lane (at most 16 CTAs)
+        int base = lane < (int)blockIdx.x ? *cl.map_shared_rank(&cta_total, lane) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) base += __shfl_xor_sync(0xffffffffu, base, o);
+        int e = base + x - s + (w > 0 ? wsum[w - 1] : 0);
+        for (int c = lo; c < hi; ++c) {
+            const int cnt = __ldcg(A.count + c);
+            A.cell_start[c] = e;
+            A.count[c] = 0;
+            e += cnt;
+        }
+        if (blockIdx.x == nct - 1 && tid == 0) A.cell_start[A.nc] = base + cta_total;
+    }
+    __threadfence();
+    cl.sync();
+
+    // scatter the owned keys
+    int lo_[ITEMS], hi_[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (!mine[i]) continue;
+        lo_[i] = __ldcg(A.cell_start + cell[i]);
+        hi_[i] = __ldcg(A.cell_start + cell[i] + 1);
+        A.keys[lo_[i] + rank[i]] = make_int2(wbits(p[i].w) & ID_MASK, g + i * G);
+    }
+    __threadfence();
+    cl.sync();
+
+    // place the owned particles
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (!mine[i]) continue;
+        const int k = g + i * G;
+        const int id = wbits(p[i].w) & ID_MASK;
+        int rk = 0;
+        for (int e = lo_[i]; e < hi_[i]; ++e) rk += (__ldcg(A.keys + e).x < id);
+        const int dst = lo_[i] + rk;
+        const RepParams &P = A.reps[wbits(v[i].w)];
+        float4 vtn = make_float4(v[i].x, v[i].y, v[i].z, vtw[i]);
+        if (pred[i]) {
+            vtn.x = __fmaf_rn(P.ldt, f[i].x, v[i].x);
+            vtn.y = __fmaf_rn(P.ldt, f[i].y, v[i].y);
+            vtn.z = __fmaf_rn(P.ldt, f[i].z, v[i].z);
+        }
+        A.nxt.pos[dst] = p[i];
+        A.nxt.vel[dst] = v[i];
+        A.nxt.frc[dst] = f[i];
+        A.nxt.vt[dst] = vtn;
+        A.inv[P.pbase + id] = dst;
+        for (int sp = 0; sp < ns; ++sp) {
+            float c, q;
+            if constexpr (NS > 0) {
+                c = cs_[i][sp];
+                q = qs_[i][sp];
+            } else {
+                c = A.cur.C[(size_t)k * ns + sp];
+                q = A.cur.Q[(size_t)k * ns + sp];
+            }
+            A.nxt.C[(size_t)dst * ns + sp] = c;
+            A.nxt.Q[(size_t)dst * ns + sp] = q;
+            A.nxt.Ct[(size_t)dst * ns + sp] = pred[i] ? __fmaf_rn(P.ldt, q, c) : c;
+        }
+    }
+}
+
 static inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
 void launch_bin_init(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum,
@@ -235,6 +455,83 @@ void launch_rank_gather(const Buffers &cur, const Buffers &nxt, const RepParams 
     case 1: launch_pdl(k_rank_gather<1>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles, q); break;
     case 2: launch_pdl(k_rank_gather<2>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles, q); break;
     default: launch_pdl(k_rank_gather<0>, g, 256, st, cur, nxt, reps, keys, cellrank, cell_start, inv, n, ns, predict, rb, n_rep, tile_zero, n_tiles, q); break;
+    }
+}
+
+
+template <int NS>
+static int sort_small_ctas_ns()
+{
+    auto k = k_sort_small<NS, SORT_SMALL_ITEMS>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
+    for (int c : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(SORT_SMALL_THREADS);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = c;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n >= 1) {
+            // the one-item form launches with the same cluster shape
+            if (cudaFuncSetAttribute(k_sort_small<NS, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess)
+                cudaGetLastError();
+            return c;
+        }
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+int sort_small_ctas(int ns)
+{
+    switch (ns) {
+    case 1: return sort_small_ctas_ns<1>();
+    case 2: return sort_small_ctas_ns<2>();
+    default: return sort_small_ctas_ns<0>();
+    }
+}
+
+template <int NS, int ITEMS>
+static void launch_sort_small_ns(const SortSmallArgs &a, int ctas, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(SORT_SMALL_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    cudaLaunchKernelEx(&cfg, k_sort_small<NS, ITEMS>, a);
+}
+
+template <int NS>
+static void launch_sort_small_items(const SortSmallArgs &a, int ctas, cudaStream_t st)
+{
+    if (a.n <= ctas * SORT_SMALL_THREADS) launch_sort_small_ns<NS, 1>(a, ctas, st);
+    else launch_sort_small_ns<NS, SORT_SMALL_ITEMS>(a, ctas, st);
+}
+
+void launch_sort_small(const SortSmallArgs &a, int ctas, cudaStream_t st)
+{
+    // the caller checks the size (commit never selects a larger system)
+    if (a.n <= 0 || ctas <= 0 || a.n > ctas * SORT_SMALL_THREADS * SORT_SMALL_ITEMS) return;
+    switch (a.ns_rt) {
+    case 1: launch_sort_small_items<1>(a, ctas, st); break;
+    case 2: launch_sort_small_items<2>(a, ctas, st); break;
+    default: launch_sort_small_items<0>(a, ctas, st); break;
     }
 }
 

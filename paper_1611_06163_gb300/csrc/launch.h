@@ -179,6 +179,27 @@ struct DecideArgs {
     uint32_t *disp_clear, *rb, *step_ctr, *builds;
     int n_rep;
 };
+// The one-launch sort of a list-mode step for a small system (k_sort_small):
+// rebuild decision, binning, scan, scatter and gather in one thread-block
+// cluster, separated by its hardware barrier.
+constexpr int SORT_SMALL_THREADS = 1024;
+constexpr int SORT_SMALL_ITEMS = 2;      // particles per thread at most
+struct SortSmallArgs {
+    Buffers cur, nxt;
+    const RepParams *reps;
+    int n, ns_rt, nc;            // particles, species, cells
+    int *count;                  // [nc] zero on entry and on return
+    int *cell_start;             // [nc + 1]
+    int *inv;
+    int2 *cellrank, *keys;       // [n] scratch
+    DecideArgs D;
+    Quarantine Qa;
+};
+// CTAs of the cluster for ns species: 16 where a 16-CTA cluster of the kernel
+// can be resident, else 8, else 0 (not available); it serves at most
+// ctas x SORT_SMALL_THREADS x SORT_SMALL_ITEMS particles
+int sort_small_ctas(int ns);
+void launch_sort_small(const SortSmallArgs &a, int ctas, cudaStream_t st);
 // cell and rank of the next predicted position of each particle of a
 // rebuilding replica (list mode, when any replica rebuilds; rb[r]: replica r
 // rebuilds, unless d.disp is set and the decision is taken here); a replica

@@ -31,7 +31,9 @@ def _same(a, b):
     return all(np.array_equal(x, y) for x, y in zip(a, b))
 
 
-def test_non_finite_replica_is_reported_and_quarantined():
+@pytest.mark.parametrize('sort_mode', [1, 2])
+def test_non_finite_replica_is_reported_and_quarantined(sort_mode):
+    """(With the list-mode sort as the kernel chain and as one cluster.)"""
     bd = B()
     reps = W.replica_ensemble(n_rep=4, seed=301, side_lo=8, side_hi=10)
     bad = 2
@@ -40,6 +42,7 @@ def test_non_finite_replica_is_reported_and_quarantined():
     batch = bd.tdpd_batch_create(hs)
     try:
         bd.tdpd_set_lanes(batch, 4)
+        bd.tdpd_set_sort_mode(batch, sort_mode)
         bd.tdpd_commit(batch)
         st = bd.tdpd_replica_status(batch)
         assert list(st) == [0, 0, ENONFINITE, 0]
@@ -62,7 +65,8 @@ def test_non_finite_replica_is_reported_and_quarantined():
             bd.tdpd_destroy(h)
 
 
-def test_list_overflow_is_reported_not_silent():
+@pytest.mark.parametrize('sort_mode', [1, 2])
+def test_list_overflow_is_reported_not_silent(sort_mode):
     """The lists are sized at commit (1.5 x the longest, plus 16). A state
     loaded into one replica with every particle squeezed into one eighth of
     its box (eight times the density) needs longer lists: the build stops at
@@ -74,6 +78,7 @@ def test_list_overflow_is_reported_not_silent():
     batch = bd.tdpd_batch_create(hs)
     try:
         bd.tdpd_set_lanes(batch, 4)
+        bd.tdpd_set_sort_mode(batch, sort_mode)
         bd.tdpd_commit(batch)
         assert (bd.tdpd_replica_status(batch) == 0).all()
         x, v, c = bd.tdpd_read_state(batch, 1, 1)

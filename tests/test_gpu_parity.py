@@ -702,3 +702,67 @@ def test_list_shape_timed_at_commit():
         assert len(ms) == 0 and abs(skin - 0.2) < 1e-6 and m == 2
     finally:
         bd.tdpd_destroy(h)
+
+
+def _run_sort(bd, descs, sort_mode, steps, lanes=4):
+    hs = [bd.create_from(dict(d, lanes=lanes, sort_mode=sort_mode)) for d in descs]
+    h = hs[0] if len(hs) == 1 else bd.tdpd_batch_create(hs)
+    try:
+        if len(hs) > 1:
+            bd.tdpd_set_lanes(h, lanes)
+            bd.tdpd_set_sort_mode(h, sort_mode)
+        bd.tdpd_commit(h)
+        assert bd.tdpd_sort_mode(h)[0] == sort_mode
+        bd.tdpd_step(h, steps)
+        assert (bd.tdpd_replica_status(h) == 0).all()
+        out = [bd.tdpd_read_state(h, k, 1) + bd.tdpd_read_forces(h, k, 1) for k in range(len(descs))]
+        builds = [bd.tdpd_list_rebuilds(h, k) for k in range(len(descs))]
+        return out, builds
+    finally:
+        if len(hs) > 1:
+            bd.tdpd_destroy(h)
+        for x in hs:
+            bd.tdpd_destroy(x)
+
+
+@pytest.mark.parametrize('pair_mode', [1, 2])
+def test_one_cluster_sort_gives_the_chains_bits(pair_mode):
+    """The list-mode sort as one thread-block cluster launch and as the chain
+    of kernels: over 40 steps with list rebuilds (some replicas rebuilding
+    while others keep their slots, in the batch), the same state and forces
+    bit for bit, and the same rebuild counts; the cluster path's trajectory
+    also matches the oracle."""
+    bd = B()
+    one = [dict(W.single_rbc(L=12.0, diameter=5.0, seed=47), pair_mode=pair_mode)]
+    many = [dict(r, pair_mode=pair_mode) for r in W.replica_ensemble(n_rep=5, seed=79, side_lo=8, side_hi=11)]
+    for descs in (one, many):
+        a, ba = _run_sort(bd, descs, 1, 40)
+        b, bb = _run_sort(bd, descs, 2, 40)
+        assert ba == bb and min(ba) > 0, (ba, bb)
+        for x, y in zip(a, b):
+            for u, v in zip(x, y):
+                assert np.array_equal(u, v)
+    d = dict(one[0], sort_mode=2, lanes=4)
+    err, obs, o, h = run_vs_oracle(d, 10)
+    check_traj(err, d)
+
+
+def test_sort_mode_chosen_at_commit_and_refused_when_too_large():
+    """Left to commit, a small system's two sorts are timed (16 steps each)
+    and the one kept is the cluster unless the chain is more than 3 % faster;
+    pinning the cluster sort on 786,432 particles is refused at commit."""
+    bd = B()
+    h = make(dict(W.single_rbc(L=12.0, diameter=5.0, seed=49), lanes=4))
+    try:
+        mode, t = bd.tdpd_sort_mode(h)
+        assert (t > 0).all(), t
+        assert mode == (2 if t[0] <= 1.03 * t[1] else 1), (mode, t)
+    finally:
+        bd.tdpd_destroy(h)
+    h = bd.create_from(dict(W.fluid_box(L=64.0, rho=3.0, seed=7), lanes=1, sort_mode=2))
+    try:
+        with pytest.raises(bd.TdpdError) as e:
+            bd.tdpd_commit(h)
+        assert 'one-cluster sort' in str(e.value)
+    finally:
+        bd.tdpd_destroy(h)
