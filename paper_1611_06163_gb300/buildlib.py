@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, 'csrc')
 INC = os.path.join(ROOT, 'include')
 OUT = os.path.join(HERE, '_build')
 LIB = os.path.join(HERE, 'libtdpd.so')
-SOURCES = ['engine.cu', 'k_sort.cu', 'k_pair.cu', 'k_list.cu', 'k_membrane.cu', 'k_misc.cu', 'noalloc.cu', 'mlp.cu']
+SOURCES = ['engine.cu', 'k_sort.cu', 'k_pair.cu', 'k_pair_std.cu', 'k_list.cu', 'k_membrane.cu', 'k_misc.cu', 'noalloc.cu', 'mlp.cu']
 
 NVCC_FLAGS = ['-gencode', 'arch=compute_103a,code=sm_103a', '-lineinfo', '-O3', '-std=c++17',
               '-Xcompiler', '-fPIC', '-Xcompiler', '-O2', '-I' + INC, '-I' + CSRC]

@@ -469,8 +469,11 @@ PairArgs pair_args(tdpd_sys *s, const Buffers &b, int integrate, int *tile_sum, 
     a.cellrank = s->cellrank; a.err = s->errw; a.quar = s->quar; a.step_ctr = s->step_ctr; a.n = s->N; a.ns = s->ns;
     a.integrate = integrate;
     a.lpp = s->lpp;
-    for (const HostRep &R : s->reps)
+    a.std_exp = 1;
+    for (const HostRep &R : s->reps) {
         if (R.qr_ms > 0.0f) a.qr = 1;
+        if (!(R.cfg.s_f == 2.0f && R.cfg.s_c == 2.0f)) a.std_exp = 0;
+    }
     if (s->use_list) {
         a.pre = b.pos == s->buf[0].pos ? s->buf[1] : s->buf[0];
         a.nl = s->nl; a.nlc = s->nlc; a.cap = s->nl_cap; a.xb = s->xb; a.disp_next = disp_next;

@@ -57,6 +57,7 @@ struct PairArgs {
     int integrate;               // 0: forces only (commit / set_state); 1: full step
     int lpp;                     // lanes per particle: 1, 2, 4, 8, 16 or 32
     int qr;                      // some replica has the random flux (general kernel)
+    int std_exp;                 // every replica has s_f = 2 and s_c = 2 (kernels with them fixed)
     // neighbour-list mode (nl != nullptr): partners from the list instead of
     // the cell stencil, no binning in the epilogue
     const int *nl;               // [warps][cap][32] partner slots per lane
