@@ -270,6 +270,35 @@ __global__ void __launch_bounds__(SORT_SMALL_THREADS, 1) k_sort_small(SortSmallA
     int cell[ITEMS], rank[ITEMS];
     bool mine[ITEMS], pred[ITEMS];
     float cs_[ITEMS][NS > 0 ? NS : 1], qs_[ITEMS][NS > 0 ? NS : 1];
+    bool rebuild[ITEMS], held[ITEMS];
+    // every owned particle's loads first (all in flight together), then the
+    // arithmetic and the atomics
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int k = g + i * G;
+        rebuild[i] = held[i] = false;
+        if (k < A.n) {
+            v[i] = A.cur.vel[k];
+            const int r = wbits(v[i].w);
+            rebuild[i] = __uint_as_float(D.disp[r]) > A.reps[r].half_skin2;
+            held[i] = err[r] != 0u;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int k = g + i * G;
+        if (!rebuild[i]) continue;
+        p[i] = A.cur.pos[k];
+        f[i] = A.cur.frc[k];
+        vtw[i] = A.cur.vt[k].w;
+        if constexpr (NS > 0) {
+#pragma unroll
+            for (int sp = 0; sp < NS; ++sp) {
+                cs_[i][sp] = A.cur.C[(size_t)k * NS + sp];
+                qs_[i][sp] = A.cur.Q[(size_t)k * NS + sp];
+            }
+        }
+    }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const int k = g + i * G;
@@ -277,22 +306,8 @@ __global__ void __launch_bounds__(SORT_SMALL_THREADS, 1) k_sort_small(SortSmallA
         pred[i] = false;
         cell[i] = rank[i] = 0;
         if (k >= A.n) continue;
-        v[i] = A.cur.vel[k];
-        const int r = wbits(v[i].w);
-        const RepParams &P = A.reps[r];
-        const bool rebuild = __uint_as_float(D.disp[r]) > P.half_skin2;
-        const bool held = err[r] != 0u;
-        if (rebuild) {
-            p[i] = A.cur.pos[k];
-            f[i] = A.cur.frc[k];
-            vtw[i] = A.cur.vt[k].w;
-            if constexpr (NS > 0) {
-#pragma unroll
-                for (int sp = 0; sp < NS; ++sp) {
-                    cs_[i][sp] = A.cur.C[(size_t)k * NS + sp];
-                    qs_[i][sp] = A.cur.Q[(size_t)k * NS + sp];
-                }
-            }
+        const RepParams &P = A.reps[wbits(v[i].w)];
+        if (rebuild[i]) {
             const int type = (int)((uint32_t)wbits(p[i].w) >> 24);
             const bool frozen = (P.frozen_mask >> type) & 1u;
             float3 rn = make_float3(p[i].x, p[i].y, p[i].z);
@@ -301,16 +316,16 @@ __global__ void __launch_bounds__(SORT_SMALL_THREADS, 1) k_sort_small(SortSmallA
             cell[i] = cell_of(P, rn.x, rn.y, rn.z);
             rank[i] = atomicAdd(A.count + cell[i], 1);
             mine[i] = true;
-            pred[i] = !frozen && !held;
+            pred[i] = !frozen && !held[i];
             if (pred[i]) {
                 p[i].x = rn.x; p[i].y = rn.y; p[i].z = rn.z;
                 if (flip) { v[i].x = -v[i].x; v[i].y = -v[i].y; v[i].z = -v[i].z; }
             }
         } else {
             if (k == P.pbase && any) atomicAdd(A.count + P.cell_base, P.n);
-            if (held) {
+            if (held[i]) {
                 // as the gather copies a quarantined replica: no predictor
-                const float4 q = A.cur.vel[k];
+                const float4 q = v[i];
                 A.nxt.pos[k] = A.cur.pos[k];
                 A.nxt.vel[k] = q;
                 A.nxt.frc[k] = A.cur.frc[k];
@@ -326,7 +341,9 @@ __global__ void __launch_bounds__(SORT_SMALL_THREADS, 1) k_sort_small(SortSmallA
         }
     }
     if (!any) return;              // uniform over the cluster: no barrier follows
-    __threadfence();
+    // (the cluster barrier's arrive has release and its wait acquire
+    // semantics at cluster scope, which orders these global writes for the
+    // other CTAs; their reads of them go through L2)
     cl.sync();
 
     // scan: CTA b owns cells [c0, c1), each thread a run of `per` of them
@@ -369,7 +386,6 @@ __global__ void __launch_bounds__(SORT_SMALL_THREADS, 1) k_sort_small(SortSmallA
         }
         if (blockIdx.x == nct - 1 && tid == 0) A.cell_start[A.nc] = base + cta_total;
     }
-    __threadfence();
     cl.sync();
 
     // scatter the owned keys
@@ -381,7 +397,6 @@ __global__ void __launch_bounds__(SORT_SMALL_THREADS, 1) k_sort_small(SortSmallA
         hi_[i] = __ldcg(A.cell_start + cell[i] + 1);
         A.keys[lo_[i] + rank[i]] = make_int2(wbits(p[i].w) & ID_MASK, g + i * G);
     }
-    __threadfence();
     cl.sync();
 
     // place the owned particles
@@ -391,7 +406,13 @@ __global__ void __launch_bounds__(SORT_SMALL_THREADS, 1) k_sort_small(SortSmallA
         const int k = g + i * G;
         const int id = wbits(p[i].w) & ID_MASK;
         int rk = 0;
-        for (int e = lo_[i]; e < hi_[i]; ++e) rk += (__ldcg(A.keys + e).x < id);
+        for (int e = lo_[i]; e < hi_[i]; e += 4) {
+            int kx[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) kx[u] = e + u < hi_[i] ? __ldcg(A.keys + e + u).x : id;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) rk += kx[u] < id;
+        }
         const int dst = lo_[i] + rk;
         const RepParams &P = A.reps[wbits(v[i].w)];
         float4 vtn = make_float4(v[i].x, v[i].y, v[i].z, vtw[i]);
