@@ -766,3 +766,43 @@ def test_sort_mode_chosen_at_commit_and_refused_when_too_large():
         assert 'one-cluster sort' in str(e.value)
     finally:
         bd.tdpd_destroy(h)
+
+
+def test_set_states_reports_the_first_bad_particle_of_a_large_batch():
+    """On a batch large enough for the host check of tdpd_set_states to run
+    in several chunks, the error names the first offending particle in load
+    order (a late replica's bad position does not mask an earlier one's
+    non-finite velocity), and the refused state changes nothing."""
+    bd = B()
+    reps = W.replica_ensemble(n_rep=32, seed=81, side_lo=12, side_hi=14, max_rbc=1)
+    hs = [bd.create_from(r) for r in reps]
+    b = bd.tdpd_batch_create(hs)
+    try:
+        bd.tdpd_set_lanes(b, 1)
+        bd.tdpd_commit(b)
+        states = [bd.tdpd_read_state(b, r, 1) for r in range(len(reps))]
+        n = [len(s[0]) for s in states]
+        assert sum(n) > 2 * 65536                     # at least two chunks
+        cat = [np.concatenate([s[k] for s in states]) for k in range(3)]
+        base = np.cumsum([0] + n)
+        bad = [c.copy() for c in cat]
+        bad[0][base[20] + 3, 1] = np.float32(reps[20]['L'][1])    # on the upper face: outside
+        bad[1][base[5] + 7, 2] = np.float32(np.inf)
+        with pytest.raises(bd.TdpdError) as e:
+            bd.tdpd_set_states(b, *bad)
+        assert e.value.status == 1 and 'replica 5 particle 7' in str(e.value), str(e.value)
+        bad[1][base[5] + 7, 2] = np.float32(0.0)
+        with pytest.raises(bd.TdpdError) as e:
+            bd.tdpd_set_states(b, *bad)
+        assert 'replica 20 particle 3' in str(e.value), str(e.value)
+        after = [bd.tdpd_read_state(b, r, 1) for r in range(len(reps))]
+        for p, q in zip(states, after):
+            for u, w in zip(p, q):
+                assert np.array_equal(u, w)
+        bd.tdpd_set_states(b, *cat)                      # the sound state loads
+        bd.tdpd_step(b, 2)
+        assert (bd.tdpd_replica_status(b) == 0).all()
+    finally:
+        bd.tdpd_destroy(b)
+        for h in hs:
+            bd.tdpd_destroy(h)
