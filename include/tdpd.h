@@ -233,9 +233,9 @@ tdpd_status tdpd_list_shape(tdpd_sys *s, float *skin, int *cells_per_cutoff, flo
  * (the reorder of Sec. 3.1): 0 (default) chosen at commit, 1 a chain of
  * kernels over the whole GPU (binning, scan, scatter, gather), 2 one launch
  * of one thread-block cluster (8 or 16 CTAs) doing all four, its phases
- * separated by the cluster barrier -- for systems of at most 262,144
- * particles and 1,048,576 cells, where the chain's launches cost more than
- * its work. Both give the same sorted order and the same bits. With 0,
+ * separated by the cluster barrier -- for systems of at most 32,768
+ * particles (16,384 where only an 8-CTA cluster fits) and 1,048,576 cells,
+ * where the chain's launches cost more than its work. Both give the same sorted order and the same bits. With 0,
  * commit times 16 steps of each (one graph replay each) where the cluster
  * sort fits, and keeps it unless the chain is more than 3 % faster. Before
  * tdpd_commit; TDPD_EINVAL for another value, TDPD_ESTATE after commit;
