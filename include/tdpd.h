@@ -306,15 +306,18 @@ tdpd_status tdpd_set_state(tdpd_sys *s, int replica, const float *pos, const flo
  * count; the layout tdpd_read_state gives replica by replica). The arrays go
  * to the device as they are (by DMA when pinned) and are read before the call
  * returns. TDPD_EINVAL for a null array, a position outside its replica's box
- * or a non-finite velocity (nothing is changed then). */
+ * or a non-finite velocity, naming the first such particle (nothing is
+ * changed then); the check runs on the device after the upload. Every state
+ * load (this call, tdpd_set_state, commit) takes each membrane's reference
+ * point for its area and volume sums from its vertices on the device: the
+ * centroid of the vertices unwrapped along the mesh by the minimum image. */
 tdpd_status tdpd_set_states(tdpd_sys *s, const float *pos, const float *vel, const float *conc);
 
 /* Device-memory variants for callers whose arrays live on the GPU (a torch
  * tensor's data pointer, say); the caller keeps ownership of its arrays.
  * tdpd_set_states_device: as tdpd_set_states with device pointers; the
  * check of positions and velocities runs on the device (TDPD_EINVAL, nothing
- * changed, on a violation), membranes' reference points are taken from a
- * host copy of the positions; returns when the arrays have been read.
+ * changed, on a violation); returns when the arrays have been read.
  * tdpd_read_state_device: enqueues on the library's stream (tdpd_set_stream)
  * a copy of replica r's state in load order into pos[3 n], vel[3 n],
  * conc[n ns] (any may be NULL) and returns at once: synchronise that stream

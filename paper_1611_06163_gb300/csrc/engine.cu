@@ -132,7 +132,6 @@ struct tdpd_sys {
     std::vector<int> rep_pbase, rep_rbc0;
     std::vector<RbcDev> h_rbcs;
     std::vector<Topo> topos;
-    std::vector<float4> h_ref;
     cudaGraphExec_t g1[2] = {nullptr, nullptr}, glong[2] = {nullptr, nullptr}, gtimed[2] = {nullptr, nullptr};
     cudaEvent_t ev[12] = {};
     int n_ev = 0;
@@ -674,36 +673,15 @@ void enqueue_step(tdpd_sys *s, int p, cudaStream_t st, cudaEvent_t *ev = nullptr
 constexpr size_t OBS_STAGE = (sizeof(double) * OBS_K + 15) / 16 * 16;
 constexpr float DEFAULT_SKIN = 0.2f;   // neighbour-list skin (length units)
 
-// Pinned staging area: observables, the step counters, the membranes'
-// reference points, then x[3N], v[3N], C[N*ns] in load order.
+// Pinned staging area: observables, the step counters, then x[3N], v[3N],
+// C[N*ns] in load order.
 uint32_t *stage_ctr(tdpd_sys *s) { return reinterpret_cast<uint32_t *>(s->h_stage + OBS_STAGE); }
-float4 *stage_ref(tdpd_sys *s) { return reinterpret_cast<float4 *>(s->h_stage + OBS_STAGE + 16); }
-float *stage_in(tdpd_sys *s) { return reinterpret_cast<float *>(stage_ref(s) + s->n_rbc); }
-size_t stage_bytes(int N, int ns, int n_rbc)
+float *stage_in(tdpd_sys *s) { return reinterpret_cast<float *>(s->h_stage + OBS_STAGE + 16); }
+size_t stage_bytes(int N, int ns)
 {
-    return OBS_STAGE + 16 + sizeof(float4) * n_rbc + sizeof(float) * (size_t)N * (6 + ns);
+    return OBS_STAGE + 16 + sizeof(float) * (size_t)N * (6 + ns);
 }
 
-// Reference point of membrane b (centroid of its unwrapped vertices) from the
-// load-order positions p of its replica.
-// verts: the membrane's own vertices (float[3 nv])
-float4 membrane_ref_v(const tdpd_sys *s, int b, const float *verts)
-{
-    const RbcDev &D = s->h_rbcs[b];
-    const HostRep &R = s->reps[D.rep];
-    std::vector<double> x;
-    unwrap(R, s->topos[D.topo], verts, x);
-    double c[3] = {0, 0, 0};
-    for (int v = 0; v < D.nv; ++v)
-        for (int k = 0; k < 3; ++k) c[k] += x[3 * v + k];
-    float cf[3];
-    for (int k = 0; k < 3; ++k) {
-        double y = c[k] / D.nv;
-        if (R.cfg.periodic[k]) y -= R.cfg.L[k] * std::floor(y / R.cfg.L[k]);
-        cf[k] = (float)y;
-    }
-    return make_float4(cf[0], cf[1], cf[2], 0.f);
-}
 
 // fn(lo, hi) over [0, n) in contiguous chunks on up to 16 host threads, one
 // thread when n is below min_chunk (the load paths' checks and reference
@@ -726,6 +704,10 @@ void host_parallel(size_t n, size_t min_chunk, F fn)
     fn((size_t)0, std::min(n, chunk));
     for (std::thread &x : th) x.join();
 }
+
+// Batches up to this many particles are checked on the host on load (while
+// their upload runs), larger ones on the device.
+constexpr int HOST_CHECK_MAX = 1 << 17;
 
 // First particle (load index over the whole batch) of pos/vel outside its
 // replica's box or with a non-finite velocity, or -1; contiguous chunks of
@@ -757,25 +739,7 @@ long first_bad_particle(const tdpd_sys *s, const float *pos, const float *vel)
     return first;
 }
 
-// Reference points of every membrane from the batch's load-order positions
-// (host), into the staging area and h_ref; membranes in parallel.
-void stage_membrane_refs(tdpd_sys *s, const float *pos)
-{
-    s->h_ref.resize(s->n_rbc);
-    host_parallel((size_t)s->n_rbc, 16, [&](size_t lo, size_t hi) {
-        for (size_t b = lo; b < hi; ++b) {
-            const RbcDev &D = s->h_rbcs[b];
-            stage_ref(s)[b] = s->h_ref[b] = membrane_ref_v(s, (int)b, pos + 3 * (size_t)D.gbase);
-        }
-    });
-}
 
-// p: the replica's load-order positions
-float4 membrane_ref(const tdpd_sys *s, int b, const float *p)
-{
-    const RbcDev &D = s->h_rbcs[b];
-    return membrane_ref_v(s, b, p + 3 * (size_t)(D.gbase - s->rep_pbase[D.rep]));
-}
 
 // Forces of a freshly loaded state: pack the uploaded load-order arrays into
 // buffer 0 (F = Q = 0), bin and sort into buffer 1, pair forces there (no
@@ -824,14 +788,17 @@ void enqueue_init(tdpd_sys *s, cudaStream_t st, bool branch)
     launch_pair(pa, st, PAIR_FINISH);
 }
 
-// Device part of loading a state whose reference points are staged and whose
-// load-order arrays are staged (upload_in) or already in d_in.
+// Device part of loading a state whose load-order arrays are staged
+// (upload_in) or already in d_in: the membranes' reference points, then the
+// forces of the state.
 tdpd_status init_device(tdpd_sys *s, bool upload_in)
 {
     cudaStream_t st = exec_stream(s);
     tdpd_status rc;
     if (upload_in && (rc = upload(s, s->d_in, stage_in(s), (size_t)s->N * (6 + s->ns)))) return rc;
-    if (s->n_rbc && (rc = upload(s, s->d_ref[1], stage_ref(s), s->n_rbc))) return rc;
+    int max_stride = 0;
+    for (const RbcDev &D : s->h_rbcs) max_stride = std::max(max_stride, D.fan_stride);
+    launch_mem_ref(s->d_in, s->d_rbcs, s->d_fan, s->d_reps, s->d_ref[1], s->n_rbc, s->max_nv, max_stride, st);
     uint32_t *ctr = stage_ctr(s);
     ctr[0] = ctr[1] = ctr[2] = (uint32_t)s->step;        // sort / pair, membrane (by parity)
     if ((rc = upload(s, s->step_ctr, ctr, 3))) return rc;
@@ -855,12 +822,6 @@ tdpd_status init_state(tdpd_sys *s)
         std::memcpy(x3 + 3 * base, R.pos.data(), sizeof(float) * 3 * n);
         std::memcpy(v3 + 3 * base, R.vel.data(), sizeof(float) * 3 * n);
         std::memcpy(c + base * ns, R.conc.data(), sizeof(float) * n * ns);
-    }
-    s->h_ref.resize(s->n_rbc);
-    for (int b = 0; b < s->n_rbc; ++b) {
-        const RbcDev &D = s->h_rbcs[b];
-        s->h_ref[b] = membrane_ref(s, b, s->reps[D.rep].pos.data());
-        stage_ref(s)[b] = s->h_ref[b];
     }
     return init_device(s, true);
 }
@@ -1456,7 +1417,7 @@ tdpd_status commit(tdpd_sys *s)
             return rc;
     }
     {
-        s->h_stage_bytes = stage_bytes(N, ns, s->n_rbc);
+        s->h_stage_bytes = stage_bytes(N, ns);
         void *hp = nullptr;
         CU(cudaMallocHost(&hp, s->h_stage_bytes));
         s->h_stage = static_cast<unsigned char *>(hp);
@@ -2169,13 +2130,6 @@ tdpd_status tdpd_set_states_device(tdpd_sys *s, const float *pos, const float *v
     CU(cudaStreamSynchronize(st));
     if (bad) return fail(s, TDPD_EINVAL, "a position outside its replica's box or a non-finite velocity");
     CU(cudaEventSynchronize(s->stage_done));
-    if (s->n_rbc) {
-        // the membranes' reference points come from their vertices (host)
-        std::vector<float> hp(3 * (size_t)N);
-        CU(cudaMemcpyAsync(hp.data(), pos, sizeof(float) * 3 * (size_t)N, cudaMemcpyDeviceToHost, st));
-        CU(cudaStreamSynchronize(st));
-        stage_membrane_refs(s, hp.data());
-    }
     CU(cudaMemcpyAsync(s->d_in, pos, sizeof(float) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, st));
     CU(cudaMemcpyAsync(s->d_in + 3 * (size_t)N, vel, sizeof(float) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, st));
     CU(cudaMemcpyAsync(s->d_in + 6 * (size_t)N, conc, sizeof(float) * (size_t)N * ns, cudaMemcpyDeviceToDevice, st));
@@ -2200,23 +2154,33 @@ tdpd_status tdpd_set_states(tdpd_sys *s, const float *pos, const float *vel, con
     if (rc) return rc;
     if (!pos || !vel || !conc) return fail(s, TDPD_EINVAL, "null array");
     const int N = s->N, ns = s->ns;
-    // the upload into the staging area goes first (by DMA from pinned arrays)
-    // and overlaps the host's check of the inputs and the membranes'
-    // reference points; nothing is adopted before the check passes
+    // the upload goes first (by DMA from pinned arrays); nothing is adopted
+    // before the inputs pass the check. A large batch is checked on the
+    // device (the host waits for one flag; a failed check is located on the
+    // host, for the message); a small one on the host while the DMA runs,
+    // which spares that round trip
     CU(cudaEventSynchronize(s->stage_done));
     cudaStream_t st = exec_stream(s);
     CU(cudaMemcpyAsync(s->d_in, pos, sizeof(float) * 3 * (size_t)N, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(s->d_in + 3 * (size_t)N, vel, sizeof(float) * 3 * (size_t)N, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(s->d_in + 6 * (size_t)N, conc, sizeof(float) * (size_t)N * ns, cudaMemcpyHostToDevice, st));
-    const long bad = first_bad_particle(s, pos, vel);
-    if (bad >= 0) {
-        CU(cudaStreamSynchronize(st));                // the caller's arrays are read
-        const size_t r = (size_t)(std::upper_bound(s->rep_pbase.begin(), s->rep_pbase.end(), (int)bad) -
-                                  s->rep_pbase.begin()) - 1;
-        return fail(s, TDPD_EINVAL, "replica %zu particle %ld: position outside the box or non-finite velocity", r,
-                    bad - s->rep_pbase[r]);
+    bool bad = false;
+    if (N > HOST_CHECK_MAX) {
+        CU(cudaMemsetAsync(s->d_flag, 0, sizeof(uint32_t), st));
+        launch_check_state(s->d_in, s->d_in + 3 * (size_t)N, s->d_wstat, s->d_reps, N, s->d_flag, st);
+        uint32_t *flag = stage_ctr(s) + 3;
+        CU(cudaMemcpyAsync(flag, s->d_flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        bad = *flag != 0u;
     }
-    stage_membrane_refs(s, pos);
+    const long first = bad || N <= HOST_CHECK_MAX ? first_bad_particle(s, pos, vel) : -1;
+    if (first >= 0 || bad) {
+        CU(cudaStreamSynchronize(st));                // the caller's arrays are read
+        const size_t r = first < 0 ? 0 : (size_t)(std::upper_bound(s->rep_pbase.begin(), s->rep_pbase.end(), (int)first) -
+                                                  s->rep_pbase.begin()) - 1;
+        return fail(s, TDPD_EINVAL, "replica %zu particle %ld: position outside the box or non-finite velocity", r,
+                    first < 0 ? -1L : first - s->rep_pbase[r]);
+    }
     if ((rc = init_device(s, false))) return rc;
     CU(cudaEventSynchronize(s->stage_done));         // the caller's arrays are read
     return TDPD_OK;
@@ -2241,7 +2205,6 @@ tdpd_status tdpd_set_state(tdpd_sys *s, int r, const float *pos, const float *ve
         // when they are pinned) and are packed there; the host copy of the
         // state is left as it was, every other path refreshes it before use
         CU(cudaEventSynchronize(s->stage_done));
-        for (int b = 0; b < s->n_rbc; ++b) stage_ref(s)[b] = s->h_ref[b] = membrane_ref(s, b, pos);
         cudaStream_t st = exec_stream(s);
         CU(cudaMemcpyAsync(s->d_in, pos, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
         CU(cudaMemcpyAsync(s->d_in + 3 * (size_t)n, vel, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));

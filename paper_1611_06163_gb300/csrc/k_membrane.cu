@@ -46,6 +46,7 @@ __device__ __forceinline__ float3 rel_pos(const RepParams &P, float4 x, float4 r
 // membranes read their triangle corners from global memory).
 constexpr int GATHER_STAGE_NV = 2048;
 constexpr int GATHER_THREADS = 512;
+constexpr int REF_THREADS = 256;
 
 // K-Gather: one CTA of GATHER_THREADS per membrane (512 at 64 registers: two
 // CTAs per SM, twice the resident membranes of 1024-thread CTAs; 46 -> 28 us
@@ -260,6 +261,112 @@ __global__ void __launch_bounds__(256, 4) k_mem_forces(MemArgs A)
         f.z += __shfl_xor_sync(0xffffffffu, f.z, o);
     }
     if (live && lane8 == 0) A.fext[R.gbase + v] = make_float4(f.x, f.y, f.z, 0.0f);
+}
+
+// Reference point of each membrane of a loaded state, from the uploaded
+// load-order positions x3 (three floats per particle): the centroid of its
+// vertices unwrapped along the mesh's edges from vertex 0 by the minimum
+// image, folded into the box. Each round, every unlabelled vertex takes its
+// image offsets k (per axis) from a labelled neighbour, k_u = k_v -
+// rint((p_u - p_v) / L); for a mesh whose edges are shorter than half the
+// box every path gives the same k. The coordinates relative to vertex 0,
+// (p_u - p_0) + k_u L, are summed with float-float compensation in a fixed
+// tree (as K-Gather sums its terms) and combined with p_0 once in binary64.
+// All arithmetic but that last step is binary32 (the FP64 unit of this GPU
+// is narrow). One CTA per membrane; the labels in shared memory (0: not
+// reached; else the three offsets, biased by 64, in the low bytes and bit
+// 24 set), and with STAGED the vertices' positions and neighbours too. A
+// vertex no edge reaches is left out of the sum.
+template <bool STAGED>
+__global__ void __launch_bounds__(REF_THREADS) k_mem_ref(const float *__restrict__ x3,
+                                                         const RbcDev *__restrict__ rbcs,
+                                                         const FanEntry *__restrict__ fan,
+                                                         const RepParams *__restrict__ reps, float4 *ref_out,
+                                                         int max_nv, int max_stride)
+{
+    extern __shared__ int sm[];
+    __shared__ FF wsum[REF_THREADS / 32][3];
+    const int b = blockIdx.x;
+    const RbcDev R = rbcs[b];
+    const RepParams &P = reps[R.rep];
+    const int nv = R.nv, stride = R.fan_stride;
+    volatile int *lab = sm;
+    float *ps = reinterpret_cast<float *>(sm + max_nv);             // STAGED: [3 nv]
+    int *nbs = sm + 4 * max_nv;                                     // STAGED: [nv stride]
+    const float *pg = x3 + 3 * (size_t)R.gbase;
+    const FanEntry *fg = fan + R.fan_off;
+    constexpr int SET = 1 << 24, ZERO = 64 | 64 << 8 | 64 << 16;
+    if (STAGED) {
+        for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) ps[i] = pg[i];
+        for (int i = threadIdx.x; i < nv * stride; i += blockDim.x) nbs[i] = fg[i].nb;
+    }
+    for (int u = threadIdx.x; u < nv; u += blockDim.x) lab[u] = u == 0 ? (SET | ZERO) : 0;
+    __syncthreads();
+    const float *p = STAGED ? ps : pg;
+    bool changed;
+    do {
+        changed = false;
+        for (int u = threadIdx.x; u < nv; u += blockDim.x) {
+            if (lab[u]) continue;
+            for (int l = 0; l < stride; ++l) {
+                const int v = STAGED ? nbs[u * stride + l] : fg[(size_t)u * stride + l].nb;
+                if (v < 0) break;
+                const int lv = lab[v];
+                if (!lv) continue;
+                int code = SET;
+                for (int c = 0; c < 3; ++c) {
+                    const int k = ((lv >> (8 * c)) & 255) - 64 - (int)rintf((p[3 * u + c] - p[3 * v + c]) * P.inv_L[c]);
+                    code |= (k + 64) << (8 * c);
+                }
+                lab[u] = code;
+                changed = true;
+                break;
+            }
+        }
+    } while (__syncthreads_or(changed));
+    FF acc[3] = {FF{0.0f, 0.0f}, FF{0.0f, 0.0f}, FF{0.0f, 0.0f}};
+    for (int u = threadIdx.x; u < nv; u += blockDim.x) {
+        const int lu = lab[u];
+        if (!lu) continue;
+        for (int c = 0; c < 3; ++c)
+            acc[c] = ff_add(acc[c], __fmaf_rn((float)(((lu >> (8 * c)) & 255) - 64), P.L[c], p[3 * u + c] - p[c]));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 3; ++c) acc[c] = ff_add(acc[c], ff_shfl_down(acc[c], o));
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) wsum[w][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    float cf[3];
+    for (int c = 0; c < 3; ++c) {
+        FF t = wsum[0][c];
+        for (int k = 1; k < REF_THREADS / 32; ++k) t = ff_add(t, wsum[k][c]);
+        double y = (double)p[c] + ff_value(t) / (double)nv;
+        if (P.periodic[c]) y -= (double)P.L[c] * floor(y / (double)P.L[c]);
+        cf[c] = (float)y;
+        if (!(cf[c] < P.L[c])) cf[c] = 0.0f;      // rounded up onto L
+    }
+    ref_out[b] = make_float4(cf[0], cf[1], cf[2], 0.0f);
+}
+
+void launch_mem_ref(const float *x3, const RbcDev *rbcs, const FanEntry *fan, const RepParams *reps, float4 *ref_out,
+                    int n_rbc, int max_nv, int max_stride, cudaStream_t st)
+{
+    if (n_rbc <= 0) return;
+    constexpr size_t SMEM_MAX = 200 * 1024;
+    const size_t staged = sizeof(int) * ((size_t)4 * max_nv + (size_t)max_nv * max_stride);
+    const size_t plain = sizeof(int) * (size_t)max_nv;
+    if (staged <= SMEM_MAX) {
+        if (staged > 48 * 1024)
+            cudaFuncSetAttribute(k_mem_ref<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged);
+        k_mem_ref<true><<<n_rbc, REF_THREADS, staged, st>>>(x3, rbcs, fan, reps, ref_out, max_nv, max_stride);
+    } else {
+        if (plain > 48 * 1024)
+            cudaFuncSetAttribute(k_mem_ref<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plain);
+        k_mem_ref<false><<<n_rbc, REF_THREADS, plain, st>>>(x3, rbcs, fan, reps, ref_out, max_nv, max_stride);
+    }
 }
 
 void launch_mem_gather(const MemArgs &a, cudaStream_t st, bool pdl)

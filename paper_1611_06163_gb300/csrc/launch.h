@@ -208,6 +208,11 @@ void launch_sort_small(const SortSmallArgs &a, int ctas, cudaStream_t st);
 void launch_bin_next(const Buffers &b, const RepParams *reps, int n, int *count, int *tile_sum, int2 *cellrank,
                      const uint32_t *rb, const uint32_t *any, cudaStream_t st, const DecideArgs &d = DecideArgs{});
 void launch_list_build(const ListArgs &a, cudaStream_t st);
+// each membrane's reference point (ref_out[b]) from the load-order positions
+// x3 (three floats per particle) of a loaded state; max_nv, max_stride: the
+// largest vertex count and fan stride of the membranes
+void launch_mem_ref(const float *x3, const RbcDev *rbcs, const FanEntry *fan, const RepParams *reps, float4 *ref_out,
+                    int n_rbc, int max_nv, int max_stride, cudaStream_t st);
 // pdl: launched as a programmatic dependent of the previous kernel on st
 void launch_mem_gather(const MemArgs &a, cudaStream_t st, bool pdl);
 void launch_mem_forces(const MemArgs &a, cudaStream_t st);
