@@ -771,7 +771,9 @@ void enqueue_init(tdpd_sys *s, cudaStream_t st, bool branch)
         launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0,
                            st, nullptr, 0, s->tile_sum[0], s->n_tiles, quarantine(s));
         cudaMemsetAsync(s->disp[1], 0, sizeof(uint32_t) * s->reps.size(), st);
-        launch_list_build(list_args(s, s->buf[1], s->rb_all, s->nl_cap), st);
+        // (the one- and two-species pair kernels build every lane's list
+        // themselves, as on a step where every replica rebuilds)
+        if (!pair_builds_lists(s)) launch_list_build(list_args(s, s->buf[1], s->rb_all, s->nl_cap), st);
     } else {
         launch_rank_gather(s->buf[0], s->buf[1], s->d_reps, s->keys, s->cellrank, s->cell_start, s->inv, N, ns, 0,
                            st, nullptr, 0, nullptr, 0, quarantine(s));
@@ -781,7 +783,8 @@ void enqueue_init(tdpd_sys *s, cudaStream_t st, bool branch)
         launch_mem_gather(m, st, true);
         launch_mem_forces(m, st);
     }
-    const PairArgs pa = pair_args(s, s->buf[1], 0, s->tile_sum[1], s->disp[1]);
+    const PairArgs pa = pair_args(s, s->buf[1], 0, s->tile_sum[1], s->disp[1],
+                                  s->use_list && pair_builds_lists(s) ? s->rb_all : nullptr);
     if (branch && !s->half) cudaStreamWaitEvent(st, s->join, 0);
     launch_pair(pa, st, PAIR_WALK);
     if (branch && s->half) cudaStreamWaitEvent(st, s->join, 0);
