@@ -20,7 +20,8 @@
 //
 // Coordinates are taken relative to a per-membrane reference point with the
 // minimum image, so a membrane may straddle the periodic boundary as long as
-// it spans less than half a box.
+// it spans less than half a box. K-Gather's vertex centroid is the next
+// step's reference point; a loaded state's comes from k_mem_ref.
 #include "launch.h"
 
 namespace tdpd {
